@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the dense registration hot path (arXiv 1807.00467, Sec. II-D).
+
+Workload: 512x512x128 voxels at 0.7x0.7x2.5 mm, grid 129x129x65, NGF eta=10,
+curvature alpha=1, volume change gamma=0.001, FP32 images, seeded synthetic
+lung phantom.  One step = one Gauss-Newton iteration of the fixed schedule at
+that level: objective + gradient + stored linearisation, a 30-step Jacobi PCG
+solve (30 full Gauss-Newton products H v = (H_D + alpha H_R + gamma H_V) v),
+and the Armijo line search.  value = Gauss-Newton products per second over
+the whole timed region (all kernels and host synchronisations included).
+
+Also reported: objective+gradient evaluations/s and matvec-only rate in
+isolated loops, the 3-level pyramid solve time, per-kernel CUDA-event times,
+the roofline of the dominant kernel, end-to-end throughput with host
+buffers, and the FP64 CPU oracle on this host as a baseline.
+
+Multi-GPU (torchrun): independent phantom pairs per rank (replicas, no
+collective on the data path), max time over ranks, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+# reuse generated phantoms between runs on the same machine
+os.environ.setdefault("NGF_PHANTOM_CACHE", os.path.join(tempfile.gettempdir(), "ngf_phantom_cache"))
+
+METRIC = "GN matvecs/s and obj+grad evals/s at 512x512x128 (GB/s vs peak); solve time"
+UNIT = "GN matvec/s"
+WORKLOAD = "512x512x128 FP32, 0.7x0.7x2.5 mm, grid 129x129x65, eta=10 alpha=1 gamma=0.001, GN step = grad+lin, 30 PCG, Armijo"
+
+# kernel ids of rg_profile_read
+K_MATVEC, K_GRADLIN, K_OBJ, K_VCC, K_VCC_GN, K_CURV, K_FIN, K_KP, K_TERMS, K_VEC, K_OTHER = range(11)
+KNAMES = {K_MATVEC: "ngf_tile_matvec", K_GRADLIN: "ngf_tile_grad_lin", K_OBJ: "ngf_tile_obj", K_VCC: "vcc_grad",
+          K_VCC_GN: "vcc_gn", K_CURV: "curv_L", K_FIN: "finalize_nodes", K_KP: "keypoints", K_TERMS: "terms",
+          K_VEC: "pcg_vector", K_OTHER: "other"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pcg-iters", type=int, default=30)
+    ap.add_argument("--no-extras", action="store_true", help="skip the isolated loops, pyramid and CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def alg_bytes(kernel, N, M):
+    """Algorithmic bytes per launch (each operand moved once)."""
+    if kernel == K_MATVEC:      # read a, dT (24 B/voxel), read v, write H v
+        return 24 * N + 24 * M
+    if kernel == K_GRADLIN:     # read R, T, write a, dT, read u, write grad
+        return 32 * N + 24 * M
+    if kernel == K_OBJ:         # read R, T, u
+        return 8 * N + 12 * M
+    if kernel in (K_VCC, K_CURV, K_FIN):
+        return 24 * M
+    if kernel == K_VCC_GN:
+        return 36 * M
+    return None
+
+
+def recorded_traffic(kernel_name):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_name}_full.md")
+    src = os.path.join(ROOT, "paper_1807_00467_gb300", "csrc", "ngf_tile.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    traffic, src_sha = None, None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+        if line.startswith("source_sha1:"):
+            src_sha = line.split(":", 1)[1].strip()
+    return traffic if (traffic and src_sha == sha) else None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[1]:
+                continue
+            try:
+                sm.append(float(parts[2]))
+                smax.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on this host, one GN product per step (bounded sample)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1807_00467_gb300 import phantom
+    c = phantom.CONFIGS["full"]
+    ph = phantom.make_phantom(c["n"], c["h"], seed=0, motion=c["motion"])
+    m = c["m"]
+    P = oracle.Problem(ph.R, ph.T, ph.h, m, eta=10.0, alpha=1.0, gamma=0.001)
+    u = phantom.motion_on_grid(ph, m, scale=0.5)
+    L = P.linearize(u)
+    v = phantom.random_grid_field(m, 100)
+    for _ in range(args.warmup):
+        L.matvec(v)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.matvec(v)
+    dt = time.perf_counter() - t0
+    val = args.steps / dt
+    cores = oracle.num_threads()
+    sample = f"{args.steps} oracle GN products at 512x512x128 (after one untimed linearisation)"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores,
+                                                               "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(ph, m, seconds):
+    import oracle
+    from paper_1807_00467_gb300 import phantom
+    P = oracle.Problem(ph.R, ph.T, ph.h, m, eta=10.0, alpha=1.0, gamma=0.001)
+    u = phantom.motion_on_grid(ph, m, scale=0.5)
+    L = P.linearize(u)
+    v = phantom.random_grid_field(m, 100)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        L.matvec(v)
+        n += 1
+        if time.perf_counter() - t0 > seconds or n >= 20:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} oracle GN products at 512x512x128 ({dt:.1f} s, after one untimed linearisation)"}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1807_00467_gb300 import _lib, api, phantom
+
+    world, rank, local = dist_setup()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    _lib.load()   # fails loudly if the CUDA library is missing
+
+    c = phantom.CONFIGS["full"]
+    n, h, m = c["n"], c["h"], c["m"]
+    ph = phantom.make_phantom(n, h, seed=rank, motion=c["motion"])
+    N, M = n[0] * n[1] * n[2], m[0] * m[1] * m[2]
+    stream = torch.cuda.Stream(device=dev)
+    params = api.make_params(eta=10.0, alpha=1.0, gamma=0.001)
+    with torch.cuda.stream(stream):
+        R = torch.from_numpy(ph.R).to(dev)
+        T = torch.from_numpy(ph.T).to(dev)
+        ctx = api.Context(R, T, h, m, params, stream=stream)
+        u = torch.zeros(ctx.grid_shape, device=dev)
+    stream.synchronize()
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    def gn_step():
+        code, rep = ctx.gn_solve(u, gn_iters=1, pcg_iters=args.pcg_iters)
+        return int(rep[0, 6])
+
+    for _ in range(args.warmup):
+        gn_step()
+    barrier()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    ctx.profile(True)
+    l0 = api.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    matvecs = 0
+    for _ in range(args.steps):
+        matvecs += gn_step()
+    e1.record(stream)
+    barrier()
+    launches = api.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    kt = {}
+    for k in KNAMES:
+        t, cnt = ctx.profile_read(k)
+        if cnt:
+            kt[k] = (t, cnt)
+    ctx.profile(False)
+    clk = clocks.stop()
+
+    local_ms = torch.tensor([ms], dtype=torch.float64, device=dev)
+    local_mv = torch.tensor([float(matvecs)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(local_ms, op=dist.ReduceOp.MAX)
+        dist.all_reduce(local_mv, op=dist.ReduceOp.SUM)
+    ms_max, mv_total = float(local_ms.item()), float(local_mv.item())
+    value = mv_total / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    peak, peak_kind = peaks()
+    dom = max(kt, key=lambda k: kt[k][0]) if kt else None
+    roof = None
+    if dom is not None:
+        t, cnt = kt[dom]
+        ab = alg_bytes(dom, N, M)
+        if ab is not None:
+            ach = ab / (t / cnt / 1e3) / 1e9
+            roof = {"bound": "hbm", "kernel": KNAMES[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "peak_source": peak_kind, "traffic": recorded_traffic(KNAMES[dom]),
+                    "alg_bytes_per_launch": ab, "avg_launch_us": 1e3 * t / cnt, "share": t / ms}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "voxels": list(n), "grid": list(m), "pcg_iters": args.pcg_iters,
+                      "l2": "inputs larger than L2 (R, T 268 MB, stored linearisation 805 MB)",
+                      "parallelism": f"replicas{world}" if world > 1 else "single"},
+           "gpu_launches": launches, "clocks": clk, "roofline": roof,
+           "kernels": {KNAMES[k]: {"ms": v[0], "launches": v[1], "avg_us": 1e3 * v[0] / v[1],
+                                   "share": v[0] / ms} for k, v in kt.items()}}
+
+    if not args.no_extras:
+        # isolated loops: objective+gradient, GN product alone
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        g = torch.empty_like(u)
+        terms = torch.empty(5, dtype=torch.float64, device=dev)
+        ctx.gn_linearize(u)
+        v = torch.from_numpy(phantom.random_grid_field(m, 100)).to(dev)
+        Hv = torch.empty_like(u)
+        for _ in range(3):
+            ctx.ngf_gradient(u, g, terms)
+            ctx.gn_matvec(v, Hv)
+        torch.cuda.synchronize(dev)
+        reps = max(10, args.steps)
+        ev[0].record(stream)
+        for _ in range(reps):
+            ctx.ngf_gradient(u, g, terms)
+        ev[1].record(stream)
+        for _ in range(reps):
+            ctx.gn_matvec(v, Hv)
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        out["obj_grad_evals_per_s"] = reps / (ev[0].elapsed_time(ev[1]) / 1e3)
+        out["matvec_only_per_s"] = reps / (ev[1].elapsed_time(ev[2]) / 1e3)
+        # end to end through the C ABI with host buffers: per step copy R, T, u
+        # from pinned host memory, one GN iteration, read u back
+        Rh, Th = torch.from_numpy(ph.R).pin_memory(), torch.from_numpy(ph.T).pin_memory()
+        uh = torch.zeros(ctx.grid_shape).pin_memory()
+        uo = torch.empty(ctx.grid_shape).pin_memory()
+        e2e_steps = max(3, args.steps // 4)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        mv = 0
+        for _ in range(e2e_steps):
+            with torch.cuda.stream(stream):
+                R.copy_(Rh, non_blocking=True)
+                T.copy_(Th, non_blocking=True)
+                u.copy_(uh, non_blocking=True)
+            mv += gn_step()
+            with torch.cuda.stream(stream):
+                uo.copy_(u, non_blocking=True)
+            stream.synchronize()
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = ev[0].elapsed_time(ev[1])
+        out["e2e"] = {"value": mv / (e2e_ms / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(Rh.numel() * 4 + Th.numel() * 4 + uh.numel() * 4),
+                      "d2h_bytes_per_step": int(uo.numel() * 4)}
+        # 3-level pyramid solve (128x128x32 -> 256x256x64 -> 512x512x128), 10 GN x 30 PCG per level
+        u3 = torch.zeros(ctx.grid_shape, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        code, rep = api.register_pyramid(R, T, h, m, u3, params, levels=3, gn_iters=10, pcg_iters=30, stream=stream)
+        torch.cuda.synchronize(dev)
+        out["solve_s"] = time.perf_counter() - t0
+        out["solve_config"] = "3 levels x 10 GN x 30 PCG, Armijo; 128x128x32 -> 512x512x128"
+        if rank == 0 and world == 1:
+            out["cpu_baseline"] = cpu_baseline(ph, m, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

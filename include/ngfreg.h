@@ -1,0 +1,197 @@
+/*
+ * ngfreg: GB300 (sm_103a) library for the dense continuous registration stage
+ * of Ruehaak et al., "Estimation of Large Motion in Lung CT by Integrating
+ * Regularized Keypoint Correspondences into Dense Deformable Registration"
+ * (arXiv 1807.00467), Sec. II-D.
+ *
+ * The objective (Eq. (11), with the mask term B left out, beta = 0) is
+ *     J(u) = D(u) + alpha R(u) + gamma V(u) + delta K(u)
+ *   D  normalized gradient fields distance, Eq. (1)
+ *   R  curvature regulariser, Eq. (5) (y_hat = identity)
+ *   V  volume change control in the 64-bound form V-hat, Eqs. (7)-(9)
+ *   K  quadratic keypoint penalty, Eq. (10)
+ * over a displacement u on a node grid, y(x) = x + (P u)(x) with P trilinear
+ * interpolation (first-order B-spline, Sec. II-D1 and II-D3).  The library
+ * evaluates J, its gradient, Gauss-Newton matrix-vector products (the
+ * "Hessian approximation" of Sec. II-D3), a fixed-length Jacobi PCG solve, a
+ * fixed Gauss-Newton schedule with Armijo backtracking, and a multilevel
+ * (pyramid) driver, all matrix-free (Sec. II-D3).
+ *
+ * Discretisation (the paper leaves these open):
+ *   - Images are [n3][n2][n1] (x fastest), cell-centred voxels: voxel i has
+ *     centre (i + 1/2) h, in mm.  D sums over interior voxels 1..n-2 of each
+ *     axis with central differences of R and of the warped template.
+ *   - The node grid has m nodes per axis spanning [0, n h] exactly, node
+ *     spacing g = n h / (m - 1); rho = n / (m - 1) must be 1, 2, 4 or 8.
+ *     Grid fields are float32 [3][m3][m2][m1] (x, y, z components, mm).
+ *   - Out-of-domain samples of the template are clamped per axis, with zero
+ *     derivative along a clamped axis.  The sample cell of each voxel is
+ *     chosen in FP32 from the displacement interpolated along x, then y, then
+ *     z (each step fma(w1, b, w0 * a)), times float(1/h), floor.
+ *
+ * Conventions for every call:
+ *   - All pointers named *_dev are device pointers (cudaMalloc'd or torch
+ *     tensors' data_ptr); the caller owns them.  Arrays are contiguous.
+ *   - Work is enqueued on the context's CUDA stream and is asynchronous unless
+ *     stated otherwise.  Outputs are written on that stream.
+ *   - The library allocates no device memory after rg_ctx_create: it carves
+ *     all scratch from the caller's workspace (rg_workspace_size bytes).
+ *   - Return value: RG_OK (0), RG_EFOLD (1: some Jacobian bound d <= 0, the
+ *     objective is +inf), or a negative error code.  Errors are latched in
+ *     the context and described by rg_last_error().
+ */
+#ifndef NGFREG_H
+#define NGFREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RG_OK 0
+#define RG_EFOLD 1
+#define RG_EINVAL (-1)
+#define RG_ECUDA (-2)
+#define RG_ENOMEM (-3)
+#define RG_ENONFINITE (-4)
+#define RG_ETIMEOUT (-5)
+
+/* Which regulariser regularizer_apply evaluates. */
+#define RG_CURV 1
+#define RG_VCC 2
+#define RG_KP 4
+
+typedef struct {
+    int32_t n[3];    /* voxels per axis (x, y, z), each >= 4 */
+    double h[3];     /* voxel spacing, mm */
+} rg_image_geom;
+
+typedef struct {
+    int32_t m[3];    /* grid nodes per axis; n[a] / (m[a] - 1) in {1, 2, 4, 8} */
+} rg_grid_geom;
+
+typedef enum { RG_F32 = 0, RG_F16 = 1 } rg_dtype;
+
+typedef struct {
+    double eta;           /* NGF edge parameter eta of Eq. (1) */
+    double alpha;         /* curvature weight, Eq. (11) */
+    double gamma;         /* volume-change weight, Eq. (11); 0 disables V */
+    double delta;         /* keypoint weight, Eq. (11) */
+    int32_t delta_adaptive; /* 1: delta = D(u0)/K(u0) at the start (Sec. II-D2) */
+    double tau;           /* extra shift added to the PCG preconditioner diagonal (0 by default) */
+} rg_params;
+
+typedef struct {
+    int32_t levels;       /* pyramid levels (register_pyramid), >= 1 */
+    int32_t gn_iters;     /* Gauss-Newton steps per level */
+    int32_t pcg_iters;    /* PCG steps per Gauss-Newton step */
+    int32_t ls_max;       /* line search tries t = 1, 1/2, ..., 2^-ls_max */
+    double armijo_c;      /* Armijo constant */
+} rg_schedule;
+
+typedef struct rg_ctx rg_ctx;
+
+/* Workspace bytes a context for this problem needs (nk_max: the largest
+ * keypoint count rg_set_keypoints will be given).  Returns RG_EINVAL on bad
+ * geometry. */
+int rg_workspace_size(const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype,
+                      int32_t nk_max, size_t *bytes);
+
+/* Create a context.  workspace_dev: caller-owned device memory of at least
+ * rg_workspace_size bytes, 256-byte aligned, kept alive until destroy.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream). */
+int rg_ctx_create(rg_ctx **ctx, const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype,
+                  const rg_params *params, int32_t nk_max, void *workspace_dev, size_t ws_bytes,
+                  void *cuda_stream);
+int rg_ctx_destroy(rg_ctx *ctx);
+int rg_set_params(rg_ctx *ctx, const rg_params *params);
+int rg_get_params(const rg_ctx *ctx, rg_params *params);
+int rg_set_stream(rg_ctx *ctx, void *cuda_stream);
+
+/* Borrow the reference R (fixed image F) and template T (moving image M),
+ * [n3][n2][n1], float32 for RG_F32, IEEE half of (HU + 1024) for RG_F16.
+ * The pointers must stay valid while the context uses them. */
+int rg_set_images(rg_ctx *ctx, const void *R_dev, const void *T_dev);
+
+/* Borrow keypoints: x_dev, ykp_dev are float32 [nk][3] (mm), Eq. (10). */
+int rg_set_keypoints(rg_ctx *ctx, int32_t nk, const float *x_dev, const float *ykp_dev);
+
+/* terms_dev: double[5] = {D, R, V, K, J}, Eq. (11).  J = +inf on a fold. */
+int ngf_objective(rg_ctx *ctx, const float *u_dev, double *terms_dev);
+
+/* As ngf_objective, plus grad_dev = dJ/du, float32 [3][m3][m2][m1]. */
+int ngf_gradient(rg_ctx *ctx, const float *u_dev, double *terms_dev, float *grad_dev);
+
+/* Store the Gauss-Newton linearisation at u (per-voxel dT/dy and dr/dg, and
+ * u itself for the VCC term) for subsequent gn_matvec / gn_pcg_solve calls.
+ * If grad_dev / terms_dev are not NULL the gradient and terms at u are
+ * produced by the same pass. */
+int gn_linearize(rg_ctx *ctx, const float *u_dev, double *terms_dev, float *grad_dev);
+
+/* Hv = H v with H = H_D + alpha H_R + gamma H_V + delta H_K at the stored
+ * linearisation; H_D = 2 hbar J^T J, J = dr/du (NGF residual Jacobian). */
+int gn_matvec(rg_ctx *ctx, const float *v_dev, float *Hv_dev);
+
+/* One regulariser (which = RG_CURV, RG_VCC or RG_KP) at u: v_dev == NULL
+ * gives out = gradient, else out = (GN) Hessian times v; energy_dev: one
+ * double (unweighted energy).  Weights alpha, gamma, delta are NOT applied. */
+int regularizer_apply(rg_ctx *ctx, int32_t which, const float *u_dev, const float *v_dev,
+                      double *energy_dev, float *out_dev);
+
+/* Fixed-length Jacobi-preconditioned CG on H p = -g at the stored
+ * linearisation, p0 = 0; stops early only if r.z or p.Hp stop being
+ * positive.  Preconditioner: the diagonal of H, with the NGF part taken
+ * without the cross terms of the central-difference adjoint
+ * (2 hbar sum_x w_k(x)^2 dT_c(x)^2 sum_a (a_{x-e_a,a}^2 + a_{x+e_a,a}^2)/(4 h_a^2)),
+ * plus tau; non-positive entries use 1.
+ * stats_dev: double[3] = {steps, |r0|, |r_end|} (may be NULL). */
+int gn_pcg_solve(rg_ctx *ctx, const float *g_dev, float *p_dev, int32_t iters, double *stats_dev);
+
+/* Fixed Gauss-Newton schedule on one level: gn_iters x (gradient +
+ * linearisation, PCG, Armijo backtracking).  u_dev is updated in place.
+ * report_host: double[gn_iters][8] = {it, J, g.p, t (0 = rejected), J new,
+ * evaluations, pcg steps, status} or NULL.  Synchronises the stream once per
+ * line-search try. */
+int gn_solve(rg_ctx *ctx, float *u_dev, const rg_schedule *sched, double *report_host);
+
+/* Multilevel registration (Sec. II-D3): levels-1 times 2x2x2 box restriction
+ * of R and T and halving of the grid, coarse-to-fine gn_solve, dyadic grid
+ * prolongation between levels.  R_dev, T_dev, u_inout_dev are at the finest
+ * level; u_inout's start value is injected onto the coarsest grid.
+ * workspace_dev: rg_pyramid_workspace_size bytes.  report_host:
+ * double[levels][gn_iters][8] (coarsest first) or NULL. */
+int rg_pyramid_workspace_size(const rg_image_geom *img, const rg_grid_geom *finest, rg_dtype dtype,
+                              int32_t levels, int32_t nk_max, size_t *bytes);
+int register_pyramid(const rg_image_geom *img, const void *R_dev, const void *T_dev, rg_dtype dtype,
+                     const rg_grid_geom *finest, const rg_params *params, const rg_schedule *sched,
+                     int32_t nk, const float *kx_dev, const float *ky_dev, float *u_inout_dev,
+                     double *report_host, void *workspace_dev, size_t ws_bytes, void *cuda_stream);
+
+/* 2x2x2 box restriction of an image (float32 or half as dtype), n even. */
+int rg_restrict_image(const int32_t *n, rg_dtype dtype, const void *in_dev, void *out_dev, void *cuda_stream);
+/* Dyadic trilinear prolongation of a grid field from mc nodes to mf = 2 mc - 1. */
+int rg_prolong_grid(const int32_t *mc, const float *uc_dev, float *uf_dev, void *cuda_stream);
+
+/* Per-kernel timing with CUDA events recorded on the context stream around
+ * every kernel launch while enabled.  Kernel ids: 0 NGF Gauss-Newton product
+ * tile kernel, 1 NGF gradient/linearisation tile kernel, 2 NGF objective tile
+ * kernel, 3 VCC gradient, 4 VCC Gauss-Newton product, 5 curvature L, 6 node
+ * finaliser, 7 keypoints, 8 objective terms, 9 PCG/vector kernels, 10 other.
+ * rg_profile_read synchronises on the recorded events, returns the summed
+ * elapsed milliseconds and launch count of one id, and forgets them. */
+int rg_profile(rg_ctx *ctx, int32_t enable);
+int rg_profile_read(rg_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches);
+/* Number of kernels this library has launched in the process so far. */
+int64_t rg_launch_count(void);
+
+/* Latched error text of the last failing call on this context. */
+const char *rg_last_error(const rg_ctx *ctx);
+/* Library build/version string. */
+const char *rg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

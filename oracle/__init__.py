@@ -71,7 +71,8 @@ def lib():
         L.orc_lin_free.argtypes = [C.c_void_p]
         L.orc_ngf_gn_matvec.argtypes = [P, C.c_void_p, dp, dp]
         L.orc_gn_matvec.argtypes = [P, C.c_void_p, dp, dp]
-        L.orc_jacobi_diag.argtypes = [P, C.c_double, dp]
+        L.orc_gn_diag.argtypes = [P, C.c_void_p, C.c_double, dp]
+        L.orc_vcc_diag.argtypes = [P, dp, dp]
         L.orc_pcg.argtypes = [P, C.c_void_p, dp, dp, C.c_int, C.c_double, dp]
         L.orc_gn_solve.argtypes = [P, dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, dp]
         L.orc_restrict_image.argtypes = [ip, fp, fp]
@@ -210,19 +211,20 @@ class Problem:
     def linearize(self, u):
         return Lin(self, u)
 
-    def jacobi_diag(self, tau=10.0):
+    def vcc_diag(self, u):
+        u = _f64(u)
         d = np.zeros(self.grid_shape)
-        lib().orc_jacobi_diag(self._ref(), tau, _dp(d))
+        lib().orc_vcc_diag(self._ref(), _dp(u), _dp(d))
         return d
 
-    def gn_solve(self, u0, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, tau=10.0, delta_adaptive=False):
+    def gn_solve(self, u0, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, tau=0.0, delta_adaptive=False):
         u = _f64(u0).copy()
         rep = np.zeros((gn_iters, 8))
         st = lib().orc_gn_solve(self._ref(), _dp(u), gn_iters, pcg_iters, ls_max, armijo_c, tau,
                                 int(delta_adaptive), _dp(rep))
         return u, rep, st
 
-    def register_pyramid(self, u0, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, tau=10.0,
+    def register_pyramid(self, u0, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, tau=0.0,
                          delta_adaptive=False):
         u = _f64(u0).copy()
         rep = np.zeros((levels, gn_iters, 8))
@@ -256,7 +258,12 @@ class Lin:
         lib().orc_gn_matvec(self.prob._ref(), self.ptr, _dp(v), _dp(out))
         return out
 
-    def pcg(self, g, iters, tau=10.0):
+    def gn_diag(self, tau=0.0):
+        d = np.zeros(self.prob.grid_shape)
+        lib().orc_gn_diag(self.prob._ref(), self.ptr, tau, _dp(d))
+        return d
+
+    def pcg(self, g, iters, tau=0.0):
         g = _f64(g)
         s = np.zeros(self.prob.grid_shape)
         stats = np.zeros(3)

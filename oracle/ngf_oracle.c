@@ -536,6 +536,68 @@ int orc_vcc(const orc_problem *p, const double *u, const double *v, double *ener
     return fold ? 1 : 0;
 }
 
+/* Diagonal of the VCC Gauss-Newton matrix: ghat sum_cells sum_abc
+ * psi''(d) (d d_abc / d u_{k,c})^2, gathered per node. */
+void orc_vcc_diag(const orc_problem *p, const double *u, double *out) {
+    const int *m = p->m;
+    long M = nnod(p);
+    int nc[3] = {m[0] - 1, m[1] - 1, m[2] - 1};
+    long NC = (long)nc[0] * nc[1] * nc[2];
+    double G = ghat(p);
+    double *cellout = calloc((size_t)NC * 24, sizeof(double));
+#pragma omp parallel for collapse(2)
+    for (int c3 = 0; c3 < nc[2]; ++c3)
+        for (int c2 = 0; c2 < nc[1]; ++c2)
+            for (int c1 = 0; c1 < nc[0]; ++c1) {
+                double E[3][4][3];
+                cell_edges(p, u, c1, c2, c3, E);
+                double *co = cellout + 24 * (long)IDX(nc, c1, c2, c3);
+                for (int a = 0; a < 4; ++a)
+                    for (int b = 0; b < 4; ++b)
+                        for (int c = 0; c < 4; ++c) {
+                            double x23[3], x31[3], x12[3];
+                            cross(E[1][b], E[2][c], x23);
+                            cross(E[2][c], E[0][a], x31);
+                            cross(E[0][a], E[1][b], x12);
+                            double d = dot3(E[0][a], x23);
+                            if (d <= 0.0) continue;
+                            double gd[8][3];
+                            memset(gd, 0, sizeof gd);
+                            int idx[3] = {a, b, c};
+                            const double *X[3] = {x23, x31, x12};
+                            for (int ax = 0; ax < 3; ++ax) {
+                                int o0[3], o1[3];
+                                edge_ends(ax, idx[ax], o0, o1);
+                                int s0 = o0[0] + 2 * o0[1] + 4 * o0[2], s1 = o1[0] + 2 * o1[1] + 4 * o1[2];
+                                for (int k = 0; k < 3; ++k) {
+                                    gd[s1][k] += X[ax][k] / gsp(p, ax);
+                                    gd[s0][k] -= X[ax][k] / gsp(p, ax);
+                                }
+                            }
+                            for (int o = 0; o < 8; ++o)
+                                for (int k = 0; k < 3; ++k) co[3 * o + k] += G * d2psi(d) * gd[o][k] * gd[o][k];
+                        }
+            }
+#pragma omp parallel for collapse(2)
+    for (int k3 = 0; k3 < m[2]; ++k3)
+        for (int k2 = 0; k2 < m[1]; ++k2)
+            for (int k1 = 0; k1 < m[0]; ++k1) {
+                double acc[3] = {0, 0, 0};
+                for (int o3 = 0; o3 < 2; ++o3)
+                    for (int o2 = 0; o2 < 2; ++o2)
+                        for (int o1 = 0; o1 < 2; ++o1) {
+                            int c1 = k1 - o1, c2 = k2 - o2, c3 = k3 - o3;
+                            if (c1 < 0 || c2 < 0 || c3 < 0 || c1 >= nc[0] || c2 >= nc[1] || c3 >= nc[2]) continue;
+                            const double *co = cellout + 24 * (long)IDX(nc, c1, c2, c3);
+                            int sidx = o1 + 2 * o2 + 4 * o3;
+                            for (int comp = 0; comp < 3; ++comp) acc[comp] += co[3 * sidx + comp];
+                        }
+                long node = IDX(m, k1, k2, k3);
+                for (int comp = 0; comp < 3; ++comp) out[comp * M + node] = acc[comp];
+            }
+    free(cellout);
+}
+
 /* ------------------------------------------------------------------ */
 /* Keypoint penalty, Eq. (10).                                         */
 /* ------------------------------------------------------------------ */
@@ -690,18 +752,67 @@ void orc_gn_matvec(const orc_problem *p, const orc_lin *L, const double *v, doub
     free(tmp);
 }
 
-/* Jacobi preconditioner diag(alpha H_R) + 2 delta diag(P_K^T P_K) + tau,
- * after the paper's initial Hessian R + tau I (Sec. II-D3). */
-void orc_jacobi_diag(const orc_problem *p, double tau, double *diag) {
-    long M = nnod(p);
-    const int *m = p->m;
-    double G = ghat(p), g2[3];
+/* Jacobi preconditioner: diagonal of the Gauss-Newton matrix H, with the
+ * NGF part taken without the cross terms of the central-difference adjoint:
+ *   M = 2 hbar sum_x w_k(x)^2 dT_c(x)^2 beta_x                 (NGF, approximate)
+ *     + alpha diag(H_R) + gamma diag(H_V) + delta diag(H_K)     (exact)
+ *     + tau,
+ * beta_x = sum_a (a_{x-e_a,a}^2 + a_{x+e_a,a}^2) / (4 h_a^2), w_k the trilinear
+ * weight of node k.  (J e_k)_v is a sum of six neighbour terms; the NGF part
+ * keeps the sum of their squares.  Entries that come out as 0 are set to 1. */
+static double node_weight(const orc_problem *p, int a, int i, int k) {
+    int c;
+    double f;
+    axis_weight(i, ratio(p, a), &c, &f);
+    if (c == k) return 1.0 - f;
+    if (c == k - 1) return f;
+    return 0.0;
+}
+
+void orc_gn_diag(const orc_problem *p, const orc_lin *L, double tau, double *diag) {
+    long N = nvox(p), M = nnod(p);
+    const int *n = p->n, *m = p->m;
+    double hb = hbar(p), G = ghat(p), g2[3];
     for (int a = 0; a < 3; ++a) g2[a] = gsp(p, a) * gsp(p, a);
+    /* beta_x */
+    double *beta = malloc(sizeof(double) * N);
+#pragma omp parallel for collapse(2)
+    for (int i3 = 0; i3 < n[2]; ++i3)
+        for (int i2 = 0; i2 < n[1]; ++i2)
+            for (int i1 = 0; i1 < n[0]; ++i1) {
+                int ii[3] = {i1, i2, i3};
+                long st[3] = {1, n[0], (long)n[0] * n[1]};
+                long x = IDX(n, i1, i2, i3);
+                double b = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    double s = 0.0;
+                    if (ii[a] - 1 >= 0) s += L->a[a * N + x - st[a]] * L->a[a * N + x - st[a]];
+                    if (ii[a] + 1 <= n[a] - 1) s += L->a[a * N + x + st[a]] * L->a[a * N + x + st[a]];
+                    b += s / (4.0 * p->h[a] * p->h[a]);
+                }
+                beta[x] = b;
+            }
+    /* NGF part and curvature part, gathered per node */
+#pragma omp parallel for collapse(2)
     for (int k3 = 0; k3 < m[2]; ++k3)
         for (int k2 = 0; k2 < m[1]; ++k2)
             for (int k1 = 0; k1 < m[0]; ++k1) {
                 int kk[3] = {k1, k2, k3};
-                /* column k of L: own row (if interior on an axis) and neighbour rows */
+                int lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    int rho = ratio(p, a);
+                    lo[a] = (kk[a] - 1) * rho; if (lo[a] < 0) lo[a] = 0;
+                    hi[a] = (kk[a] + 1) * rho - 1; if (hi[a] > n[a] - 1) hi[a] = n[a] - 1;
+                }
+                double acc[3] = {0, 0, 0};
+                for (int i3 = lo[2]; i3 <= hi[2]; ++i3)
+                    for (int i2 = lo[1]; i2 <= hi[1]; ++i2)
+                        for (int i1 = lo[0]; i1 <= hi[0]; ++i1) {
+                            double w = node_weight(p, 0, i1, k1) * node_weight(p, 1, i2, k2) * node_weight(p, 2, i3, k3);
+                            if (w == 0.0) continue;
+                            long x = IDX(n, i1, i2, i3);
+                            for (int c = 0; c < 3; ++c) acc[c] += w * w * L->dT[c * N + x] * L->dT[c * N + x] * beta[x];
+                        }
                 double own = 0.0, nb = 0.0;
                 for (int a = 0; a < 3; ++a) {
                     if (node_interior_axis(m, kk, a)) own += -2.0 / g2[a];
@@ -710,10 +821,17 @@ void orc_jacobi_diag(const orc_problem *p, double tau, double *diag) {
                     if (km[a] >= 0 && node_interior_axis(m, km, a)) nb += 1.0 / (g2[a] * g2[a]);
                     if (kp[a] <= m[a] - 1 && node_interior_axis(m, kp, a)) nb += 1.0 / (g2[a] * g2[a]);
                 }
-                double dR = G * (own * own + nb);
                 long node = IDX(m, k1, k2, k3);
-                for (int comp = 0; comp < 3; ++comp) diag[comp * M + node] = p->alpha * dR + tau;
+                for (int c = 0; c < 3; ++c) diag[c * M + node] = 2.0 * hb * acc[c] + p->alpha * G * (own * own + nb);
             }
+    free(beta);
+    /* VCC part: per cell, psi''(d) (d d / d u_{k,c})^2 for its 8 corners */
+    if (p->gamma != 0.0) {
+        double *vd = malloc(sizeof(double) * 3 * M);
+        orc_vcc_diag(p, L->u, vd);
+        for (long i = 0; i < 3 * M; ++i) diag[i] += p->gamma * vd[i];
+        free(vd);
+    }
     if (p->nk > 0 && p->delta != 0.0)
         for (int i = 0; i < p->nk; ++i) {
             int c[3];
@@ -727,6 +845,10 @@ void orc_jacobi_diag(const orc_problem *p, double tau, double *diag) {
                         for (int comp = 0; comp < 3; ++comp) diag[comp * M + node] += 2.0 * p->delta * w * w;
                     }
         }
+    for (long i = 0; i < 3 * M; ++i) {
+        diag[i] += tau;
+        if (!(diag[i] > 0.0)) diag[i] = 1.0;
+    }
 }
 
 static double vdot(long n, const double *a, const double *b) {
@@ -744,7 +866,7 @@ int orc_pcg(const orc_problem *p, const orc_lin *L, const double *g, double *s, 
     double *r = malloc(sizeof(double) * n3), *z = malloc(sizeof(double) * n3);
     double *d = malloc(sizeof(double) * n3), *q = malloc(sizeof(double) * n3);
     double *Md = malloc(sizeof(double) * n3);
-    orc_jacobi_diag(p, tau, Md);
+    orc_gn_diag(p, L, tau, Md);
     for (long i = 0; i < n3; ++i) { s[i] = 0.0; r[i] = -g[i]; z[i] = r[i] / Md[i]; d[i] = z[i]; }
     double rz = vdot(n3, r, z);
     double r0 = sqrt(vdot(n3, r, r));

@@ -74,7 +74,10 @@ orc_lin *orc_linearize(const orc_problem *p, const double *u);
 void orc_lin_free(orc_lin *L);
 void orc_ngf_gn_matvec(const orc_problem *p, const orc_lin *L, const double *v, double *Hv);
 void orc_gn_matvec(const orc_problem *p, const orc_lin *L, const double *v, double *Hv);
-void orc_jacobi_diag(const orc_problem *p, double tau, double *diag);
+/* Jacobi preconditioner at the linearisation: NGF diagonal without the
+ * adjoint's cross terms, exact curvature / VCC / keypoint diagonals, + tau. */
+void orc_gn_diag(const orc_problem *p, const orc_lin *L, double tau, double *diag);
+void orc_vcc_diag(const orc_problem *p, const double *u, double *out);
 
 /* Jacobi-preconditioned CG on H s = -g, fixed iteration count, s0 = 0. */
 int orc_pcg(const orc_problem *p, const orc_lin *L, const double *g, double *s, int iters,

@@ -1,0 +1,835 @@
+// C ABI of the ngfreg library: contexts over a caller-provided workspace,
+// objective / gradient / Gauss-Newton products, PCG, the fixed Gauss-Newton
+// schedule and the multilevel driver (Sec. II-D of arXiv 1807.00467).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ngfreg.h"
+#include "kernels.h"
+
+using namespace ngf;
+
+struct rg_ctx {
+    rg_image_geom img;
+    rg_grid_geom grid;
+    rg_dtype dtype;
+    rg_params P;
+    int nk_max;
+    cudaStream_t st;
+    const void *R, *T;
+    int nk;
+    const float *kx, *ky;
+    long N, M;
+    double g[3], hbar, ghat;
+    TileGeom tg;
+    BoxGeom bA, bB;
+    int nA, nB, nR, nKb, nV;
+    float *lin_dT, *lin_a, *lin_u;
+    float *boxA, *boxB, *curv_w;
+    double *dpart, *rpart, *vpart, *kpart, *vecpart, *terms_tmp, *dminmax;
+    int *fold;
+    float *dmin, *dmax;
+    float *minv, *r, *z, *d, *q, *tg_, *tu, *ts;
+    PcgScalars *sc;
+    bool has_lin, minv_valid;
+    char err[512];
+    // optional per-kernel CUDA-event timing (rg_profile)
+    bool prof;
+    std::vector<cudaEvent_t> *ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *ev_used;
+};
+
+static std::atomic<long long> g_launches{0};
+struct ProfScope;
+
+// Record events around one library kernel launch when profiling is on.
+struct ProfScope {
+    rg_ctx *c;
+    int id;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(rg_ctx *c_, int id_) : c(c_), id(id_) {
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (!c || !c->prof) return;
+        a = take();
+        b = take();
+        if (a && b) cudaEventRecord(a, c->st);
+    }
+    cudaEvent_t take() {
+        cudaEvent_t e = nullptr;
+        if (!c->ev_pool->empty()) {
+            e = c->ev_pool->back();
+            c->ev_pool->pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+        }
+        return e;
+    }
+    ~ProfScope() {
+        if (!c || !c->prof || !a || !b) return;
+        cudaEventRecord(b, c->st);
+        c->ev_used->push_back({id, {a, b}});
+    }
+};
+
+#define LAUNCH(id, expr)           \
+    do {                           \
+        ProfScope ps_(c, (id));    \
+        CK(expr);                  \
+    } while (0)
+
+static int set_err(rg_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(expr)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return set_err(c, RG_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+static bool pow2_le8(int r) { return r == 1 || r == 2 || r == 4 || r == 8; }
+
+static int check_geom(const rg_image_geom *img, const rg_grid_geom *grid) {
+    if (!img || !grid) return RG_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        if (img->n[a] < 4 || grid->m[a] < 2 || !(img->h[a] > 0.0)) return RG_EINVAL;
+        if (img->n[a] % (grid->m[a] - 1) != 0) return RG_EINVAL;
+        if (!pow2_le8(img->n[a] / (grid->m[a] - 1))) return RG_EINVAL;
+    }
+    if ((long)img->n[0] * img->n[1] * img->n[2] >= (1L << 31) * 3L / 4) return RG_EINVAL;
+    return RG_OK;
+}
+
+// Tile shape: 32 x TY voxels in x-y, TZ voxels per z chunk.
+static void tile_geom(const rg_image_geom *img, const rg_grid_geom *grid, TileGeom &t) {
+    for (int a = 0; a < 3; ++a) {
+        t.n[a] = img->n[a];
+        t.m[a] = grid->m[a];
+        t.rho[a] = img->n[a] / (grid->m[a] - 1);
+        t.invh[a] = (float)(1.0 / img->h[a]);
+        t.invh_rel[a] = (float)(1.0 - img->h[a] * (double)t.invh[a]);
+        t.inv2h[a] = (float)(1.0 / (2.0 * img->h[a]));
+    }
+    t.TY = 16;
+    t.nxt = (kTileX + 3) / t.rho[0] + 3;
+    t.nyt = (t.TY + 3) / t.rho[1] + 3;
+    t.C[0] = kTileX / t.rho[0];
+    t.C[1] = t.TY / t.rho[1];
+    t.nb[0] = (t.n[0] + kTileX - 1) / kTileX;
+    t.nb[1] = (t.n[1] + t.TY - 1) / t.TY;
+    // z chunk: 32 voxels, shrunk (in whole cells) while the shared memory of
+    // the gradient kernel would exceed 110 KB (fine grids: large node boxes)
+    int tz = 32 - 32 % t.rho[2];
+    if (tz < t.rho[2]) tz = t.rho[2];
+    for (;;) {
+        t.TZ = tz;
+        t.C[2] = tz / t.rho[2];
+        t.box = (t.C[0] + 1) * (t.C[1] + 1) * (t.C[2] + 1);
+        if (tile_smem_bytes(t, MODE_GRAD) <= 110 * 1024 || tz <= t.rho[2]) break;
+        tz -= t.rho[2];
+    }
+    t.nb[2] = (t.n[2] + t.TZ - 1) / t.TZ;
+}
+
+struct Carver {
+    char *base;
+    size_t off;
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static void layout(rg_ctx *c, Carver &cv) {
+    const long N = c->N, M = c->M;
+    c->lin_dT = cv.take<float>(3 * N);
+    c->lin_a = cv.take<float>(3 * N);
+    c->lin_u = cv.take<float>(3 * M);
+    c->boxA = cv.take<float>((size_t)c->nA * 3 * c->bA.box);
+    c->boxB = cv.take<float>((size_t)c->nB * 3 * c->bB.box);
+    c->curv_w = cv.take<float>(3 * M);
+    c->dpart = cv.take<double>(c->nA);
+    c->rpart = cv.take<double>(c->nR);
+    c->vpart = cv.take<double>(c->nB);
+    c->kpart = cv.take<double>(c->nKb);
+    c->vecpart = cv.take<double>(c->nV);
+    c->terms_tmp = cv.take<double>(8);
+    c->dminmax = cv.take<double>(2);
+    c->fold = cv.take<int>(c->nB);
+    c->dmin = cv.take<float>(c->nB);
+    c->dmax = cv.take<float>(c->nB);
+    c->minv = cv.take<float>(3 * M);
+    c->r = cv.take<float>(3 * M);
+    c->z = cv.take<float>(3 * M);
+    c->d = cv.take<float>(3 * M);
+    c->q = cv.take<float>(3 * M);
+    c->tg_ = cv.take<float>(3 * M);
+    c->tu = cv.take<float>(3 * M);
+    c->ts = cv.take<float>(3 * M);
+    c->sc = cv.take<PcgScalars>(1);
+}
+
+static void derive(rg_ctx *c) {
+    c->N = (long)c->img.n[0] * c->img.n[1] * c->img.n[2];
+    c->M = (long)c->grid.m[0] * c->grid.m[1] * c->grid.m[2];
+    for (int a = 0; a < 3; ++a) c->g[a] = c->img.n[a] * c->img.h[a] / (c->grid.m[a] - 1);
+    c->hbar = c->img.h[0] * c->img.h[1] * c->img.h[2];
+    c->ghat = c->g[0] * c->g[1] * c->g[2];
+    tile_geom(&c->img, &c->grid, c->tg);
+    c->nA = c->tg.nb[0] * c->tg.nb[1] * c->tg.nb[2];
+    for (int a = 0; a < 3; ++a) {
+        c->bA.m[a] = c->grid.m[a];
+        c->bA.nb[a] = c->tg.nb[a];
+        c->bA.C[a] = c->tg.C[a];
+        c->bB.m[a] = c->grid.m[a];
+        c->bB.C[a] = kVccTile[a];
+        c->bB.nb[a] = (c->grid.m[a] - 1 + kVccTile[a] - 1) / kVccTile[a];
+    }
+    c->bA.box = c->tg.box;
+    c->bB.box = (kVccTile[0] + 1) * (kVccTile[1] + 1) * (kVccTile[2] + 1);
+    c->nB = c->bB.nb[0] * c->bB.nb[1] * c->bB.nb[2];
+    c->nR = curv_blocks(c->grid.m);
+    c->nKb = kp_blocks(c->nk_max > 0 ? c->nk_max : 1);
+    c->nV = vec_blocks(3 * c->M);
+}
+
+extern "C" int rg_workspace_size(const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype, int32_t nk_max,
+                                 size_t *bytes) {
+    if (check_geom(img, grid) != RG_OK || !bytes || (dtype != RG_F32 && dtype != RG_F16) || nk_max < 0)
+        return RG_EINVAL;
+    rg_ctx tmp;
+    memset(&tmp, 0, sizeof tmp);
+    tmp.img = *img;
+    tmp.grid = *grid;
+    tmp.nk_max = nk_max;
+    derive(&tmp);
+    Carver cv{nullptr, 0};
+    layout(&tmp, cv);
+    *bytes = (cv.off + 255) & ~(size_t)255;
+    return RG_OK;
+}
+
+extern "C" int rg_ctx_create(rg_ctx **out, const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype,
+                             const rg_params *params, int32_t nk_max, void *ws, size_t ws_bytes, void *stream) {
+    if (!out || !params) return RG_EINVAL;
+    *out = nullptr;
+    size_t need = 0;
+    int st = rg_workspace_size(img, grid, dtype, nk_max, &need);
+    if (st != RG_OK) return st;
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return RG_EINVAL;
+    rg_ctx *c = (rg_ctx *)calloc(1, sizeof(rg_ctx));
+    if (!c) return RG_ENOMEM;
+    c->img = *img;
+    c->grid = *grid;
+    c->dtype = dtype;
+    c->P = *params;
+    c->nk_max = nk_max;
+    c->st = (cudaStream_t)stream;
+    derive(c);
+    Carver cv{(char *)ws, 0};
+    layout(c, cv);
+    c->tg.eta2 = (float)(params->eta * params->eta);
+    c->ev_pool = new std::vector<cudaEvent_t>();
+    c->ev_used = new std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>();
+    *out = c;
+    return RG_OK;
+}
+
+extern "C" int rg_ctx_destroy(rg_ctx *c) {
+    if (!c) return RG_OK;
+    if (c->ev_used) {
+        for (auto &u : *c->ev_used) {
+            cudaEventDestroy(u.second.first);
+            cudaEventDestroy(u.second.second);
+        }
+        delete c->ev_used;
+    }
+    if (c->ev_pool) {
+        for (auto e : *c->ev_pool) cudaEventDestroy(e);
+        delete c->ev_pool;
+    }
+    free(c);
+    return RG_OK;
+}
+
+extern "C" int rg_profile(rg_ctx *c, int32_t enable) {
+    if (!c) return RG_EINVAL;
+    c->prof = enable != 0;
+    return RG_OK;
+}
+
+extern "C" int rg_profile_read(rg_ctx *c, int32_t kernel, double *total_ms, int64_t *launches) {
+    if (!c || !total_ms || !launches) return RG_EINVAL;
+    *total_ms = 0.0;
+    *launches = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> keep;
+    for (auto &u : *c->ev_used) {
+        if (u.first != kernel) {
+            keep.push_back(u);
+            continue;
+        }
+        float ms = 0.f;
+        CK(cudaEventSynchronize(u.second.second));
+        CK(cudaEventElapsedTime(&ms, u.second.first, u.second.second));
+        *total_ms += ms;
+        *launches += 1;
+        c->ev_pool->push_back(u.second.first);
+        c->ev_pool->push_back(u.second.second);
+    }
+    c->ev_used->swap(keep);
+    return RG_OK;
+}
+
+extern "C" int64_t rg_launch_count(void) { return (int64_t)g_launches.load(); }
+
+extern "C" int rg_set_params(rg_ctx *c, const rg_params *p) {
+    if (!c || !p || !(p->eta > 0.0) || p->alpha < 0 || p->gamma < 0 || p->delta < 0 || p->tau < 0)
+        return set_err(c, RG_EINVAL, "rg_set_params: invalid parameters");
+    c->P = *p;
+    c->tg.eta2 = (float)(p->eta * p->eta);
+    c->minv_valid = false;
+    return RG_OK;
+}
+
+extern "C" int rg_get_params(const rg_ctx *c, rg_params *p) {
+    if (!c || !p) return RG_EINVAL;
+    *p = c->P;
+    return RG_OK;
+}
+
+extern "C" int rg_set_stream(rg_ctx *c, void *stream) {
+    if (!c) return RG_EINVAL;
+    c->st = (cudaStream_t)stream;
+    return RG_OK;
+}
+
+extern "C" int rg_set_images(rg_ctx *c, const void *R, const void *T) {
+    if (!c || !R || !T) return set_err(c, RG_EINVAL, "rg_set_images: NULL image");
+    c->R = R;
+    c->T = T;
+    c->has_lin = false;
+    return RG_OK;
+}
+
+extern "C" int rg_set_keypoints(rg_ctx *c, int32_t nk, const float *x, const float *y) {
+    if (!c) return RG_EINVAL;
+    if (nk < 0 || nk > c->nk_max || (nk > 0 && (!x || !y)))
+        return set_err(c, RG_EINVAL, "rg_set_keypoints: nk=%d exceeds nk_max=%d or NULL arrays", nk, c->nk_max);
+    c->nk = nk;
+    c->kx = x;
+    c->ky = y;
+    c->minv_valid = false;
+    return RG_OK;
+}
+
+// ---------------------------------------------------------------- internals
+static int run_tile(rg_ctx *c, int mode, const float *field) {
+    if (!c->R || !c->T) return set_err(c, RG_EINVAL, "images not set");
+    if (c->dtype == RG_F32) {
+        TileArgs<float> a;
+        a.g = c->tg;
+        a.R = (const float *)c->R;
+        a.T = (const float *)c->T;
+        a.u = field;
+        a.lin_dT = c->lin_dT;
+        a.lin_a = c->lin_a;
+        a.st_dT = c->lin_dT;
+        a.st_a = c->lin_a;
+        a.boxes = c->boxA;
+        a.dpart = c->dpart;
+        LAUNCH((mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1))), launch_ngf_tile(mode, a, c->st));
+    } else {
+        TileArgs<__half> a;
+        a.g = c->tg;
+        a.R = (const __half *)c->R;
+        a.T = (const __half *)c->T;
+        a.u = field;
+        a.lin_dT = c->lin_dT;
+        a.lin_a = c->lin_a;
+        a.st_dT = c->lin_dT;
+        a.st_a = c->lin_a;
+        a.boxes = c->boxA;
+        a.dpart = c->dpart;
+        LAUNCH((mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1))), launch_ngf_tile(mode, a, c->st));
+    }
+    return RG_OK;
+}
+
+static int run_vcc(rg_ctx *c, const float *u, const float *v, int diag = 0) {
+    VccArgs a;
+    a.diag = diag;
+    for (int i = 0; i < 3; ++i) {
+        a.m[i] = c->grid.m[i];
+        a.ig[i] = (float)(1.0 / c->g[i]);
+        a.nb[i] = c->bB.nb[i];
+    }
+    a.box = c->bB.box;
+    a.u = u;
+    a.v = v;
+    a.wscale = 1.f;
+    a.boxes = c->boxB;
+    a.epart = c->vpart;
+    a.fold = c->fold;
+    a.dmin = c->dmin;
+    a.dmax = c->dmax;
+    LAUNCH((diag ? 10 : (a.v ? 4 : 3)), launch_vcc(a, c->st));
+    return RG_OK;
+}
+
+static int run_curv(rg_ctx *c, const float *u, bool energy) {
+    CurvArgs a;
+    for (int i = 0; i < 3; ++i) {
+        a.m[i] = c->grid.m[i];
+        a.ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
+    }
+    a.u = u;
+    a.w = c->curv_w;
+    a.part = energy ? c->rpart : nullptr;
+    LAUNCH(5, launch_curv_L(a, c->st));
+    return RG_OK;
+}
+
+static int run_finalize(rg_ctx *c, float *out, double sA, double sB, double sC, bool useA, bool useB, bool useC) {
+    FinalizeArgs f;
+    for (int i = 0; i < 3; ++i) {
+        f.m[i] = c->grid.m[i];
+        f.ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
+    }
+    f.boxA = useA ? c->boxA : nullptr;
+    f.gA = c->bA;
+    f.sA = (float)sA;
+    f.boxB = useB ? c->boxB : nullptr;
+    f.gB = c->bB;
+    f.sB = (float)sB;
+    f.curv_w = useC ? c->curv_w : nullptr;
+    f.sC = (float)sC;
+    f.out = out;
+    LAUNCH(6, launch_finalize(f, c->st));
+    return RG_OK;
+}
+
+static int run_kp(rg_ctx *c, const float *u, const float *v, double scale, float *out, bool energy) {
+    if (c->nk <= 0) return RG_OK;
+    KpArgs k;
+    for (int i = 0; i < 3; ++i) {
+        k.m[i] = c->grid.m[i];
+        k.ig[i] = (float)(1.0 / c->g[i]);
+    }
+    k.nk = c->nk;
+    k.kx = c->kx;
+    k.ky = c->ky;
+    k.u = u;
+    k.v = v;
+    k.scale = (float)scale;
+    k.out = out;
+    k.part = energy ? c->kpart : nullptr;
+    LAUNCH(7, launch_kp(k, c->st));
+    return RG_OK;
+}
+
+static int run_terms(rg_ctx *c, double *terms, bool useD, bool useR, bool useV, bool useK) {
+    TermsArgs t;
+    t.dpart = useD ? c->dpart : nullptr;
+    t.nd = c->nA;
+    t.dscale = c->hbar;
+    t.rpart = useR ? c->rpart : nullptr;
+    t.nr = c->nR;
+    t.rscale = 0.5 * c->ghat;
+    t.vpart = useV ? c->vpart : nullptr;
+    t.nv = c->nB;
+    t.vscale = c->ghat;
+    t.fold = c->fold;
+    t.kpart = (useK && c->nk > 0) ? c->kpart : nullptr;
+    t.nkp = kp_blocks(c->nk);
+    t.alpha = c->P.alpha;
+    t.gamma = c->P.gamma;
+    t.delta = c->P.delta;
+    t.dmin = c->dmin;
+    t.dmax = c->dmax;
+    t.dminmax = c->dminmax;
+    t.terms = terms;
+    LAUNCH(8, launch_terms(t, c->st));
+    return RG_OK;
+}
+
+// Objective (and gradient) of Eq. (11).
+static int evaluate(rg_ctx *c, const float *u, double *terms, float *grad, bool store_lin) {
+    int mode = grad ? (store_lin ? MODE_GRADLIN : MODE_GRAD) : (store_lin ? MODE_LIN : MODE_OBJ);
+    int st;
+    if ((st = run_tile(c, mode, u))) return st;
+    const bool vcc = c->P.gamma != 0.0;
+    if (vcc && (st = run_vcc(c, u, nullptr))) return st;
+    if ((st = run_curv(c, u, true))) return st;
+    if (grad) {
+        if ((st = run_finalize(c, grad, c->hbar, c->P.gamma * c->ghat, c->P.alpha * c->ghat, true, vcc, true)))
+            return st;
+    }
+    if ((st = run_kp(c, u, nullptr, c->P.delta, grad, true))) return st;
+    if ((st = run_terms(c, terms ? terms : c->terms_tmp, true, true, vcc, true))) return st;
+    if (store_lin) {
+        CK(cudaMemcpyAsync(c->lin_u, u, sizeof(float) * 3 * c->M, cudaMemcpyDeviceToDevice, c->st));
+        c->has_lin = true;
+        c->minv_valid = false;
+    }
+    return RG_OK;
+}
+
+extern "C" int ngf_objective(rg_ctx *c, const float *u, double *terms) {
+    if (!c || !u || !terms) return set_err(c, RG_EINVAL, "ngf_objective: NULL argument");
+    return evaluate(c, u, terms, nullptr, false);
+}
+
+extern "C" int ngf_gradient(rg_ctx *c, const float *u, double *terms, float *grad) {
+    if (!c || !u || !grad) return set_err(c, RG_EINVAL, "ngf_gradient: NULL argument");
+    return evaluate(c, u, terms, grad, false);
+}
+
+extern "C" int gn_linearize(rg_ctx *c, const float *u, double *terms, float *grad) {
+    if (!c || !u) return set_err(c, RG_EINVAL, "gn_linearize: NULL argument");
+    return evaluate(c, u, terms, grad, true);
+}
+
+static int matvec(rg_ctx *c, const float *v, float *Hv) {
+    int st;
+    if ((st = run_tile(c, MODE_MATVEC, v))) return st;
+    const bool vcc = c->P.gamma != 0.0;
+    if (vcc && (st = run_vcc(c, c->lin_u, v))) return st;
+    if ((st = run_curv(c, v, false))) return st;
+    if ((st = run_finalize(c, Hv, c->hbar, c->P.gamma * c->ghat, c->P.alpha * c->ghat, true, vcc, true))) return st;
+    if ((st = run_kp(c, c->lin_u, v, c->P.delta, Hv, false))) return st;
+    return RG_OK;
+}
+
+extern "C" int gn_matvec(rg_ctx *c, const float *v, float *Hv) {
+    if (!c || !v || !Hv) return set_err(c, RG_EINVAL, "gn_matvec: NULL argument");
+    if (!c->has_lin) return set_err(c, RG_EINVAL, "gn_matvec: no linearisation (call gn_linearize first)");
+    return matvec(c, v, Hv);
+}
+
+extern "C" int regularizer_apply(rg_ctx *c, int32_t which, const float *u, const float *v, double *energy,
+                                 float *out) {
+    if (!c || !u || !out) return set_err(c, RG_EINVAL, "regularizer_apply: NULL argument");
+    int st;
+    if (which == RG_CURV) {
+        if (v) {
+            if ((st = run_curv(c, u, true))) return st;     // energy at u
+            if (energy && (st = run_terms(c, c->terms_tmp, false, true, false, false))) return st;
+            if ((st = run_curv(c, v, false))) return st;
+        } else {
+            if ((st = run_curv(c, u, true))) return st;
+            if (energy && (st = run_terms(c, c->terms_tmp, false, true, false, false))) return st;
+        }
+        if ((st = run_finalize(c, out, 0, 0, c->ghat, false, false, true))) return st;
+        if (energy) CK(cudaMemcpyAsync(energy, c->terms_tmp + 1, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    } else if (which == RG_VCC) {
+        if (v) {
+            if ((st = run_vcc(c, u, nullptr))) return st;   // energy at u
+            if (energy && (st = run_terms(c, c->terms_tmp, false, false, true, false))) return st;
+            if ((st = run_vcc(c, u, v))) return st;
+        } else {
+            if ((st = run_vcc(c, u, nullptr))) return st;
+            if (energy && (st = run_terms(c, c->terms_tmp, false, false, true, false))) return st;
+        }
+        if ((st = run_finalize(c, out, 0, c->ghat, 0, false, true, false))) return st;
+        if (energy) CK(cudaMemcpyAsync(energy, c->terms_tmp + 2, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    } else if (which == RG_KP) {
+        CK(cudaMemsetAsync(out, 0, sizeof(float) * 3 * c->M, c->st));
+        if (c->nk > 0) {
+            KpArgs k;
+            for (int i = 0; i < 3; ++i) {
+                k.m[i] = c->grid.m[i];
+                k.ig[i] = (float)(1.0 / c->g[i]);
+            }
+            k.nk = c->nk; k.kx = c->kx; k.ky = c->ky; k.u = u; k.v = v; k.scale = 1.f; k.out = out; k.part = c->kpart;
+            LAUNCH(7, launch_kp(k, c->st));
+        }
+        if (energy) {
+            if ((st = run_terms(c, c->terms_tmp, false, false, false, true))) return st;
+            CK(cudaMemcpyAsync(energy, c->terms_tmp + 3, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        }
+    } else {
+        return set_err(c, RG_EINVAL, "regularizer_apply: unknown term %d", which);
+    }
+    return RG_OK;
+}
+
+// Jacobi preconditioner at the stored linearisation: NGF diagonal without
+// the cross terms of the central-difference adjoint, exact curvature, VCC and
+// keypoint diagonals, plus tau; reciprocal stored in minv.
+static int ensure_minv(rg_ctx *c) {
+    if (c->minv_valid) return RG_OK;
+    int st;
+    if ((st = run_tile(c, MODE_DIAG, c->lin_u))) return st;
+    const bool vcc = c->P.gamma != 0.0;
+    if (vcc && (st = run_vcc(c, c->lin_u, nullptr, 1))) return st;
+    if ((st = run_finalize(c, c->minv, 2.0 * c->hbar, c->P.gamma * c->ghat, 0.0, true, vcc, false))) return st;
+    float ig2[3], ig[3];
+    for (int i = 0; i < 3; ++i) {
+        ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
+        ig[i] = (float)(1.0 / c->g[i]);
+    }
+    LAUNCH(10, launch_jacobi_diag(1, c->grid.m, ig2, c->P.alpha * c->ghat, c->P.tau, c->minv, c->st));
+    if (c->nk > 0 && c->P.delta != 0.0)
+        LAUNCH(10, launch_kp_diag(c->grid.m, ig, c->nk, c->kx, 2.0 * c->P.delta, c->minv, c->st));
+    LAUNCH(10, launch_invert(3 * c->M, c->minv, c->st));
+    c->minv_valid = true;
+    return RG_OK;
+}
+
+__global__ void pcg_stats_kernel(const PcgScalars *sc, double *stats) {
+    stats[0] = sc->steps;
+    stats[1] = sc->r0;
+    stats[2] = sc->rend;
+}
+
+static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
+    int st;
+    if ((st = ensure_minv(c))) return st;
+    const long n = 3 * c->M;
+    const int nb = vec_blocks(n);
+    LAUNCH(9, launch_pcg_scalar(5, nullptr, 0, c->sc, c->st));
+    LAUNCH(9, launch_dot(n, g, g, c->vecpart, c->st));
+    LAUNCH(9, launch_pcg_scalar(3, c->vecpart, nb, c->sc, c->st));
+    LAUNCH(9, launch_pcg_init(n, g, c->minv, p, c->r, c->z, c->d, c->vecpart, c->st));
+    LAUNCH(9, launch_pcg_scalar(0, c->vecpart, nb, c->sc, c->st));
+    for (int k = 0; k < iters; ++k) {
+        if ((st = matvec(c, c->d, c->q))) return st;
+        LAUNCH(9, launch_dot(n, c->d, c->q, c->vecpart, c->st));
+        LAUNCH(9, launch_pcg_scalar(1, c->vecpart, nb, c->sc, c->st));
+        LAUNCH(9, launch_pcg_update(n, c->sc, c->d, c->q, c->minv, p, c->r, c->z, c->vecpart, c->st));
+        LAUNCH(9, launch_pcg_scalar(2, c->vecpart, nb, c->sc, c->st));
+        LAUNCH(9, launch_pcg_dir(n, c->sc, c->z, c->d, c->st));
+    }
+    LAUNCH(9, launch_dot(n, c->r, c->r, c->vecpart, c->st));
+    LAUNCH(9, launch_pcg_scalar(4, c->vecpart, nb, c->sc, c->st));
+    if (stats) {
+        ProfScope ps_(c, 9);
+        pcg_stats_kernel<<<1, 1, 0, c->st>>>(c->sc, stats);
+        CK(cudaGetLastError());
+    }
+    return RG_OK;
+}
+
+extern "C" int gn_pcg_solve(rg_ctx *c, const float *g, float *p, int32_t iters, double *stats) {
+    if (!c || !g || !p || iters < 0) return set_err(c, RG_EINVAL, "gn_pcg_solve: bad argument");
+    if (!c->has_lin) return set_err(c, RG_EINVAL, "gn_pcg_solve: no linearisation (call gn_linearize first)");
+    return pcg(c, g, p, iters, stats);
+}
+
+static int read_terms(rg_ctx *c, double *terms_dev, double *host5) {
+    CK(cudaMemcpyAsync(host5, terms_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return RG_OK;
+}
+
+static int set_delta_adaptive(rg_ctx *c, const float *u) {
+    // delta such that D = delta K at the start (Sec. II-D2)
+    int st;
+    double h5[5];
+    rg_params P = c->P;
+    c->P.delta = 1.0;
+    if ((st = evaluate(c, u, c->terms_tmp, nullptr, false))) return st;
+    if ((st = read_terms(c, c->terms_tmp, h5))) return st;
+    P.delta = (c->nk > 0 && h5[3] > 0.0) ? h5[0] / h5[3] : 0.0;
+    c->P = P;
+    c->minv_valid = false;
+    return RG_OK;
+}
+
+static int gn_solve_impl(rg_ctx *c, float *u, const rg_schedule *s, double *report, bool adapt) {
+    int st;
+    if (adapt && (st = set_delta_adaptive(c, u))) return st;
+    const long n = 3 * c->M;
+    double h5[5], slope;
+    for (int it = 0; it < s->gn_iters; ++it) {
+        double *rep = report ? report + 8 * it : nullptr;
+        if ((st = evaluate(c, u, c->terms_tmp, c->tg_, true))) return st;
+        if ((st = read_terms(c, c->terms_tmp, h5))) return st;
+        const double J0 = h5[4];
+        if (!isfinite(J0)) {
+            if (rep) { rep[0] = it; rep[1] = J0; rep[7] = isinf(J0) ? RG_EFOLD : RG_ENONFINITE; }
+            return isinf(J0) ? set_err(c, RG_EFOLD, "gn_solve: fold at the current iterate")
+                             : set_err(c, RG_ENONFINITE, "gn_solve: non-finite objective");
+        }
+        if ((st = pcg(c, c->tg_, c->ts, s->pcg_iters, c->terms_tmp + 5))) return st;
+        // slope g.p, summed on the host in a fixed order from the FP64 partials
+        LAUNCH(9, launch_dot(n, c->tg_, c->ts, c->vecpart, c->st));
+        {
+            const int nbv = vec_blocks(n);
+            double hp[152 * 8], pst[3];
+            CK(cudaMemcpyAsync(hp, c->vecpart, sizeof(double) * nbv, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(pst, c->terms_tmp + 5, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            slope = 0.0;
+            for (int i = 0; i < nbv; ++i) slope += hp[i];
+            if (rep) rep[6] = pst[0];
+        }
+        double t = 1.0, acc_t = 0.0, Jn = J0;
+        int evals = 0;
+        for (int k = 0; k <= s->ls_max; ++k) {
+            LAUNCH(9, launch_axpy_copy(n, (float)t, u, c->ts, c->tu, c->st));
+            if ((st = evaluate(c, c->tu, c->terms_tmp, nullptr, false))) return st;
+            if ((st = read_terms(c, c->terms_tmp, h5))) return st;
+            ++evals;
+            if (isfinite(h5[4]) && h5[4] <= J0 + s->armijo_c * t * slope) {
+                acc_t = t;
+                Jn = h5[4];
+                break;
+            }
+            t *= 0.5;
+        }
+        if (acc_t > 0.0) CK(cudaMemcpyAsync(u, c->tu, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->st));
+        if (rep) {
+            rep[0] = it; rep[1] = J0; rep[2] = slope; rep[3] = acc_t; rep[4] = Jn; rep[5] = evals; rep[7] = 0;
+        }
+    }
+    CK(cudaStreamSynchronize(c->st));
+    return RG_OK;
+}
+
+extern "C" int gn_solve(rg_ctx *c, float *u, const rg_schedule *s, double *report) {
+    if (!c || !u || !s || s->gn_iters < 0 || s->pcg_iters < 0 || s->ls_max < 0)
+        return set_err(c, RG_EINVAL, "gn_solve: bad argument");
+    return gn_solve_impl(c, u, s, report, c->P.delta_adaptive != 0);
+}
+
+// ---------------------------------------------------------------- pyramid
+static void level_geom(const rg_image_geom *img, const rg_grid_geom *fin, int l, rg_image_geom &il, rg_grid_geom &gl) {
+    for (int a = 0; a < 3; ++a) {
+        il.n[a] = img->n[a] >> l;
+        il.h[a] = img->h[a] * (double)(1 << l);
+        gl.m[a] = ((fin->m[a] - 1) >> l) + 1;
+    }
+}
+
+static int pyramid_check(const rg_image_geom *img, const rg_grid_geom *fin, int levels) {
+    if (levels < 1 || levels > 8) return RG_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (img->n[a] % (1 << (levels - 1)) || (fin->m[a] - 1) % (1 << (levels - 1))) return RG_EINVAL;
+    for (int l = 0; l < levels; ++l) {
+        rg_image_geom il;
+        rg_grid_geom gl;
+        level_geom(img, fin, l, il, gl);
+        if (check_geom(&il, &gl) != RG_OK) return RG_EINVAL;
+    }
+    return RG_OK;
+}
+
+extern "C" int rg_pyramid_workspace_size(const rg_image_geom *img, const rg_grid_geom *fin, rg_dtype dtype,
+                                         int32_t levels, int32_t nk_max, size_t *bytes) {
+    if (!bytes || pyramid_check(img, fin, levels) != RG_OK) return RG_EINVAL;
+    size_t total = 0, es = dtype == RG_F16 ? 2 : 4;
+    for (int l = 0; l < levels; ++l) {
+        rg_image_geom il;
+        rg_grid_geom gl;
+        level_geom(img, fin, l, il, gl);
+        size_t w;
+        if (rg_workspace_size(&il, &gl, dtype, nk_max, &w) != RG_OK) return RG_EINVAL;
+        total += w;
+        long N = (long)il.n[0] * il.n[1] * il.n[2], M = (long)gl.m[0] * gl.m[1] * gl.m[2];
+        if (l > 0) total += 2 * ((N * es + 255) & ~(size_t)255);
+        total += (3 * M * sizeof(float) + 255) & ~(size_t)255;
+    }
+    *bytes = total;
+    return RG_OK;
+}
+
+extern "C" int register_pyramid(const rg_image_geom *img, const void *R, const void *T, rg_dtype dtype,
+                                const rg_grid_geom *fin, const rg_params *params, const rg_schedule *s, int32_t nk,
+                                const float *kx, const float *ky, float *u_inout, double *report, void *ws,
+                                size_t ws_bytes, void *stream) {
+    if (!img || !R || !T || !fin || !params || !s || !u_inout || !ws || ((uintptr_t)ws & 255)) return RG_EINVAL;
+    const int levels = s->levels;
+    size_t need;
+    if (rg_pyramid_workspace_size(img, fin, dtype, levels, nk, &need) != RG_OK || ws_bytes < need) return RG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    rg_ctx *c = nullptr;   // for CK in this scope
+    char *base = (char *)ws;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        off = (off + 255) & ~(size_t)255;
+        char *p = base + off;
+        off += b;
+        return (void *)p;
+    };
+    const size_t es = dtype == RG_F16 ? 2 : 4;
+    const void *Rl[8], *Tl[8];
+    float *ul[8];
+    rg_image_geom il[8];
+    rg_grid_geom gl[8];
+    Rl[0] = R;
+    Tl[0] = T;
+    for (int l = 0; l < levels; ++l) {
+        level_geom(img, fin, l, il[l], gl[l]);
+        long N = (long)il[l].n[0] * il[l].n[1] * il[l].n[2], M = (long)gl[l].m[0] * gl[l].m[1] * gl[l].m[2];
+        if (l > 0) {
+            void *r = take(N * es), *t = take(N * es);
+            LAUNCH(10, launch_restrict(il[l - 1].n, dtype == RG_F16, Rl[l - 1], r, st));
+            LAUNCH(10, launch_restrict(il[l - 1].n, dtype == RG_F16, Tl[l - 1], t, st));
+            Rl[l] = r;
+            Tl[l] = t;
+        }
+        ul[l] = (float *)take(3 * M * sizeof(float));
+    }
+    const int Lc = levels - 1;
+    if (Lc == 0) CK(cudaMemcpyAsync(ul[0], u_inout, sizeof(float) * 3 * (long)fin->m[0] * fin->m[1] * fin->m[2],
+                                    cudaMemcpyDeviceToDevice, st));
+    else LAUNCH(10, launch_inject_grid(fin->m, 1 << Lc, u_inout, gl[Lc].m, ul[Lc], st));
+    rg_params P = *params;
+    int status = RG_OK;
+    for (int l = Lc; l >= 0; --l) {
+        size_t w;
+        rg_workspace_size(&il[l], &gl[l], dtype, nk, &w);
+        void *wl = take(w);
+        rg_ctx *cl = nullptr;
+        int e = rg_ctx_create(&cl, &il[l], &gl[l], dtype, &P, nk, wl, w, stream);
+        if (e != RG_OK) return e;
+        rg_set_images(cl, Rl[l], Tl[l]);
+        if (nk > 0) rg_set_keypoints(cl, nk, kx, ky);
+        status = gn_solve_impl(cl, ul[l], s, report ? report + (long)(Lc - l) * s->gn_iters * 8 : nullptr,
+                               P.delta_adaptive != 0 && l == Lc);
+        P.delta = cl->P.delta;
+        rg_ctx_destroy(cl);
+        if (status != RG_OK) return status;
+        if (l > 0) LAUNCH(10, launch_prolong_grid(gl[l].m, ul[l], ul[l - 1], st));
+    }
+    CK(cudaMemcpyAsync(u_inout, ul[0], sizeof(float) * 3 * (long)fin->m[0] * fin->m[1] * fin->m[2],
+                       cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return status;
+}
+
+extern "C" int rg_restrict_image(const int32_t *n, rg_dtype dtype, const void *in, void *out, void *stream) {
+    if (!n || !in || !out || n[0] % 2 || n[1] % 2 || n[2] % 2) return RG_EINVAL;
+    rg_ctx *c = nullptr;
+    LAUNCH(10, launch_restrict(n, dtype == RG_F16, in, out, (cudaStream_t)stream));
+    return RG_OK;
+}
+
+extern "C" int rg_prolong_grid(const int32_t *mc, const float *uc, float *uf, void *stream) {
+    if (!mc || !uc || !uf) return RG_EINVAL;
+    rg_ctx *c = nullptr;
+    LAUNCH(10, launch_prolong_grid(mc, uc, uf, (cudaStream_t)stream));
+    return RG_OK;
+}
+
+extern "C" const char *rg_last_error(const rg_ctx *c) { return c ? c->err : "no context"; }
+
+extern "C" const char *rg_version(void) { return "ngfreg 0.1 (sm_103a)"; }

@@ -1,0 +1,63 @@
+// Shared device helpers and launch descriptors of the ngfreg kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ngf {
+
+constexpr int kThreads = 256;          // threads per CTA of the voxel-tile kernels
+constexpr int kTileX = 32;             // voxels per tile along x (one warp lane per column)
+
+// Image element loads: float32, or IEEE half storing (HU + 1024).  The NGF
+// distance only sees differences, so the offset cancels (Eq. (1)).
+__device__ __forceinline__ float ldimg(const float *p, long i) { return __ldg(p + i); }
+__device__ __forceinline__ float ldimg(const __half *p, long i) { return __half2float(__ldg(p + i)); }
+
+// One interpolation step of the fixed-order FP32 prolongation: w0 * a, then
+// fma(w1, b, .), one rounding each (no contraction of the product).
+__device__ __forceinline__ float lerp_fixed(float a, float b, float w0, float w1) {
+    return __fmaf_rn(w1, b, __fmul_rn(w0, a));
+}
+
+// Voxel-tile kernel geometry (host fills, passed by value).
+struct TileGeom {
+    int n[3];          // voxels
+    int m[3];          // nodes
+    int rho[3];        // n / (m - 1)
+    float invh[3];     // float(1 / h), used for the FP32 cell decision
+    float invh_rel[3]; // 1 - h * float(1 / h): relative error of invh
+    float inv2h[3];    // 1 / (2 h) for central differences
+    float eta2;        // eta^2
+    int TZ;            // voxels per z chunk (multiple of rho[2])
+    int TY;            // voxels per tile along y
+    int nb[3];         // tiles per axis
+    int C[3];          // cells per tile per axis (box = C + 1 nodes)
+    int nxt, nyt;      // node-tile extent loaded for the prolongation
+    int box;           // floats per box per component: (C0+1)(C1+1)(C2+1)
+};
+
+template <typename TImg>
+struct TileArgs {
+    TileGeom g;
+    const TImg *R;          // reference image
+    const TImg *T;          // template image
+    const float *u;         // node field interpolated per voxel (u, or v for the matvec)
+    const float *lin_dT;    // stored dT/dy [3][N] (matvec input)
+    const float *lin_a;     // stored dr/dg [3][N] (matvec input)
+    float *st_dT;           // linearisation output dT/dy [3][N]
+    float *st_a;            // linearisation output dr/dg [3][N]
+    float *boxes;           // per-CTA node partials [cta][3][C2+1][C1+1][C0+1]
+    double *dpart;          // per-CTA partial sums of (1 - r^2)
+};
+
+// Node-box finaliser: out[c][k] = scale * sum over the CTA boxes holding k.
+struct BoxGeom {
+    int m[3];
+    int nb[3];
+    int C[3];
+    int box;
+};
+
+}  // namespace ngf

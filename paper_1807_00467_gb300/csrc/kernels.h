@@ -1,0 +1,108 @@
+// Kernel launchers of the ngfreg library (internal).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ngf {
+
+enum TileMode { MODE_OBJ = 0, MODE_LIN = 1, MODE_GRAD = 2, MODE_GRADLIN = 3, MODE_MATVEC = 4, MODE_DIAG = 5 };
+
+size_t tile_smem_bytes(const TileGeom &g, int mode);
+cudaError_t launch_ngf_tile(int mode, const TileArgs<float> &a, cudaStream_t st);
+cudaError_t launch_ngf_tile(int mode, const TileArgs<__half> &a, cudaStream_t st);
+
+// Curvature, Eq. (5): w = L u on nodes (and per-CTA partial sums of |w|^2).
+struct CurvArgs {
+    int m[3];
+    float ig2[3];          // 1 / g_a^2
+    const float *u;        // [3][M]
+    float *w;              // [3][M]
+    double *part;          // per-CTA partial sums of |L u|^2
+};
+int curv_blocks(const int *m);
+cudaError_t launch_curv_L(const CurvArgs &a, cudaStream_t st);
+
+// Volume change control, Eqs. (7)-(9): per grid cell the 64 bounds d_abc.
+struct VccArgs {
+    int m[3];
+    float ig[3];           // 1 / g_a
+    int nb[3];             // cell tiles per axis
+    int box;               // nodes per box
+    const float *u;        // linearisation point [3][M]
+    const float *v;        // direction for the GN product (NULL: gradient)
+    int diag;              // 1: diagonal of the GN matrix instead
+    float wscale;          // multiplies the node contributions (e.g. gamma * ghat)
+    float *boxes;          // per-CTA node boxes [cta][3][box]
+    double *epart;         // per-CTA partial sums of psi(d)
+    int *fold;             // per-CTA count of d <= 0
+    float *dmin, *dmax;    // per-CTA min / max of d
+};
+constexpr int kVccTile[3] = {8, 8, 4};
+cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st);
+
+// Sum node boxes of up to two box sets and optionally the curvature adjoint.
+struct FinalizeArgs {
+    int m[3];
+    const float *boxA; BoxGeom gA; float sA;   // NGF boxes (scale hbar), may be NULL
+    const float *boxB; BoxGeom gB; float sB;   // VCC boxes (scale gamma ghat), may be NULL
+    const float *curv_w; float ig2[3]; float sC;  // curvature L u, scale alpha ghat, may be NULL
+    float *out;            // [3][M]
+};
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st);
+
+// Keypoint penalty, Eq. (10).
+struct KpArgs {
+    int m[3];
+    float ig[3];           // 1 / g_a
+    int nk;
+    const float *kx, *ky;  // [nk][3]
+    const float *u;        // [3][M]
+    const float *v;        // NULL: gradient 2 P^T res; else 2 P^T P v
+    float scale;           // multiplies the node contributions (delta)
+    float *out;            // accumulated with atomics
+    double *part;          // per-CTA partial sums of |res|^2
+};
+int kp_blocks(int nk);
+cudaError_t launch_kp(const KpArgs &a, cudaStream_t st);
+
+// Objective terms {D, R, V, K, J} from the partial sums.
+struct TermsArgs {
+    const double *dpart; int nd; double dscale;
+    const double *rpart; int nr; double rscale;
+    const double *vpart; int nv; double vscale; const int *fold;
+    const double *kpart; int nkp;
+    double alpha, gamma, delta;
+    const float *dmin, *dmax; double *dminmax;
+    double *terms;         // [5]
+};
+cudaError_t launch_terms(const TermsArgs &a, cudaStream_t st);
+
+// PCG vector kernels (device-resident FP64 scalars).
+struct PcgScalars {
+    double rz, rz_new, pq, alpha, beta, r0, rend;
+    int stop, steps;
+};
+int vec_blocks(long n);
+cudaError_t launch_jacobi_diag(int alpha_on, const int *m, const float *ig2, double alpha_ghat, double tau,
+                               float *minv, cudaStream_t st);
+cudaError_t launch_kp_diag(const int *m, const float *ig, int nk, const float *kx, double two_delta, float *diag,
+                           cudaStream_t st);
+cudaError_t launch_invert(long n, float *d, cudaStream_t st);
+cudaError_t launch_pcg_init(long n, const float *g, const float *minv, float *s, float *r, float *z, float *d,
+                            double *part, cudaStream_t st);
+cudaError_t launch_dot(long n, const float *x, const float *y, double *part, cudaStream_t st);
+cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScalars *sc, cudaStream_t st);
+cudaError_t launch_pcg_update(long n, const PcgScalars *sc, const float *d, const float *q, const float *minv,
+                              float *s, float *r, float *z, double *part, cudaStream_t st);
+cudaError_t launch_pcg_dir(long n, const PcgScalars *sc, const float *z, float *d, cudaStream_t st);
+cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, float *y, cudaStream_t st);
+
+// Pyramid.
+cudaError_t launch_restrict(const int *n, bool half, const void *in, void *out, cudaStream_t st);
+cudaError_t launch_prolong_grid(const int *mc, const float *uc, float *uf, cudaStream_t st);
+cudaError_t launch_inject_grid(const int *mf, int step, const float *uf, const int *mc, float *uc, cudaStream_t st);
+
+}  // namespace ngf

@@ -1,0 +1,711 @@
+// Node-grid kernels: curvature (Eq. (5)), volume change control (Eqs. (7)-(9)),
+// keypoint penalty (Eq. (10)), the node-box finaliser, objective terms,
+// PCG vector operations with FP64 reductions, and pyramid transfers.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ngf {
+
+// ------------------------------------------------------------------ reductions
+// Block sum of one double per thread; thread 0 receives the total.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (blockDim.x + 31) / 32; ++i) t += red[i];
+    return t;
+}
+
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// ------------------------------------------------------------------ curvature
+int curv_blocks(const int *m) {
+    long M = (long)m[0] * m[1] * m[2];
+    long b = (M + 4 * 256 - 1) / (4 * 256);
+    return (int)(b < 1 ? 1 : b);
+}
+
+__global__ void curv_L_kernel(const CurvArgs a) {
+    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
+    const long mxy = (long)mx * my, M = mxy * mz;
+    Kahan acc;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < M; k += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(k / mxy), rem = (int)(k - kz * mxy), ky = rem / mx, kx = rem - ky * mx;
+        const bool ix = kx >= 1 && kx <= mx - 2, iy = ky >= 1 && ky <= my - 2, iz = kz >= 1 && kz <= mz - 2;
+        float e = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            const float *u = a.u + c * M;
+            const float u0 = u[k];
+            float s = 0.f;
+            if (ix) s += (u[k + 1] - 2.f * u0 + u[k - 1]) * a.ig2[0];
+            if (iy) s += (u[k + mx] - 2.f * u0 + u[k - mx]) * a.ig2[1];
+            if (iz) s += (u[k + mxy] - 2.f * u0 + u[k - mxy]) * a.ig2[2];
+            a.w[c * M + k] = s;
+            e = fmaf(s, s, e);
+        }
+        acc.add(e);
+    }
+    if (a.part) {
+        double t = block_sum(acc.value());
+        if (threadIdx.x == 0) a.part[blockIdx.x] = t;
+    }
+}
+
+cudaError_t launch_curv_L(const CurvArgs &a, cudaStream_t st) {
+    curv_L_kernel<<<curv_blocks(a.m), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ VCC
+// Edge e of the axis-a edges joins corner offsets o0 -> o1; the two other
+// axes carry (e & 1, e >> 1) in increasing axis order.
+__device__ __forceinline__ int edge_corner(int a, int e, int hi) {
+    int o[3];
+    const int p = e & 1, q = e >> 1;
+    if (a == 0) { o[0] = hi; o[1] = p; o[2] = q; }
+    else if (a == 1) { o[0] = p; o[1] = hi; o[2] = q; }
+    else { o[0] = p; o[1] = q; o[2] = hi; }
+    return o[0] + 2 * o[1] + 4 * o[2];
+}
+
+__device__ __forceinline__ void cross3(const float *a, const float *b, float *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// VM = 0: gradient of sum psi(d) (+ energy, folds, min/max d); VM = 1: GN
+// product sum psi''(d) (grad d . v) grad d; VM = 2: diagonal of the GN matrix
+// sum psi''(d) (d d / d u_{k,c})^2.
+template <int VM>
+__global__ void __launch_bounds__(256) vcc_kernel(const VccArgs a) {
+    constexpr bool GN = VM == 1, DG = VM == 2;
+    constexpr int TX = kVccTile[0], TY = kVccTile[1], TZ = kVccTile[2];
+    constexpr int BX = TX + 1, BY = TY + 1, BZ = TZ + 1, NB = BX * BY * BZ;
+    __shared__ float su[3][NB];
+    __shared__ float sv[GN ? 3 : 1][GN ? NB : 1];
+    __shared__ float scell[TX * TY * TZ][8][3];
+    const int tid = threadIdx.x;
+    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
+    const long mxy = (long)mx * my, M = mxy * mz;
+    const int cx0 = blockIdx.x * TX, cy0 = blockIdx.y * TY, cz0 = blockIdx.z * TZ;
+    for (int i = tid; i < NB; i += 256) {
+        const int lz = i / (BX * BY), r = i - lz * BX * BY, ly = r / BX, lx = r - ly * BX;
+        const int gx = cx0 + lx, gy = cy0 + ly, gz = cz0 + lz;
+        const bool ok = gx < mx && gy < my && gz < mz;
+        const long k = (long)gz * mxy + (long)gy * mx + gx;
+        for (int c = 0; c < 3; ++c) {
+            su[c][i] = ok ? a.u[c * M + k] : 0.f;
+            if (GN) sv[c][i] = ok ? a.v[c * M + k] : 0.f;
+        }
+    }
+    __syncthreads();
+    const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+    const bool valid = cx0 + lx < mx - 1 && cy0 + ly < my - 1 && cz0 + lz < mz - 1;
+    float E[3][4][3], DE[GN ? 3 : 1][4][3], G[3][4][3];
+    int fold = 0;
+    float dmn = 3.4e38f, dmx = -3.4e38f;
+    Kahan en;
+    for (int c = 0; c < 8; ++c)
+        for (int k = 0; k < 3; ++k) scell[tid][c][k] = 0.f;
+    if (valid) {
+        const int base = (lz * BY + ly) * BX + lx;
+        auto corner = [&](int o) { return base + (o & 1) + ((o >> 1) & 1) * BX + (o >> 2) * BX * BY; };
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int n0 = corner(edge_corner(ax, e, 0)), n1 = corner(edge_corner(ax, e, 1));
+                for (int k = 0; k < 3; ++k) {
+                    E[ax][e][k] = (k == ax ? 1.f : 0.f) + (su[k][n1] - su[k][n0]) * a.ig[ax];
+                    if (GN) DE[ax][e][k] = (sv[k][n1] - sv[k][n0]) * a.ig[ax];
+                    G[ax][e][k] = 0.f;
+                }
+            }
+        if (DG) {
+            float acc[8][3];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) acc[o][0] = acc[o][1] = acc[o][2] = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float x23[3];
+                    cross3(E[1][b], E[2][c], x23);
+#pragma unroll
+                    for (int aa = 0; aa < 4; ++aa) {
+                        const float *e1 = E[0][aa];
+                        const float d = e1[0] * x23[0] + e1[1] * x23[1] + e1[2] * x23[2];
+                        if (!(d > 0.f)) continue;
+                        const float rd = __frcp_rn(d);
+                        const float w = 2.f * rd * rd * rd;     // psi''(d)
+                        float x31[3], x12[3];
+                        cross3(E[2][c], e1, x31);
+                        cross3(e1, E[1][b], x12);
+                        const int xo0 = edge_corner(0, aa, 0), xo1 = edge_corner(0, aa, 1);
+                        const int yo0 = edge_corner(1, b, 0), yo1 = edge_corner(1, b, 1);
+                        const int zo0 = edge_corner(2, c, 0), zo1 = edge_corner(2, c, 1);
+#pragma unroll
+                        for (int o = 0; o < 8; ++o) {
+                            const float sx = (o == xo1 ? 1.f : 0.f) - (o == xo0 ? 1.f : 0.f);
+                            const float sy = (o == yo1 ? 1.f : 0.f) - (o == yo0 ? 1.f : 0.f);
+                            const float sz = (o == zo1 ? 1.f : 0.f) - (o == zo0 ? 1.f : 0.f);
+                            if (sx == 0.f && sy == 0.f && sz == 0.f) continue;
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const float gd = sx * a.ig[0] * x23[k] + sy * a.ig[1] * x31[k] + sz * a.ig[2] * x12[k];
+                                acc[o][k] = fmaf(w * gd, gd, acc[o][k]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+            for (int o = 0; o < 8; ++o)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) scell[tid][o][k] = acc[o][k];
+        } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float x23[3], y23[3], W1[3] = {0.f, 0.f, 0.f};
+                cross3(E[1][b], E[2][c], x23);
+                if (GN) {
+                    float p[3], q[3];
+                    cross3(DE[1][b], E[2][c], p);
+                    cross3(E[1][b], DE[2][c], q);
+                    y23[0] = p[0] + q[0]; y23[1] = p[1] + q[1]; y23[2] = p[2] + q[2];
+                }
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa) {
+                    const float *e1 = E[0][aa];
+                    const float d = e1[0] * x23[0] + e1[1] * x23[1] + e1[2] * x23[2];
+                    dmn = fminf(dmn, d);
+                    dmx = fmaxf(dmx, d);
+                    if (!(d > 0.f)) { ++fold; continue; }
+                    const float rd = __frcp_rn(d);
+                    en.add(d - 2.f + rd);                       // psi(d) = (d - 1)^2 / d
+                    float w;
+                    if (GN) {
+                        const float *de1 = DE[0][aa];
+                        const float dd = de1[0] * x23[0] + de1[1] * x23[1] + de1[2] * x23[2] +
+                                         e1[0] * y23[0] + e1[1] * y23[1] + e1[2] * y23[2];
+                        w = 2.f * rd * rd * rd * dd;            // psi''(d) (grad d . v)
+                    } else {
+                        w = 1.f - rd * rd;                      // psi'(d)
+                    }
+                    for (int k = 0; k < 3; ++k) {
+                        G[0][aa][k] = fmaf(w, x23[k], G[0][aa][k]);
+                        W1[k] = fmaf(w, e1[k], W1[k]);
+                    }
+                }
+                float t2[3], t3[3];
+                cross3(E[2][c], W1, t2);   // sum_a w (e3_c x e1_a)
+                cross3(W1, E[1][b], t3);   // sum_a w (e1_a x e2_b)
+                for (int k = 0; k < 3; ++k) {
+                    G[1][b][k] += t2[k];
+                    G[2][c][k] += t3[k];
+                }
+            }
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int o0 = edge_corner(ax, e, 0), o1 = edge_corner(ax, e, 1);
+                for (int k = 0; k < 3; ++k) {
+                    const float gval = G[ax][e][k] * a.ig[ax];
+                    scell[tid][o1][k] += gval;
+                    scell[tid][o0][k] -= gval;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // gather per node of the box from the (up to) 8 cells of this tile
+    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    float *dst = a.boxes + (long)cta * 3 * a.box;
+    for (int i = tid; i < NB; i += 256) {
+        const int bz = i / (BX * BY), r = i - bz * BX * BY, by = r / BX, bx = r - by * BX;
+        float acc[3] = {0.f, 0.f, 0.f};
+        for (int o = 0; o < 8; ++o) {
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+            const int qx = bx - ox, qy = by - oy, qz = bz - oz;
+            if (qx < 0 || qy < 0 || qz < 0 || qx >= TX || qy >= TY || qz >= TZ) continue;
+            const int cell = (qz * TY + qy) * TX + qx;
+            for (int k = 0; k < 3; ++k) acc[k] += scell[cell][o][k];
+        }
+        for (int k = 0; k < 3; ++k) dst[k * a.box + i] = acc[k] * a.wscale;
+    }
+    if (VM == 0) {
+        double t = block_sum(en.value());
+        __shared__ int sfold;
+        __shared__ float smn, smx;
+        if (tid == 0) { sfold = 0; smn = 3.4e38f; smx = -3.4e38f; }
+        __syncthreads();
+        if (fold) atomicAdd(&sfold, fold);
+        // float min/max through the ordered-int trick is not needed: use a warp reduction
+        for (int off = 16; off > 0; off >>= 1) {
+            dmn = fminf(dmn, __shfl_xor_sync(0xffffffffu, dmn, off));
+            dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, off));
+        }
+        __shared__ float wmn[8], wmx[8];
+        if ((tid & 31) == 0) { wmn[tid >> 5] = dmn; wmx[tid >> 5] = dmx; }
+        __syncthreads();
+        if (tid == 0) {
+            float mn = wmn[0], mxv = wmx[0];
+            for (int i = 1; i < 8; ++i) { mn = fminf(mn, wmn[i]); mxv = fmaxf(mxv, wmx[i]); }
+            a.epart[cta] = t;
+            a.fold[cta] = sfold;
+            a.dmin[cta] = mn;
+            a.dmax[cta] = mxv;
+        }
+    }
+}
+
+cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st) {
+    dim3 grid(a.nb[0], a.nb[1], a.nb[2]);
+    if (a.diag) vcc_kernel<2><<<grid, 256, 0, st>>>(a);
+    else if (a.v) vcc_kernel<1><<<grid, 256, 0, st>>>(a);
+    else vcc_kernel<0><<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ finalize
+__device__ __forceinline__ float gather_boxes(const float *boxes, const BoxGeom &b, int comp, int kx, int ky, int kz) {
+    const int k[3] = {kx, ky, kz};
+    int cand[3][2], nc[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        nc[ax] = 0;
+        const int hi = k[ax] / b.C[ax];
+        for (int bb = hi - 1; bb <= hi; ++bb) {
+            const int l = k[ax] - bb * b.C[ax];
+            if (bb >= 0 && bb < b.nb[ax] && l >= 0 && l <= b.C[ax]) cand[ax][nc[ax]++] = bb;
+        }
+    }
+    const int BX = b.C[0] + 1, BY = b.C[1] + 1;
+    float s = 0.f;
+    for (int iz = 0; iz < nc[2]; ++iz)
+        for (int iy = 0; iy < nc[1]; ++iy)
+            for (int ix = 0; ix < nc[0]; ++ix) {
+                const int bx = cand[0][ix], by = cand[1][iy], bz = cand[2][iz];
+                const long cta = ((long)bz * b.nb[1] + by) * b.nb[0] + bx;
+                const int lx = kx - bx * b.C[0], ly = ky - by * b.C[1], lz = kz - bz * b.C[2];
+                s += boxes[(cta * 3 + comp) * b.box + (lz * BY + ly) * BX + lx];
+            }
+    return s;
+}
+
+__global__ void finalize_kernel(const FinalizeArgs a) {
+    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
+    const long mxy = (long)mx * my, M = mxy * mz;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < M; k += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(k / mxy), rem = (int)(k - kz * mxy), ky = rem / mx, kx = rem - ky * mx;
+        for (int c = 0; c < 3; ++c) {
+            float v = 0.f;
+            if (a.boxA) v += a.sA * gather_boxes(a.boxA, a.gA, c, kx, ky, kz);
+            if (a.boxB) v += a.sB * gather_boxes(a.boxB, a.gB, c, kx, ky, kz);
+            if (a.curv_w) {
+                // L^T w: rows of L that reference node k along each axis
+                const float *w = a.curv_w + c * M;
+                const int kk[3] = {kx, ky, kz}, mm[3] = {mx, my, mz};
+                const long st[3] = {1, mx, mxy};
+                float s = 0.f;
+                for (int ax = 0; ax < 3; ++ax) {
+                    const bool in0 = kk[ax] >= 1 && kk[ax] <= mm[ax] - 2;
+                    float t = 0.f;
+                    if (in0) t -= 2.f * w[k];
+                    if (kk[ax] - 1 >= 1) t += w[k - st[ax]];
+                    if (kk[ax] + 1 <= mm[ax] - 2) t += w[k + st[ax]];
+                    s = fmaf(t, a.ig2[ax], s);
+                }
+                v = fmaf(a.sC, s, v);
+            }
+            a.out[c * M + k] = v;
+        }
+    }
+}
+
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st) {
+    long M = (long)a.m[0] * a.m[1] * a.m[2];
+    int blocks = (int)((M + 255) / 256);
+    finalize_kernel<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ keypoints
+int kp_blocks(int nk) { return nk <= 0 ? 1 : (nk + 255) / 256; }
+
+__global__ void kp_kernel(const KpArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
+    const long mxy = (long)mx * my, M = mxy * mz;
+    float e = 0.f;
+    if (i < a.nk) {
+        int c[3];
+        float f[3];
+        const int mm[3] = {mx, my, mz};
+        for (int ax = 0; ax < 3; ++ax) {
+            const float t = a.kx[3 * i + ax] * a.ig[ax];
+            int ci = (int)floorf(t);
+            ci = max(0, min(ci, mm[ax] - 2));
+            c[ax] = ci;
+            f[ax] = t - ci;
+        }
+        const long base = (long)c[2] * mxy + (long)c[1] * mx + c[0];
+        float w[8];
+        long nd[8];
+        for (int o = 0; o < 8; ++o) {
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+            w[o] = (ox ? f[0] : 1.f - f[0]) * (oy ? f[1] : 1.f - f[1]) * (oz ? f[2] : 1.f - f[2]);
+            nd[o] = base + ox + oy * mx + oz * mxy;
+        }
+        float src[3];
+        for (int k = 0; k < 3; ++k) {
+            float pu = 0.f, pv = 0.f;
+            for (int o = 0; o < 8; ++o) {
+                pu = fmaf(w[o], a.u[k * M + nd[o]], pu);
+                if (a.v) pv = fmaf(w[o], a.v[k * M + nd[o]], pv);
+            }
+            const float res = a.kx[3 * i + k] + pu - a.ky[3 * i + k];
+            e = fmaf(res, res, e);
+            src[k] = a.v ? pv : res;
+        }
+        if (a.out)
+            for (int o = 0; o < 8; ++o)
+                for (int k = 0; k < 3; ++k) atomicAdd(a.out + k * M + nd[o], 2.f * a.scale * w[o] * src[k]);
+    }
+    if (a.part) {
+        double t = block_sum((double)e);
+        if (threadIdx.x == 0) a.part[blockIdx.x] = t;
+    }
+}
+
+cudaError_t launch_kp(const KpArgs &a, cudaStream_t st) {
+    kp_kernel<<<kp_blocks(a.nk), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ terms
+__device__ double sum_parts(const double *p, int n) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+    return block_sum(s);
+}
+
+__global__ void terms_kernel(const TermsArgs a) {
+    double D = a.dpart ? sum_parts(a.dpart, a.nd) * a.dscale : 0.0;
+    __syncthreads();
+    double R = a.rpart ? sum_parts(a.rpart, a.nr) * a.rscale : 0.0;
+    __syncthreads();
+    double V = a.vpart ? sum_parts(a.vpart, a.nv) * a.vscale : 0.0;
+    __syncthreads();
+    double K = a.kpart ? sum_parts(a.kpart, a.nkp) : 0.0;
+    __syncthreads();
+    __shared__ int sfold;
+    __shared__ float smn, smx;
+    if (threadIdx.x == 0) { sfold = 0; smn = 3.4e38f; smx = -3.4e38f; }
+    __syncthreads();
+    if (a.vpart) {
+        int f = 0;
+        float mn = 3.4e38f, mx = -3.4e38f;
+        for (int i = threadIdx.x; i < a.nv; i += blockDim.x) {
+            f += a.fold[i];
+            mn = fminf(mn, a.dmin[i]);
+            mx = fmaxf(mx, a.dmax[i]);
+        }
+        if (f) atomicAdd(&sfold, f);
+        // min/max via shared atomics on the float bit patterns is avoided: serialise per warp
+        for (int off = 16; off > 0; off >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        }
+        __shared__ float wmn[32], wmx[32];
+        if ((threadIdx.x & 31) == 0) { wmn[threadIdx.x >> 5] = mn; wmx[threadIdx.x >> 5] = mx; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) { smn = fminf(smn, wmn[i]); smx = fmaxf(smx, wmx[i]); }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double J = D + a.alpha * R + a.gamma * V + a.delta * K;
+        if (sfold) { J = INFINITY; V = INFINITY; }
+        a.terms[0] = D; a.terms[1] = R; a.terms[2] = V; a.terms[3] = K; a.terms[4] = J;
+        if (a.dminmax) { a.dminmax[0] = a.vpart ? smn : 1.0; a.dminmax[1] = a.vpart ? smx : 1.0; }
+    }
+}
+
+cudaError_t launch_terms(const TermsArgs &a, cudaStream_t st) {
+    terms_kernel<<<1, 512, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ PCG vectors
+int vec_blocks(long n) {
+    long b = (n + 256 * 8 - 1) / (256 * 8);
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)(b < 1 ? 1 : b);
+}
+
+#define GRID_STRIDE(i, n) for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (n); i += (long)gridDim.x * blockDim.x)
+
+// diag += alpha ghat diag(L^T L) + tau (the curvature part of the
+// preconditioner; L^T L column k: own row and the rows of its neighbours)
+__global__ void jacobi_diag_kernel(int alpha_on, int mx, int my, int mz, float ig2x, float ig2y, float ig2z,
+                                   double alpha_ghat, double tau, float *diag) {
+    const long mxy = (long)mx * my, M = mxy * mz;
+    GRID_STRIDE(k, M) {
+        const int kz = (int)(k / mxy), rem = (int)(k - kz * mxy), ky = rem / mx, kx = rem - ky * mx;
+        const int kk[3] = {kx, ky, kz}, mm[3] = {mx, my, mz};
+        const double ig2[3] = {ig2x, ig2y, ig2z};
+        double own = 0.0, nb = 0.0;
+        for (int ax = 0; ax < 3; ++ax) {
+            if (kk[ax] >= 1 && kk[ax] <= mm[ax] - 2) own -= 2.0 * ig2[ax];
+            if (kk[ax] - 1 >= 1) nb += ig2[ax] * ig2[ax];
+            if (kk[ax] + 1 <= mm[ax] - 2) nb += ig2[ax] * ig2[ax];
+        }
+        const float d = (float)((alpha_on ? alpha_ghat * (own * own + nb) : 0.0) + tau);
+        diag[k] += d; diag[M + k] += d; diag[2 * M + k] += d;
+    }
+}
+
+cudaError_t launch_jacobi_diag(int alpha_on, const int *m, const float *ig2, double alpha_ghat, double tau,
+                               float *diag, cudaStream_t st) {
+    long M = (long)m[0] * m[1] * m[2];
+    jacobi_diag_kernel<<<vec_blocks(M), 256, 0, st>>>(alpha_on, m[0], m[1], m[2], ig2[0], ig2[1], ig2[2], alpha_ghat,
+                                                     tau, diag);
+    return cudaGetLastError();
+}
+
+__global__ void kp_diag_kernel(int mx, int my, int mz, float igx, float igy, float igz, int nk, const float *kx,
+                               double two_delta, float *diag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nk) return;
+    const long mxy = (long)mx * my, M = mxy * mz;
+    const int mm[3] = {mx, my, mz};
+    const float ig[3] = {igx, igy, igz};
+    int c[3];
+    float f[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        const float t = kx[3 * i + ax] * ig[ax];
+        int ci = (int)floorf(t);
+        ci = max(0, min(ci, mm[ax] - 2));
+        c[ax] = ci;
+        f[ax] = t - ci;
+    }
+    for (int o = 0; o < 8; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        const float w = (ox ? f[0] : 1.f - f[0]) * (oy ? f[1] : 1.f - f[1]) * (oz ? f[2] : 1.f - f[2]);
+        const long nd = (long)(c[2] + oz) * mxy + (long)(c[1] + oy) * mx + c[0] + ox;
+        const float add = (float)(two_delta * w * w);
+        for (int k = 0; k < 3; ++k) atomicAdd(diag + k * M + nd, add);
+    }
+}
+
+cudaError_t launch_kp_diag(const int *m, const float *ig, int nk, const float *kx, double two_delta, float *diag,
+                           cudaStream_t st) {
+    if (nk <= 0) return cudaSuccess;
+    kp_diag_kernel<<<(nk + 255) / 256, 256, 0, st>>>(m[0], m[1], m[2], ig[0], ig[1], ig[2], nk, kx, two_delta, diag);
+    return cudaGetLastError();
+}
+
+// reciprocal of the preconditioner diagonal; entries that are not positive
+// (rows without any term) use 1
+__global__ void invert_kernel(long n, float *d) {
+    GRID_STRIDE(i, n) d[i] = d[i] > 0.f ? 1.f / d[i] : 1.f;
+}
+
+cudaError_t launch_invert(long n, float *d, cudaStream_t st) {
+    invert_kernel<<<vec_blocks(n), 256, 0, st>>>(n, d);
+    return cudaGetLastError();
+}
+
+__global__ void pcg_init_kernel(long n, const float *g, const float *minv, float *s, float *r, float *z, float *d,
+                                double *part) {
+    Kahan acc;
+    GRID_STRIDE(i, n) {
+        const float ri = -g[i];
+        const float zi = minv[i] * ri;
+        s[i] = 0.f;
+        r[i] = ri;
+        z[i] = zi;
+        d[i] = zi;
+        acc.add(ri * zi);
+    }
+    double t = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+cudaError_t launch_pcg_init(long n, const float *g, const float *minv, float *s, float *r, float *z, float *d,
+                            double *part, cudaStream_t st) {
+    pcg_init_kernel<<<vec_blocks(n), 256, 0, st>>>(n, g, minv, s, r, z, d, part);
+    return cudaGetLastError();
+}
+
+__global__ void dot_kernel(long n, const float *x, const float *y, double *part) {
+    Kahan acc;
+    GRID_STRIDE(i, n) acc.add(x[i] * y[i]);
+    double t = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+cudaError_t launch_dot(long n, const float *x, const float *y, double *part, cudaStream_t st) {
+    dot_kernel<<<vec_blocks(n), 256, 0, st>>>(n, x, y, part);
+    return cudaGetLastError();
+}
+
+// which: 0 rz = sum (start); 1 pq = sum -> alpha; 2 rz_new = sum -> beta;
+//        3 r0 = sqrt(sum); 4 rend = sqrt(sum); 5 reset (no sum)
+__global__ void pcg_scalar_kernel(int which, const double *part, int nparts, PcgScalars *sc) {
+    double v = 0.0;
+    if (which != 5) v = sum_parts(part, nparts);
+    if (threadIdx.x != 0) return;
+    switch (which) {
+        case 0: sc->rz = v; break;
+        case 1:
+            sc->pq = v;
+            if (sc->stop || !(sc->rz != 0.0) || !(v > 0.0)) { sc->stop = 1; sc->alpha = 0.0; }
+            else sc->alpha = sc->rz / v;
+            break;
+        case 2:
+            sc->rz_new = v;
+            if (sc->stop) { sc->beta = 0.0; }
+            else { sc->beta = v / sc->rz; sc->rz = v; sc->steps += 1; }
+            break;
+        case 3: sc->r0 = sqrt(v); break;
+        case 4: sc->rend = sqrt(v); break;
+        case 5:
+            sc->rz = sc->rz_new = sc->pq = sc->alpha = sc->beta = sc->r0 = sc->rend = 0.0;
+            sc->stop = 0; sc->steps = 0;
+            break;
+    }
+}
+
+cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScalars *sc, cudaStream_t st) {
+    pcg_scalar_kernel<<<1, 256, 0, st>>>(which, part, nparts, sc);
+    return cudaGetLastError();
+}
+
+__global__ void pcg_update_kernel(long n, const PcgScalars *sc, const float *d, const float *q, const float *minv,
+                                  float *s, float *r, float *z, double *part) {
+    const float al = (float)sc->alpha;
+    Kahan acc;
+    GRID_STRIDE(i, n) {
+        const float ri = fmaf(-al, q[i], r[i]);
+        const float zi = minv[i] * ri;
+        s[i] = fmaf(al, d[i], s[i]);
+        r[i] = ri;
+        z[i] = zi;
+        acc.add(ri * zi);
+    }
+    double t = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+cudaError_t launch_pcg_update(long n, const PcgScalars *sc, const float *d, const float *q, const float *minv, float *s,
+                              float *r, float *z, double *part, cudaStream_t st) {
+    pcg_update_kernel<<<vec_blocks(n), 256, 0, st>>>(n, sc, d, q, minv, s, r, z, part);
+    return cudaGetLastError();
+}
+
+__global__ void pcg_dir_kernel(long n, const PcgScalars *sc, const float *z, float *d) {
+    const float be = (float)sc->beta;
+    GRID_STRIDE(i, n) d[i] = fmaf(be, d[i], z[i]);
+}
+
+cudaError_t launch_pcg_dir(long n, const PcgScalars *sc, const float *z, float *d, cudaStream_t st) {
+    pcg_dir_kernel<<<vec_blocks(n), 256, 0, st>>>(n, sc, z, d);
+    return cudaGetLastError();
+}
+
+__global__ void axpy_copy_kernel(long n, float t, const float *x, const float *p, float *y) {
+    GRID_STRIDE(i, n) y[i] = fmaf(t, p[i], x[i]);
+}
+
+cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, float *y, cudaStream_t st) {
+    axpy_copy_kernel<<<vec_blocks(n), 256, 0, st>>>(n, t, x, p, y);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pyramid
+template <typename TImg>
+__global__ void restrict_kernel(int nx, int ny, int nz, const TImg *in, TImg *out) {
+    const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+    const long N = (long)cx * cy * cz;
+    GRID_STRIDE(i, N) {
+        const int jz = (int)(i / ((long)cx * cy)), rem = (int)(i - (long)jz * cx * cy), jy = rem / cx, jx = rem - jy * cx;
+        float s = 0.f;
+        for (int o = 0; o < 8; ++o) {
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+            s += ldimg(in, ((long)(2 * jz + oz) * ny + (2 * jy + oy)) * nx + 2 * jx + ox);
+        }
+        s *= 0.125f;
+        if constexpr (sizeof(TImg) == 2) out[i] = __float2half_rn(s);
+        else out[i] = s;
+    }
+}
+
+cudaError_t launch_restrict(const int *n, bool half, const void *in, void *out, cudaStream_t st) {
+    long N = (long)(n[0] / 2) * (n[1] / 2) * (n[2] / 2);
+    if (half)
+        restrict_kernel<__half><<<vec_blocks(N), 256, 0, st>>>(n[0], n[1], n[2], (const __half *)in, (__half *)out);
+    else
+        restrict_kernel<float><<<vec_blocks(N), 256, 0, st>>>(n[0], n[1], n[2], (const float *)in, (float *)out);
+    return cudaGetLastError();
+}
+
+__global__ void prolong_grid_kernel(int cx, int cy, int cz, const float *uc, float *uf) {
+    const int fx = 2 * cx - 1, fy = 2 * cy - 1, fz = 2 * cz - 1;
+    const long Mf = (long)fx * fy * fz, Mc = (long)cx * cy * cz;
+    GRID_STRIDE(k, Mf) {
+        const int kz = (int)(k / ((long)fx * fy)), rem = (int)(k - (long)kz * fx * fy), ky = rem / fx, kx = rem - ky * fx;
+        const int lo[3] = {kx / 2, ky / 2, kz / 2}, hi[3] = {(kx + 1) / 2, (ky + 1) / 2, (kz + 1) / 2};
+        for (int c = 0; c < 3; ++c) {
+            float s = 0.f;
+            for (int o = 0; o < 8; ++o) {
+                const int x = (o & 1) ? hi[0] : lo[0], y = ((o >> 1) & 1) ? hi[1] : lo[1], z = (o >> 2) ? hi[2] : lo[2];
+                s += uc[c * Mc + ((long)z * cy + y) * cx + x];
+            }
+            uf[c * Mf + k] = 0.125f * s;
+        }
+    }
+}
+
+cudaError_t launch_prolong_grid(const int *mc, const float *uc, float *uf, cudaStream_t st) {
+    long Mf = (long)(2 * mc[0] - 1) * (2 * mc[1] - 1) * (2 * mc[2] - 1);
+    prolong_grid_kernel<<<vec_blocks(Mf), 256, 0, st>>>(mc[0], mc[1], mc[2], uc, uf);
+    return cudaGetLastError();
+}
+
+__global__ void inject_grid_kernel(int fx, int fy, int fz, int step, const float *uf, int cx, int cy, int cz, float *uc) {
+    const long Mc = (long)cx * cy * cz, Mf = (long)fx * fy * fz;
+    GRID_STRIDE(k, Mc) {
+        const int kz = (int)(k / ((long)cx * cy)), rem = (int)(k - (long)kz * cx * cy), ky = rem / cx, kx = rem - ky * cx;
+        for (int c = 0; c < 3; ++c)
+            uc[c * Mc + k] = uf[c * Mf + ((long)(step * kz) * fy + step * ky) * fx + step * kx];
+    }
+}
+
+cudaError_t launch_inject_grid(const int *mf, int step, const float *uf, const int *mc, float *uc, cudaStream_t st) {
+    long Mc = (long)mc[0] * mc[1] * mc[2];
+    inject_grid_kernel<<<vec_blocks(Mc), 256, 0, st>>>(mf[0], mf[1], mf[2], step, uf, mc[0], mc[1], mc[2], uc);
+    return cudaGetLastError();
+}
+
+}  // namespace ngf

@@ -37,6 +37,9 @@ from one ``SeedSequence(seed)``.
 """
 from __future__ import annotations
 
+import hashlib
+import json
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -207,9 +210,40 @@ def _trilinear_upsample(coarse, src_axes, dst_axes):
     return out
 
 
+_RECIPE_VERSION = 1
+
+
 def make_phantom(n, h, seed, motion="small", amp_range=(5.0, 20.0), n_vessels=30,
                  n_keypoints=0, kp_sigma=1.0, noise_sigma=15.0):
-    """Generate a seeded (R, T) phantom pair; see module docstring for the recipe."""
+    """Generate a seeded (R, T) phantom pair; see module docstring for the recipe.
+
+    If the environment variable NGF_PHANTOM_CACHE names a directory, phantoms
+    are stored there (.npz) and reused by later calls with the same arguments.
+    """
+    cache = os.environ.get("NGF_PHANTOM_CACHE")
+    if cache:
+        key = json.dumps([_RECIPE_VERSION, list(n), list(h), int(seed), motion, list(amp_range), n_vessels,
+                          n_keypoints, kp_sigma, noise_sigma])
+        path = os.path.join(cache, hashlib.sha1(key.encode()).hexdigest()[:16] + ".npz")
+        if os.path.exists(path):
+            z = np.load(path, allow_pickle=False)
+            kx = z["kp_x"] if z["kp_x"].size else None
+            ky = z["kp_y"] if z["kp_y"].size else None
+            return Phantom(R=z["R"], T=z["T"], n=tuple(int(v) for v in n), h=tuple(float(v) for v in h),
+                           amps=z["amps"], centres=z["centres"], kp_x=kx, kp_y=ky, meta=json.loads(str(z["meta"])))
+        ph = _make_phantom(n, h, seed, motion, amp_range, n_vessels, n_keypoints, kp_sigma, noise_sigma)
+        os.makedirs(cache, exist_ok=True)
+        tmp = path + f".{os.getpid()}.npz"
+        empty = np.zeros((0, 3), np.float32)
+        np.savez(tmp, R=ph.R, T=ph.T, amps=ph.amps, centres=ph.centres,
+                 kp_x=ph.kp_x if ph.kp_x is not None else empty, kp_y=ph.kp_y if ph.kp_y is not None else empty,
+                 meta=json.dumps(ph.meta))
+        os.replace(tmp, path)
+        return ph
+    return _make_phantom(n, h, seed, motion, amp_range, n_vessels, n_keypoints, kp_sigma, noise_sigma)
+
+
+def _make_phantom(n, h, seed, motion, amp_range, n_vessels, n_keypoints, kp_sigma, noise_sigma):
     n = tuple(int(v) for v in n)
     h = tuple(float(v) for v in h)
     fov = np.array(n, dtype=np.float64) * np.array(h)
@@ -291,7 +325,7 @@ def make_phantom(n, h, seed, motion="small", amp_range=(5.0, 20.0), n_vessels=30
         kp_x = kx.astype(np.float32)
         kp_y = ky.astype(np.float32)
 
-    meta = dict(seed=int(seed), motion=motion, rescales=rescales, det_range=(dmin, dmax),
+    meta = dict(seed=int(seed), motion=motion, rescales=rescales, det_range=[dmin, dmax],
                 lung="two ellipsoids", n_vessels=n_vessels, noise_sigma=noise_sigma)
     return Phantom(R=np.ascontiguousarray(R), T=np.ascontiguousarray(T), n=n, h=h,
                    amps=amps, centres=centres, kp_x=kp_x, kp_y=kp_y, meta=meta)

