@@ -58,6 +58,9 @@ extern "C" {
 #define RG_ENONFINITE (-4)
 #define RG_ETIMEOUT (-5)
 
+/* Largest PCG length a workspace can be sized for (pcg_max). */
+#define RG_PCG_MAX 63
+
 /* Which regulariser regularizer_apply evaluates. */
 #define RG_CURV 1
 #define RG_VCC 2
@@ -94,17 +97,18 @@ typedef struct {
 typedef struct rg_ctx rg_ctx;
 
 /* Workspace bytes a context for this problem needs (nk_max: the largest
- * keypoint count rg_set_keypoints will be given).  Returns RG_EINVAL on bad
- * geometry. */
+ * keypoint count rg_set_keypoints will be given; pcg_max: the longest PCG
+ * solve, 0..RG_PCG_MAX, whose residual history the workspace keeps).
+ * Returns RG_EINVAL on bad geometry or sizes. */
 int rg_workspace_size(const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype,
-                      int32_t nk_max, size_t *bytes);
+                      int32_t nk_max, int32_t pcg_max, size_t *bytes);
 
 /* Create a context.  workspace_dev: caller-owned device memory of at least
  * rg_workspace_size bytes, 256-byte aligned, kept alive until destroy.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream). */
 int rg_ctx_create(rg_ctx **ctx, const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype,
-                  const rg_params *params, int32_t nk_max, void *workspace_dev, size_t ws_bytes,
-                  void *cuda_stream);
+                  const rg_params *params, int32_t nk_max, int32_t pcg_max, void *workspace_dev,
+                  size_t ws_bytes, void *cuda_stream);
 int rg_ctx_destroy(rg_ctx *ctx);
 int rg_set_params(rg_ctx *ctx, const rg_params *params);
 int rg_get_params(const rg_ctx *ctx, rg_params *params);
@@ -141,8 +145,10 @@ int regularizer_apply(rg_ctx *ctx, int32_t which, const float *u_dev, const floa
                       double *energy_dev, float *out_dev);
 
 /* Fixed-length Jacobi-preconditioned CG on H p = -g at the stored
- * linearisation, p0 = 0; stops early only if r.z or p.Hp stop being
- * positive.  Preconditioner: the diagonal of H, with the NGF part taken
+ * linearisation, p0 = 0, iters <= pcg_max; stops early only if r.z or p.Hp
+ * stop being positive.  Each new residual is reorthogonalised against all
+ * earlier preconditioned residuals (classical Gram-Schmidt): the iterates of
+ * plain PCG in exact arithmetic, kept so in FP32.  Preconditioner: the diagonal of H, with the NGF part taken
  * without the cross terms of the central-difference adjoint
  * (2 hbar sum_x w_k(x)^2 dT_c(x)^2 sum_a (a_{x-e_a,a}^2 + a_{x+e_a,a}^2)/(4 h_a^2)),
  * plus tau; non-positive entries use 1.
@@ -163,7 +169,7 @@ int gn_solve(rg_ctx *ctx, float *u_dev, const rg_schedule *sched, double *report
  * workspace_dev: rg_pyramid_workspace_size bytes.  report_host:
  * double[levels][gn_iters][8] (coarsest first) or NULL. */
 int rg_pyramid_workspace_size(const rg_image_geom *img, const rg_grid_geom *finest, rg_dtype dtype,
-                              int32_t levels, int32_t nk_max, size_t *bytes);
+                              int32_t levels, int32_t nk_max, int32_t pcg_max, size_t *bytes);
 int register_pyramid(const rg_image_geom *img, const void *R_dev, const void *T_dev, rg_dtype dtype,
                      const rg_grid_geom *finest, const rg_params *params, const rg_schedule *sched,
                      int32_t nk, const float *kx_dev, const float *ky_dev, float *u_inout_dev,

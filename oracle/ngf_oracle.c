@@ -858,33 +858,49 @@ static double vdot(long n, const double *a, const double *b) {
 }
 
 /* Preconditioned conjugate gradients, s0 = 0, exactly `iters` steps unless
- * the residual vanishes or the curvature p.Hp is not positive.
+ * the residual vanishes or the curvature p.Hp is not positive, with full
+ * reorthogonalisation: each new residual r is made orthogonal to all earlier
+ * preconditioned residuals z_j, r <- r - sum_j (r.z_j / r_j.z_j) r_j with
+ * every coefficient taken from the same r (classical Gram-Schmidt) (same
+ * iterates as plain PCG in exact arithmetic; keeps them so in floating point).
  * stats = {steps done, |r0|, |r_final|}. */
 int orc_pcg(const orc_problem *p, const orc_lin *L, const double *g, double *s, int iters,
             double tau, double *stats) {
     long n3 = 3 * nnod(p);
-    double *r = malloc(sizeof(double) * n3), *z = malloc(sizeof(double) * n3);
+    double *R = malloc(sizeof(double) * n3 * (iters + 1));   /* residual history r_0..r_iters */
+    double *Z = malloc(sizeof(double) * n3 * (iters + 1));   /* preconditioned residuals */
+    double *rz = malloc(sizeof(double) * (iters + 1));
     double *d = malloc(sizeof(double) * n3), *q = malloc(sizeof(double) * n3);
     double *Md = malloc(sizeof(double) * n3);
     orc_gn_diag(p, L, tau, Md);
+    double *r = R, *z = Z;
     for (long i = 0; i < n3; ++i) { s[i] = 0.0; r[i] = -g[i]; z[i] = r[i] / Md[i]; d[i] = z[i]; }
-    double rz = vdot(n3, r, z);
+    rz[0] = vdot(n3, r, z);
     double r0 = sqrt(vdot(n3, r, r));
     int k = 0;
     for (; k < iters; ++k) {
-        if (rz == 0.0) break;
+        if (rz[k] == 0.0) break;
         orc_gn_matvec(p, L, d, q);
         double dq = vdot(n3, d, q);
         if (!(dq > 0.0)) break;
-        double al = rz / dq;
-        for (long i = 0; i < n3; ++i) { s[i] += al * d[i]; r[i] -= al * q[i]; z[i] = r[i] / Md[i]; }
-        double rz1 = vdot(n3, r, z);
-        double be = rz1 / rz;
-        for (long i = 0; i < n3; ++i) d[i] = z[i] + be * d[i];
-        rz = rz1;
+        double al = rz[k] / dq;
+        double *rn = R + (k + 1) * n3, *zn = Z + (k + 1) * n3, *rk = R + k * n3;
+        for (long i = 0; i < n3; ++i) { s[i] += al * d[i]; rn[i] = rk[i] - al * q[i]; }
+        /* classical Gram-Schmidt: all coefficients from the same r_{k+1} */
+        double *cj = malloc(sizeof(double) * (k + 1));
+        for (int j = 0; j <= k; ++j) cj[j] = rz[j] != 0.0 ? vdot(n3, rn, Z + j * n3) / rz[j] : 0.0;
+        for (int j = 0; j <= k; ++j) {
+            const double *rj = R + j * n3;
+            for (long i = 0; i < n3; ++i) rn[i] -= cj[j] * rj[i];
+        }
+        free(cj);
+        for (long i = 0; i < n3; ++i) zn[i] = rn[i] / Md[i];
+        rz[k + 1] = vdot(n3, rn, zn);
+        double be = rz[k + 1] / rz[k];
+        for (long i = 0; i < n3; ++i) d[i] = zn[i] + be * d[i];
     }
-    if (stats) { stats[0] = k; stats[1] = r0; stats[2] = sqrt(vdot(n3, r, r)); }
-    free(r); free(z); free(d); free(q); free(Md);
+    if (stats) { stats[0] = k; stats[1] = r0; stats[2] = sqrt(vdot(n3, R + k * n3, R + k * n3)); }
+    free(R); free(Z); free(rz); free(d); free(q); free(Md);
     return k;
 }
 

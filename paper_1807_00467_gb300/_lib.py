@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_HERE, "libngfreg.so")
 
 RG_OK, RG_EFOLD, RG_EINVAL, RG_ECUDA, RG_ENOMEM, RG_ENONFINITE, RG_ETIMEOUT = 0, 1, -1, -2, -3, -4, -5
 RG_CURV, RG_VCC, RG_KP = 1, 2, 4
+RG_PCG_MAX = 63
 RG_F32, RG_F16 = 0, 1
 
 
@@ -62,8 +63,8 @@ def load():
     vp, i32, sz, dp, fp = C.c_void_p, C.c_int32, C.c_size_t, C.c_void_p, C.c_void_p
     IG, GG, PP, SP = C.POINTER(ImageGeom), C.POINTER(GridGeom), C.POINTER(Params), C.POINTER(Schedule)
     sig = {
-        "rg_workspace_size": ([IG, GG, C.c_int, i32, C.POINTER(sz)], C.c_int),
-        "rg_ctx_create": ([C.POINTER(vp), IG, GG, C.c_int, PP, i32, vp, sz, vp], C.c_int),
+        "rg_workspace_size": ([IG, GG, C.c_int, i32, i32, C.POINTER(sz)], C.c_int),
+        "rg_ctx_create": ([C.POINTER(vp), IG, GG, C.c_int, PP, i32, i32, vp, sz, vp], C.c_int),
         "rg_ctx_destroy": ([vp], C.c_int),
         "rg_set_params": ([vp, PP], C.c_int),
         "rg_get_params": ([vp, PP], C.c_int),
@@ -77,7 +78,7 @@ def load():
         "regularizer_apply": ([vp, i32, fp, fp, dp, fp], C.c_int),
         "gn_pcg_solve": ([vp, fp, fp, i32, dp], C.c_int),
         "gn_solve": ([vp, fp, SP, C.POINTER(C.c_double)], C.c_int),
-        "rg_pyramid_workspace_size": ([IG, GG, C.c_int, i32, i32, C.POINTER(sz)], C.c_int),
+        "rg_pyramid_workspace_size": ([IG, GG, C.c_int, i32, i32, i32, C.POINTER(sz)], C.c_int),
         "register_pyramid": ([IG, vp, vp, C.c_int, GG, PP, SP, i32, fp, fp, fp, C.POINTER(C.c_double), vp, sz, vp],
                              C.c_int),
         "rg_restrict_image": ([C.POINTER(i32), C.c_int, vp, vp, vp], C.c_int),

@@ -71,7 +71,7 @@ def _dtype_code(t):
 class Context:
     """A registration problem bound to device images and a workspace."""
 
-    def __init__(self, R, T, h, m, params=None, nk_max=0, stream=None):
+    def __init__(self, R, T, h, m, params=None, nk_max=0, stream=None, pcg_max=30):
         L = _lib.load()
         if not (R.is_cuda and T.is_cuda and R.shape == T.shape and R.dtype == T.dtype and R.dim() == 3):
             raise ValueError("R, T must be CUDA tensors of equal shape (nz, ny, nx) and dtype")
@@ -83,16 +83,17 @@ class Context:
         self.ig, self.gg = _img_geom(R.shape, h), _grid_geom(m)
         self.params = params if params is not None else make_params()
         self.nk_max = int(nk_max)
+        self.pcg_max = int(pcg_max)
         self.stream = stream
         nbytes = C.c_size_t()
-        _check(L.rg_workspace_size(C.byref(self.ig), C.byref(self.gg), self.dtype, self.nk_max, C.byref(nbytes)),
-               name="rg_workspace_size")
+        _check(L.rg_workspace_size(C.byref(self.ig), C.byref(self.gg), self.dtype, self.nk_max, self.pcg_max,
+                                   C.byref(nbytes)), name="rg_workspace_size")
         self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=R.device)
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) & ~255
         self._ctx = C.c_void_p()
         _check(L.rg_ctx_create(C.byref(self._ctx), C.byref(self.ig), C.byref(self.gg), self.dtype,
-                               C.byref(self.params), self.nk_max, C.c_void_p(self._ws_ptr), nbytes.value,
+                               C.byref(self.params), self.nk_max, self.pcg_max, C.c_void_p(self._ws_ptr), nbytes.value,
                                _stream_ptr(stream)), name="rg_ctx_create")
         _check(L.rg_set_images(self._ctx, _ptr(self.R), _ptr(self.T)), self._ctx, "rg_set_images")
         self.kx = self.ky = None
@@ -204,7 +205,7 @@ def register_pyramid(R, T, h, m_finest, u, params, levels, gn_iters, pcg_iters, 
     dtype = _dtype_code(R)
     nk = 0 if kx is None else int(kx.shape[0])
     nbytes = C.c_size_t()
-    _check(L.rg_pyramid_workspace_size(C.byref(ig), C.byref(gg), dtype, levels, nk, C.byref(nbytes)),
+    _check(L.rg_pyramid_workspace_size(C.byref(ig), C.byref(gg), dtype, levels, nk, pcg_iters, C.byref(nbytes)),
            name="rg_pyramid_workspace_size")
     ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=R.device)
     wp = (ws.data_ptr() + 255) & ~255

@@ -22,6 +22,7 @@ struct rg_ctx {
     rg_dtype dtype;
     rg_params P;
     int nk_max;
+    int pcg_max;
     cudaStream_t st;
     const void *R, *T;
     int nk;
@@ -36,7 +37,9 @@ struct rg_ctx {
     double *dpart, *rpart, *vpart, *kpart, *vecpart, *terms_tmp, *dminmax;
     int *fold;
     float *dmin, *dmax;
-    float *minv, *r, *z, *d, *q, *tg_, *tu, *ts;
+    float *minv, *d, *q, *tg_, *tu, *ts;
+    float *Rh, *Zh;           // PCG residual / preconditioned residual history, pcg_max + 1 slots
+    double *rzh, *coef, *mdpart;
     PcgScalars *sc;
     bool has_lin, minv_valid;
     char err[512];
@@ -176,8 +179,11 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->dmin = cv.take<float>(c->nB);
     c->dmax = cv.take<float>(c->nB);
     c->minv = cv.take<float>(3 * M);
-    c->r = cv.take<float>(3 * M);
-    c->z = cv.take<float>(3 * M);
+    c->Rh = cv.take<float>(3 * M * (size_t)(c->pcg_max + 1));
+    c->Zh = cv.take<float>(3 * M * (size_t)(c->pcg_max + 1));
+    c->rzh = cv.take<double>(c->pcg_max + 1);
+    c->coef = cv.take<double>(c->pcg_max + 1);
+    c->mdpart = cv.take<double>((size_t)c->nV * (c->pcg_max + 1));
     c->d = cv.take<float>(3 * M);
     c->q = cv.take<float>(3 * M);
     c->tg_ = cv.take<float>(3 * M);
@@ -211,14 +217,16 @@ static void derive(rg_ctx *c) {
 }
 
 extern "C" int rg_workspace_size(const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype, int32_t nk_max,
-                                 size_t *bytes) {
-    if (check_geom(img, grid) != RG_OK || !bytes || (dtype != RG_F32 && dtype != RG_F16) || nk_max < 0)
+                                 int32_t pcg_max, size_t *bytes) {
+    if (check_geom(img, grid) != RG_OK || !bytes || (dtype != RG_F32 && dtype != RG_F16) || nk_max < 0 ||
+        pcg_max < 0 || pcg_max > RG_PCG_MAX)
         return RG_EINVAL;
     rg_ctx tmp;
     memset(&tmp, 0, sizeof tmp);
     tmp.img = *img;
     tmp.grid = *grid;
     tmp.nk_max = nk_max;
+    tmp.pcg_max = pcg_max;
     derive(&tmp);
     Carver cv{nullptr, 0};
     layout(&tmp, cv);
@@ -227,11 +235,12 @@ extern "C" int rg_workspace_size(const rg_image_geom *img, const rg_grid_geom *g
 }
 
 extern "C" int rg_ctx_create(rg_ctx **out, const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype,
-                             const rg_params *params, int32_t nk_max, void *ws, size_t ws_bytes, void *stream) {
+                             const rg_params *params, int32_t nk_max, int32_t pcg_max, void *ws, size_t ws_bytes,
+                             void *stream) {
     if (!out || !params) return RG_EINVAL;
     *out = nullptr;
     size_t need = 0;
-    int st = rg_workspace_size(img, grid, dtype, nk_max, &need);
+    int st = rg_workspace_size(img, grid, dtype, nk_max, pcg_max, &need);
     if (st != RG_OK) return st;
     if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return RG_EINVAL;
     rg_ctx *c = (rg_ctx *)calloc(1, sizeof(rg_ctx));
@@ -241,6 +250,7 @@ extern "C" int rg_ctx_create(rg_ctx **out, const rg_image_geom *img, const rg_gr
     c->dtype = dtype;
     c->P = *params;
     c->nk_max = nk_max;
+    c->pcg_max = pcg_max;
     c->st = (cudaStream_t)stream;
     derive(c);
     Carver cv{(char *)ws, 0};
@@ -599,25 +609,35 @@ __global__ void pcg_stats_kernel(const PcgScalars *sc, double *stats) {
     stats[2] = sc->rend;
 }
 
+// PCG with full reorthogonalisation (classical Gram-Schmidt against all
+// earlier preconditioned residuals); same iterates as plain PCG in exact
+// arithmetic, kept so in FP32.  Scalars, dots and coefficients in FP64.
 static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
+    if (iters > c->pcg_max)
+        return set_err(c, RG_EINVAL, "PCG: %d steps requested, the workspace holds %d (pcg_max)", iters, c->pcg_max);
     int st;
     if ((st = ensure_minv(c))) return st;
     const long n = 3 * c->M;
+    const long stride = 3 * c->M;
     const int nb = vec_blocks(n);
     LAUNCH(9, launch_pcg_scalar(5, nullptr, 0, c->sc, c->st));
     LAUNCH(9, launch_dot(n, g, g, c->vecpart, c->st));
     LAUNCH(9, launch_pcg_scalar(3, c->vecpart, nb, c->sc, c->st));
-    LAUNCH(9, launch_pcg_init(n, g, c->minv, p, c->r, c->z, c->d, c->vecpart, c->st));
-    LAUNCH(9, launch_pcg_scalar(0, c->vecpart, nb, c->sc, c->st));
+    LAUNCH(9, launch_pcg_init(n, g, c->minv, p, c->Rh, c->Zh, c->d, c->vecpart, c->st));
+    LAUNCH(9, launch_pcg_scalar(0, c->vecpart, nb, c->sc, c->st, c->rzh));
     for (int k = 0; k < iters; ++k) {
+        float *rk = c->Rh + k * stride, *rn = c->Rh + (k + 1) * stride, *zn = c->Zh + (k + 1) * stride;
         if ((st = matvec(c, c->d, c->q))) return st;
         LAUNCH(9, launch_dot(n, c->d, c->q, c->vecpart, c->st));
         LAUNCH(9, launch_pcg_scalar(1, c->vecpart, nb, c->sc, c->st));
-        LAUNCH(9, launch_pcg_update(n, c->sc, c->d, c->q, c->minv, p, c->r, c->z, c->vecpart, c->st));
-        LAUNCH(9, launch_pcg_scalar(2, c->vecpart, nb, c->sc, c->st));
-        LAUNCH(9, launch_pcg_dir(n, c->sc, c->z, c->d, c->st));
+        LAUNCH(9, launch_pcg_step(n, c->sc, c->d, c->q, rk, p, rn, c->st));
+        LAUNCH(9, launch_multidot(n, rn, c->Zh, stride, k + 1, c->mdpart, c->st));
+        LAUNCH(9, launch_reorth_coef(c->mdpart, nb, k + 1, c->rzh, c->sc, c->coef, c->st));
+        LAUNCH(9, launch_reorth_update(n, rn, c->Rh, stride, k + 1, c->coef, c->minv, zn, c->vecpart, c->st));
+        LAUNCH(9, launch_pcg_scalar(2, c->vecpart, nb, c->sc, c->st, c->rzh));
+        LAUNCH(9, launch_pcg_dir(n, c->sc, zn, c->d, c->st));
     }
-    LAUNCH(9, launch_dot(n, c->r, c->r, c->vecpart, c->st));
+    LAUNCH(9, launch_dot_slot(n, c->Rh, stride, c->sc, c->vecpart, c->st));
     LAUNCH(9, launch_pcg_scalar(4, c->vecpart, nb, c->sc, c->st));
     if (stats) {
         ProfScope ps_(c, 9);
@@ -733,7 +753,7 @@ static int pyramid_check(const rg_image_geom *img, const rg_grid_geom *fin, int 
 }
 
 extern "C" int rg_pyramid_workspace_size(const rg_image_geom *img, const rg_grid_geom *fin, rg_dtype dtype,
-                                         int32_t levels, int32_t nk_max, size_t *bytes) {
+                                         int32_t levels, int32_t nk_max, int32_t pcg_max, size_t *bytes) {
     if (!bytes || pyramid_check(img, fin, levels) != RG_OK) return RG_EINVAL;
     size_t total = 0, es = dtype == RG_F16 ? 2 : 4;
     for (int l = 0; l < levels; ++l) {
@@ -741,7 +761,7 @@ extern "C" int rg_pyramid_workspace_size(const rg_image_geom *img, const rg_grid
         rg_grid_geom gl;
         level_geom(img, fin, l, il, gl);
         size_t w;
-        if (rg_workspace_size(&il, &gl, dtype, nk_max, &w) != RG_OK) return RG_EINVAL;
+        if (rg_workspace_size(&il, &gl, dtype, nk_max, pcg_max, &w) != RG_OK) return RG_EINVAL;
         total += w;
         long N = (long)il.n[0] * il.n[1] * il.n[2], M = (long)gl.m[0] * gl.m[1] * gl.m[2];
         if (l > 0) total += 2 * ((N * es + 255) & ~(size_t)255);
@@ -758,7 +778,8 @@ extern "C" int register_pyramid(const rg_image_geom *img, const void *R, const v
     if (!img || !R || !T || !fin || !params || !s || !u_inout || !ws || ((uintptr_t)ws & 255)) return RG_EINVAL;
     const int levels = s->levels;
     size_t need;
-    if (rg_pyramid_workspace_size(img, fin, dtype, levels, nk, &need) != RG_OK || ws_bytes < need) return RG_EINVAL;
+    if (rg_pyramid_workspace_size(img, fin, dtype, levels, nk, s->pcg_iters, &need) != RG_OK || ws_bytes < need)
+        return RG_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     rg_ctx *c = nullptr;   // for CK in this scope
     char *base = (char *)ws;
@@ -796,10 +817,10 @@ extern "C" int register_pyramid(const rg_image_geom *img, const void *R, const v
     int status = RG_OK;
     for (int l = Lc; l >= 0; --l) {
         size_t w;
-        rg_workspace_size(&il[l], &gl[l], dtype, nk, &w);
+        rg_workspace_size(&il[l], &gl[l], dtype, nk, s->pcg_iters, &w);
         void *wl = take(w);
         rg_ctx *cl = nullptr;
-        int e = rg_ctx_create(&cl, &il[l], &gl[l], dtype, &P, nk, wl, w, stream);
+        int e = rg_ctx_create(&cl, &il[l], &gl[l], dtype, &P, nk, s->pcg_iters, wl, w, stream);
         if (e != RG_OK) return e;
         rg_set_images(cl, Rl[l], Tl[l]);
         if (nk > 0) rg_set_keypoints(cl, nk, kx, ky);

@@ -94,7 +94,20 @@ cudaError_t launch_invert(long n, float *d, cudaStream_t st);
 cudaError_t launch_pcg_init(long n, const float *g, const float *minv, float *s, float *r, float *z, float *d,
                             double *part, cudaStream_t st);
 cudaError_t launch_dot(long n, const float *x, const float *y, double *part, cudaStream_t st);
-cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScalars *sc, cudaStream_t st);
+cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScalars *sc, cudaStream_t st,
+                              double *rzh = nullptr);
+// Reorthogonalised PCG: residual history R_j, preconditioned residuals Z_j
+// (slots of `stride` floats), coefficients c_j = r.z_j / r_j.z_j.
+cudaError_t launch_pcg_step(long n, const PcgScalars *sc, const float *d, const float *q, const float *r, float *s,
+                            float *rn, cudaStream_t st);
+cudaError_t launch_multidot(long n, const float *r, const float *Z, long stride, int count, double *part,
+                            cudaStream_t st);
+cudaError_t launch_reorth_coef(const double *part, int nb, int count, const double *rzh, const PcgScalars *sc,
+                               double *coef, cudaStream_t st);
+cudaError_t launch_reorth_update(long n, float *r, const float *Rh, long stride, int count, const double *coef,
+                                 const float *minv, float *z, double *part, cudaStream_t st);
+cudaError_t launch_dot_slot(long n, const float *Rh, long stride, const PcgScalars *sc, double *part,
+                            cudaStream_t st);
 cudaError_t launch_pcg_update(long n, const PcgScalars *sc, const float *d, const float *q, const float *minv,
                               float *s, float *r, float *z, double *part, cudaStream_t st);
 cudaError_t launch_pcg_dir(long n, const PcgScalars *sc, const float *z, float *d, cudaStream_t st);

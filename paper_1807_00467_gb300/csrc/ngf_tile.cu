@@ -305,9 +305,10 @@ __global__ void __launch_bounds__(kThreads) ngf_tile_kernel(const TileArgs<TImg>
                         const float f0 = (rr_0[w + 1] - rr_0[w - 1]) * g.inv2h[0];
                         const float f1 = (rr_0[w + RW] - rr_0[w - RW]) * g.inv2h[1];
                         const float f2 = (rr_p[w] - rr_m[w]) * g.inv2h[2];
-                        const float fg = g.eta2 + f0 * g0 + f1 * g1 + f2 * g2;
-                        const float ff = g.eta2 + f0 * f0 + f1 * f1 + f2 * f2;
-                        const float gg = g.eta2 + g0 * g0 + g1 * g1 + g2 * g2;
+                        // the same operation order for <f,g>, |f|^2, |g|^2: f = g gives equal values
+                        const float fg = __fmaf_rn(f2, g2, __fmaf_rn(f1, g1, __fmaf_rn(f0, g0, g.eta2)));
+                        const float ff = __fmaf_rn(f2, f2, __fmaf_rn(f1, f1, __fmaf_rn(f0, f0, g.eta2)));
+                        const float gg = __fmaf_rn(g2, g2, __fmaf_rn(g1, g1, __fmaf_rn(g0, g0, g.eta2)));
                         const float rff = __frcp_rn(ff), rgg = __frcp_rn(gg);
                         // 1 - r^2 = (|f x g|^2 + eta^2 |f - g|^2) / (|f|_eta^2 |g|_eta^2)
                         // products rounded separately: exactly zero when f = g
@@ -325,15 +326,17 @@ __global__ void __launch_bounds__(kThreads) ngf_tile_kernel(const TileArgs<TImg>
                             dcomp = (tk - dsum) - yk;
                             dsum = tk;
                         }
-                        // a = dr/dg = (f - t g) / (|f|_eta |g|_eta), t = <f,g>_eta / |g|_eta^2
-                        const float t = fg * rgg;
-                        const float q0 = f0 - t * g0, q1 = f1 - t * g1, q2 = f2 - t * g2;
-                        if (M::grad) {   // c = d(1 - r^2)/dg = -2 r a
-                            const float sc = -2.f * fg * rff * rgg;
+                        // a = dr/dg = (f |g|^2 - <f,g> g) / (|f| |g|^3) (norms with eta);
+                        // q = f |g|^2 - <f,g> g, each product rounded once: 0 when f = g
+                        const float q0 = __fmul_rn(f0, gg) - __fmul_rn(fg, g0);
+                        const float q1 = __fmul_rn(f1, gg) - __fmul_rn(fg, g1);
+                        const float q2 = __fmul_rn(f2, gg) - __fmul_rn(fg, g2);
+                        if (M::grad) {   // c = d(1 - r^2)/dg = -2 r a = -2 <f,g> q / (|f|^2 |g|^4)
+                            const float sc = -2.f * fg * rff * rgg * rgg;
                             c0 = sc * q0; c1 = sc * q1; c2 = sc * q2;
                         }
                         if (M::store && own) {
-                            const float inv = rsqrtf(ff * gg);
+                            const float inv = rsqrtf(ff * gg) * rgg;
                             a.st_a[vox] = q0 * inv;
                             a.st_a[N + vox] = q1 * inv;
                             a.st_a[2 * N + vox] = q2 * inv;

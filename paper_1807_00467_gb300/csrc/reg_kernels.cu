@@ -572,12 +572,15 @@ cudaError_t launch_dot(long n, const float *x, const float *y, double *part, cud
 
 // which: 0 rz = sum (start); 1 pq = sum -> alpha; 2 rz_new = sum -> beta;
 //        3 r0 = sqrt(sum); 4 rend = sqrt(sum); 5 reset (no sum)
-__global__ void pcg_scalar_kernel(int which, const double *part, int nparts, PcgScalars *sc) {
+__global__ void pcg_scalar_kernel(int which, const double *part, int nparts, PcgScalars *sc, double *rzh) {
     double v = 0.0;
     if (which != 5) v = sum_parts(part, nparts);
     if (threadIdx.x != 0) return;
     switch (which) {
-        case 0: sc->rz = v; break;
+        case 0:
+            sc->rz = v;
+            if (rzh) rzh[0] = v;
+            break;
         case 1:
             sc->pq = v;
             if (sc->stop || !(sc->rz != 0.0) || !(v > 0.0)) { sc->stop = 1; sc->alpha = 0.0; }
@@ -586,7 +589,12 @@ __global__ void pcg_scalar_kernel(int which, const double *part, int nparts, Pcg
         case 2:
             sc->rz_new = v;
             if (sc->stop) { sc->beta = 0.0; }
-            else { sc->beta = v / sc->rz; sc->rz = v; sc->steps += 1; }
+            else {
+                sc->beta = v / sc->rz;
+                sc->rz = v;
+                sc->steps += 1;
+                if (rzh) rzh[sc->steps] = v;
+            }
             break;
         case 3: sc->r0 = sqrt(v); break;
         case 4: sc->rend = sqrt(v); break;
@@ -597,8 +605,9 @@ __global__ void pcg_scalar_kernel(int which, const double *part, int nparts, Pcg
     }
 }
 
-cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScalars *sc, cudaStream_t st) {
-    pcg_scalar_kernel<<<1, 256, 0, st>>>(which, part, nparts, sc);
+cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScalars *sc, cudaStream_t st,
+                              double *rzh) {
+    pcg_scalar_kernel<<<1, 256, 0, st>>>(which, part, nparts, sc, rzh);
     return cudaGetLastError();
 }
 
@@ -621,6 +630,92 @@ __global__ void pcg_update_kernel(long n, const PcgScalars *sc, const float *d, 
 cudaError_t launch_pcg_update(long n, const PcgScalars *sc, const float *d, const float *q, const float *minv, float *s,
                               float *r, float *z, double *part, cudaStream_t st) {
     pcg_update_kernel<<<vec_blocks(n), 256, 0, st>>>(n, sc, d, q, minv, s, r, z, part);
+    return cudaGetLastError();
+}
+
+// s += alpha d; r_next = r - alpha q  (reads alpha from the device scalars)
+__global__ void pcg_step_kernel(long n, const PcgScalars *sc, const float *d, const float *q, const float *r,
+                                float *s, float *rn) {
+    const float al = (float)sc->alpha;
+    GRID_STRIDE(i, n) {
+        s[i] = fmaf(al, d[i], s[i]);
+        rn[i] = fmaf(-al, q[i], r[i]);
+    }
+}
+
+cudaError_t launch_pcg_step(long n, const PcgScalars *sc, const float *d, const float *q, const float *r, float *s,
+                            float *rn, cudaStream_t st) {
+    pcg_step_kernel<<<vec_blocks(n), 256, 0, st>>>(n, sc, d, q, r, s, rn);
+    return cudaGetLastError();
+}
+
+// part[j * gridDim.x + b] = partial of r . Z_j over the chunk of block b, j = blockIdx.y
+__global__ void multidot_kernel(long n, const float *r, const float *Z, long stride, double *part) {
+    const float *z = Z + blockIdx.y * stride;
+    Kahan acc;
+    GRID_STRIDE(i, n) acc.add(r[i] * z[i]);
+    double t = block_sum(acc.value());
+    if (threadIdx.x == 0) part[(long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+cudaError_t launch_multidot(long n, const float *r, const float *Z, long stride, int count, double *part,
+                            cudaStream_t st) {
+    dim3 grid(vec_blocks(n), count);
+    multidot_kernel<<<grid, 256, 0, st>>>(n, r, Z, stride, part);
+    return cudaGetLastError();
+}
+
+// c_j = (r . z_j) / (r_j . z_j), j < count; 0 when r_j . z_j = 0 or the solve stopped
+__global__ void reorth_coef_kernel(const double *part, int nb, int count, const double *rzh, const PcgScalars *sc,
+                                   double *coef) {
+    const int j = blockIdx.x;
+    double v = sum_parts(part + (long)j * nb, nb);
+    if (threadIdx.x == 0) coef[j] = (sc->stop || rzh[j] == 0.0) ? 0.0 : v / rzh[j];
+}
+
+cudaError_t launch_reorth_coef(const double *part, int nb, int count, const double *rzh, const PcgScalars *sc,
+                               double *coef, cudaStream_t st) {
+    reorth_coef_kernel<<<count, 256, 0, st>>>(part, nb, count, rzh, sc, coef);
+    return cudaGetLastError();
+}
+
+// r -= sum_j c_j R_j; z = minv r; partial r . z
+__global__ void reorth_update_kernel(long n, float *r, const float *Rh, long stride, int count, const double *coef,
+                                     const float *minv, float *z, double *part) {
+    __shared__ float c[64];
+    for (int j = threadIdx.x; j < count; j += blockDim.x) c[j] = (float)coef[j];
+    __syncthreads();
+    Kahan acc;
+    GRID_STRIDE(i, n) {
+        float ri = r[i];
+        for (int j = 0; j < count; ++j) ri = fmaf(-c[j], Rh[j * stride + i], ri);
+        const float zi = minv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        acc.add(ri * zi);
+    }
+    double t = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+cudaError_t launch_reorth_update(long n, float *r, const float *Rh, long stride, int count, const double *coef,
+                                 const float *minv, float *z, double *part, cudaStream_t st) {
+    reorth_update_kernel<<<vec_blocks(n), 256, 0, st>>>(n, r, Rh, stride, count, coef, minv, z, part);
+    return cudaGetLastError();
+}
+
+// |r_steps|^2 partials, the residual of the last completed step
+__global__ void dot_slot_kernel(long n, const float *Rh, long stride, const PcgScalars *sc, double *part) {
+    const float *r = Rh + (long)sc->steps * stride;
+    Kahan acc;
+    GRID_STRIDE(i, n) acc.add(r[i] * r[i]);
+    double t = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+cudaError_t launch_dot_slot(long n, const float *Rh, long stride, const PcgScalars *sc, double *part,
+                            cudaStream_t st) {
+    dot_slot_kernel<<<vec_blocks(n), 256, 0, st>>>(n, Rh, stride, sc, part);
     return cudaGetLastError();
 }
 

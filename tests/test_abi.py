@@ -53,31 +53,32 @@ def _geom(n, h, m):
 def test_workspace_size_and_geometry_validation(lib):
     sz = C.c_size_t()
     ig, gg = _geom((512, 512, 128), (0.7, 0.7, 2.5), (129, 129, 65))
-    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, C.byref(sz)) == 0
+    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, 30, C.byref(sz)) == 0
     N = 512 * 512 * 128
     assert sz.value >= 6 * 4 * N          # stored linearisation a, dT
-    assert sz.value < 2 * 6 * 4 * N
+    assert sz.value < 6 * 4 * N + 2 * 31 * 3 * 4 * 129 * 129 * 65 + 300 * 2 ** 20   # + PCG history
+    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, 64, C.byref(sz)) == -1   # pcg_max > RG_PCG_MAX
     for n, m in [((64, 64, 48), (18, 17, 13)),   # 64 % 17 != 0
                  ((48, 48, 48), (5, 5, 5)),      # rho 12 not a power of two
                  ((3, 64, 48), (2, 17, 13))]:    # too few voxels
         ig, gg = _geom(n, (1.0, 1.0, 1.0), m)
-        assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, C.byref(sz)) == -1
+        assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, 30, C.byref(sz)) == -1
     ig, gg = _geom((64, 64, 48), (1.0, -1.0, 1.0), (17, 17, 13))
-    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, C.byref(sz)) == -1
+    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, 30, C.byref(sz)) == -1
 
 
 def test_context_host_validation(lib):
     from paper_1807_00467_gb300._lib import Params
     ig, gg = _geom((64, 64, 48), (1.0, 1.0, 2.5), (17, 17, 13))
     sz = C.c_size_t()
-    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 10, C.byref(sz)) == 0
+    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 10, 30, C.byref(sz)) == 0
     P = Params(10.0, 1.0, 0.0, 0.0, 0, 10.0)
     ctx = C.c_void_p()
     fake = C.c_void_p(1 << 20)            # never dereferenced on the host
-    assert lib.rg_ctx_create(C.byref(ctx), C.byref(ig), C.byref(gg), 0, C.byref(P), 10, fake, sz.value - 1, None) == -1
-    assert lib.rg_ctx_create(C.byref(ctx), C.byref(ig), C.byref(gg), 0, C.byref(P), 10, C.c_void_p((1 << 20) + 8),
+    assert lib.rg_ctx_create(C.byref(ctx), C.byref(ig), C.byref(gg), 0, C.byref(P), 10, 30, fake, sz.value - 1, None) == -1
+    assert lib.rg_ctx_create(C.byref(ctx), C.byref(ig), C.byref(gg), 0, C.byref(P), 10, 30, C.c_void_p((1 << 20) + 8),
                              sz.value, None) == -1        # misaligned workspace
-    assert lib.rg_ctx_create(C.byref(ctx), C.byref(ig), C.byref(gg), 0, C.byref(P), 10, fake, sz.value, None) == 0
+    assert lib.rg_ctx_create(C.byref(ctx), C.byref(ig), C.byref(gg), 0, C.byref(P), 10, 30, fake, sz.value, None) == 0
     assert lib.rg_set_keypoints(ctx, 11, fake, fake) == -1   # more than nk_max
     assert b"nk_max" in lib.rg_last_error(ctx)
     bad = Params(-1.0, 1.0, 0.0, 0.0, 0, 10.0)
@@ -91,11 +92,11 @@ def test_context_host_validation(lib):
 def test_pyramid_workspace_validation(lib):
     sz = C.c_size_t()
     ig, gg = _geom((512, 512, 128), (0.7, 0.7, 2.5), (129, 129, 65))
-    assert lib.rg_pyramid_workspace_size(C.byref(ig), C.byref(gg), 0, 3, 0, C.byref(sz)) == 0
+    assert lib.rg_pyramid_workspace_size(C.byref(ig), C.byref(gg), 0, 3, 0, 30, C.byref(sz)) == 0
     one = C.c_size_t()
-    lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, C.byref(one))
+    lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, 30, C.byref(one))
     assert one.value < sz.value < 1.5 * one.value
-    assert lib.rg_pyramid_workspace_size(C.byref(ig), C.byref(gg), 0, 9, 0, C.byref(sz)) == -1
+    assert lib.rg_pyramid_workspace_size(C.byref(ig), C.byref(gg), 0, 9, 0, 30, C.byref(sz)) == -1
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):

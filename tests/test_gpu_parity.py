@@ -208,7 +208,8 @@ def _replay(ph, m, ctx, u, gn_iters, pcg_iters, steps_checked=None, gamma=0.001)
 
 def test_gn_solve_tiny(tiny):
     """Five Gauss-Newton steps of 30 PCG steps each: every step within 0.01 mm of
-    the oracle's step from the same iterate; J decreases monotonically."""
+    the oracle's step from the same iterate, and the whole trajectory's final
+    displacement within 0.01 mm of the oracle's; J decreases monotonically."""
     import torch
     m = TINY_M
     ctx = gpu_context(tiny, m, gamma=0.001)
@@ -216,27 +217,28 @@ def test_gn_solve_tiny(tiny):
     worst, rep = _replay(tiny, m, ctx, u, 5, 30)
     print(f"tiny GN replay: worst per-step |du| = {worst:.2e} mm")
     assert np.all(rep[:, 4] <= rep[:, 1])
-    # the whole trajectory against the oracle's own trajectory (not gated:
-    # the schedule amplifies 1e-6-level differences)
     P = oracle_problem(tiny, m, gamma=0.001)
     uo, repo, st = P.gn_solve(np.zeros(P.grid_shape), gn_iters=5, pcg_iters=30)
-    print(f"tiny GN trajectory: max |u_gpu - u_oracle| = {np.abs(u.cpu().numpy() - uo).max():.3f} mm, "
-          f"J {rep[-1, 4]:.6e} vs {repo[-1, 4]:.6e}")
-    assert rel(rep[-1, 4], repo[-1, 4]) <= 1e-3
+    d = np.abs(u.cpu().numpy() - uo).max()
+    print(f"tiny GN trajectory: max |u_gpu - u_oracle| = {d:.3e} mm, J {rep[-1, 4]:.6e} vs {repo[-1, 4]:.6e}")
+    np.testing.assert_array_equal(rep[:, 3], repo[:, 3])
+    assert d <= TOL_U
 
 
 def test_pyramid_small():
-    """Two levels, short schedule (2 GN x 5 PCG per level): final u within 0.01 mm."""
+    """Two levels x 2 GN x 10 PCG on a well-conditioned problem (noise-free
+    images, alpha = 10: the oracle's own result moves < 1e-3 mm under 1e-3 HU
+    perturbations), so the whole multilevel trajectory can be compared."""
     import torch
     from paper_1807_00467_gb300 import api
-    ph = small_phantom((64, 64, 32), (1.5, 1.5, 3.0), seed=9)
+    ph = phantom.make_phantom((64, 64, 32), (1.5, 1.5, 3.0), seed=9, motion="small", n_vessels=12, noise_sigma=0.0)
     m = (17, 17, 9)
     R, T = torch.from_numpy(ph.R).cuda(), torch.from_numpy(ph.T).cuda()
     u = torch.zeros((3,) + m[::-1], device="cuda")
-    params = api.make_params(eta=10.0, alpha=1.0, gamma=0.001)
-    code, rep = api.register_pyramid(R, T, ph.h, m, u, params, levels=2, gn_iters=2, pcg_iters=5)
-    P = oracle_problem(ph, m, gamma=0.001)
-    uo, repo, st = P.register_pyramid(np.zeros(P.grid_shape), levels=2, gn_iters=2, pcg_iters=5)
+    params = api.make_params(eta=10.0, alpha=10.0, gamma=0.001)
+    code, rep = api.register_pyramid(R, T, ph.h, m, u, params, levels=2, gn_iters=2, pcg_iters=10)
+    P = oracle_problem(ph, m, alpha=10.0, gamma=0.001)
+    uo, repo, st = P.register_pyramid(np.zeros(P.grid_shape), levels=2, gn_iters=2, pcg_iters=10)
     assert code == 0 and st == 0
     np.testing.assert_array_equal(rep[..., 3], repo[..., 3])
     d = np.abs(u.cpu().numpy() - uo).max()
@@ -259,16 +261,23 @@ def test_restrict_and_prolong_grid_against_oracle():
 
 @pytest.mark.slow
 def test_mid_config_solve():
-    """256x256x64, grid 65x65x33, curvature + VCC, 20 GN x 30 PCG: the oracle
-    repeats steps 0, 1, 5, 10, 19 from the GPU iterate (0.01 mm)."""
+    """256x256x64, grid 65x65x33, curvature + VCC, fixed 20 GN x 30 PCG schedule:
+    final displacement within 0.01 mm of the oracle's; the oracle also repeats
+    steps 0, 10, 19 from the GPU iterate."""
     import torch
     ph = get_phantom("mid", seed=0)
     m = phantom.CONFIGS["mid"]["m"]
     ctx = gpu_context(ph, m, gamma=0.001)
     u = torch.zeros(ctx.grid_shape, device="cuda")
-    worst, rep = _replay(ph, m, ctx, u, 20, 30, steps_checked={0, 1, 5, 10, 19})
-    print(f"mid GN replay: worst per-step |du| = {worst:.2e} mm, J {rep[0, 1]:.6e} -> {rep[-1, 4]:.6e}")
+    worst, rep = _replay(ph, m, ctx, u, 20, 30, steps_checked={0, 10, 19})
+    P = oracle_problem(ph, m, gamma=0.001)
+    uo, repo, st = P.gn_solve(np.zeros(P.grid_shape), gn_iters=20, pcg_iters=30)
+    d = np.abs(u.cpu().numpy() - uo).max()
+    print(f"mid GN: worst per-step |du| = {worst:.2e} mm, final max |u_gpu - u_oracle| = {d:.3e} mm, "
+          f"J {rep[0, 1]:.6e} -> {rep[-1, 4]:.6e} (oracle {repo[-1, 4]:.6e})")
+    assert st == 0
     assert rep[-1, 4] < rep[0, 1]
+    assert d <= TOL_U
 
 
 def test_full_size_objective_gradient_matvec():
