@@ -57,6 +57,7 @@ extern "C" {
 #define RG_ENOMEM (-3)
 #define RG_ENONFINITE (-4)
 #define RG_ETIMEOUT (-5)
+#define RG_ESCRATCH (-6)
 
 /* Largest PCG length a workspace can be sized for (pcg_max). */
 #define RG_PCG_MAX 63
@@ -179,6 +180,26 @@ int register_pyramid(const rg_image_geom *img, const void *R_dev, const void *T_
 int rg_restrict_image(const int32_t *n, rg_dtype dtype, const void *in_dev, void *out_dev, void *cuda_stream);
 /* Dyadic trilinear prolongation of a grid field from mc nodes to mf = 2 mc - 1. */
 int rg_prolong_grid(const int32_t *mc, const float *uc_dev, float *uf_dev, void *cuda_stream);
+
+/* NGF distance D of Eq. (1) at u without any device allocation (the paper
+ * has no counterpart: this serves callers that cannot allocate device
+ * memory, e.g. while a stream is being captured, inside a host application
+ * that owns all device buffers, or under a fixed memory budget).  Images are
+ * float32 [n3][n2][n1]; u is float32 [3][m3][m2][m1]; D_dev receives one
+ * double.  Its only scratch is a file-scope device array of
+ * RG_NOALLOC_MAX_CTAS doubles (512 KB on every GPU that loads the library,
+ * held until the process exits), one partial sum per CTA: problems needing
+ * more CTAs (32 x 16 voxels in x-y times z chunks of up to 32 slices) return
+ * RG_ESCRATCH.  Each call overwrites the partials before reading them.  All
+ * calls share that array, so calls whose kernels overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The first call on each device looks the array's device address up with
+ * cudaGetSymbolAddress on the current device; make that first call before
+ * any stream capture.  Enqueued on cuda_stream; asynchronous. */
+#define RG_NOALLOC_MAX_CTAS 65536
+int ngf_distance_noalloc(const rg_image_geom *img, const rg_grid_geom *grid, const float *R_dev,
+                         const float *T_dev, const float *u_dev, double eta, double *D_dev,
+                         void *cuda_stream);
 
 /* Per-kernel timing with CUDA events recorded on the context stream around
  * every kernel launch while enabled.  Kernel ids: 0 NGF Gauss-Newton product

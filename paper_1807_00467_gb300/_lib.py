@@ -12,6 +12,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libngfreg.so")
 
 RG_OK, RG_EFOLD, RG_EINVAL, RG_ECUDA, RG_ENOMEM, RG_ENONFINITE, RG_ETIMEOUT = 0, 1, -1, -2, -3, -4, -5
+RG_ESCRATCH = -6
+RG_NOALLOC_MAX_CTAS = 65536
 RG_CURV, RG_VCC, RG_KP = 1, 2, 4
 RG_PCG_MAX = 63
 RG_F32, RG_F16 = 0, 1
@@ -40,7 +42,7 @@ EXPORTS = [
     "rg_set_images", "rg_set_keypoints", "ngf_objective", "ngf_gradient", "gn_linearize", "gn_matvec",
     "regularizer_apply", "gn_pcg_solve", "gn_solve", "rg_pyramid_workspace_size", "register_pyramid",
     "rg_restrict_image", "rg_prolong_grid", "rg_last_error", "rg_version", "rg_profile", "rg_profile_read",
-    "rg_launch_count",
+    "rg_launch_count", "ngf_distance_noalloc",
 ]
 
 _lib = None
@@ -86,6 +88,7 @@ def load():
         "rg_profile": ([vp, i32], C.c_int),
         "rg_profile_read": ([vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
         "rg_launch_count": ([], C.c_int64),
+        "ngf_distance_noalloc": ([IG, GG, vp, vp, vp, C.c_double, vp, vp], C.c_int),
         "rg_last_error": ([vp], C.c_char_p),
         "rg_version": ([], C.c_char_p),
     }

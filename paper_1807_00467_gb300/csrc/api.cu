@@ -148,6 +148,14 @@ static void tile_geom(const rg_image_geom *img, const rg_grid_geom *grid, TileGe
     t.nb[2] = (t.n[2] + t.TZ - 1) / t.TZ;
 }
 
+// Tile geometry for callers outside this file (the no-allocation entry point).
+int ngf_host_tile_geom(const rg_image_geom *img, const rg_grid_geom *grid, double eta, TileGeom *t) {
+    if (check_geom(img, grid) != RG_OK || !t) return RG_EINVAL;
+    tile_geom(img, grid, *t);
+    t->eta2 = (float)(eta * eta);
+    return RG_OK;
+}
+
 struct Carver {
     char *base;
     size_t off;
