@@ -115,6 +115,11 @@ int rg_set_params(rg_ctx *ctx, const rg_params *params);
 int rg_get_params(const rg_ctx *ctx, rg_params *params);
 int rg_set_stream(rg_ctx *ctx, void *cuda_stream);
 
+/* Tile height (voxel rows per CTA, 8 or 16; default 16) of the NGF kernels,
+ * for tuning.  The workspace covers both; results do not depend on it beyond
+ * FP32 summation order.  Invalidates the stored preconditioner. */
+int rg_set_tile(rg_ctx *ctx, int32_t tile_y);
+
 /* Borrow the reference R (fixed image F) and template T (moving image M),
  * [n3][n2][n1], float32 for RG_F32, IEEE half of (HU + 1024) for RG_F16.
  * The pointers must stay valid while the context uses them. */

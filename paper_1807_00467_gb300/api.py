@@ -131,6 +131,10 @@ class Context:
         _lib.load().rg_get_params(self._ctx, C.byref(p))
         return p
 
+    def set_tile(self, tile_y):
+        """Tile height (8 or 16 voxel rows) of the NGF kernels (tuning)."""
+        _check(_lib.load().rg_set_tile(self._ctx, int(tile_y)), self._ctx, "rg_set_tile")
+
     def set_keypoints(self, kx, ky):
         kx = kx.contiguous().float()
         ky = ky.contiguous().float()

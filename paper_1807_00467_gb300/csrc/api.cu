@@ -32,6 +32,7 @@ struct rg_ctx {
     TileGeom tg;
     BoxGeom bA, bB;
     int nA, nB, nR, nKb, nV;
+    long nA_cap, boxA_cap;      // NGF tile scratch sized for every supported tile height
     float *lin_dT, *lin_a, *lin_u;
     float *boxA, *boxB, *curv_w;
     double *dpart, *rpart, *vpart, *kpart, *vecpart, *terms_tmp, *dminmax;
@@ -39,6 +40,9 @@ struct rg_ctx {
     float *dmin, *dmax;
     float *minv, *d, *q, *tg_, *tu, *ts;
     float *Rh, *Zh;           // PCG residual / preconditioned residual history, pcg_max + 1 slots
+    int *tma_err;             // set by the kernels if a bounded TMA wait gave up
+    bool err_zeroed;
+    CUtensorMap map_dT, map_a;
     double *rzh, *coef, *mdpart;
     PcgScalars *sc;
     bool has_lin, minv_valid;
@@ -117,35 +121,71 @@ static int check_geom(const rg_image_geom *img, const rg_grid_geom *grid) {
     return RG_OK;
 }
 
-// Tile shape: 32 x TY voxels in x-y, TZ voxels per z chunk.
-static void tile_geom(const rg_image_geom *img, const rg_grid_geom *grid, TileGeom &t) {
+// Tile shape: TXI x TY voxel columns in x-y (one thread per column, plus a
+// 2-voxel halo: TXI + 4 <= 32 lanes), TZ voxel planes per z chunk.
+static void tile_geom(const rg_image_geom *img, const rg_grid_geom *grid, TileGeom &t, int TY = 16) {
     for (int a = 0; a < 3; ++a) {
         t.n[a] = img->n[a];
         t.m[a] = grid->m[a];
         t.rho[a] = img->n[a] / (grid->m[a] - 1);
+        t.lrho[a] = t.rho[a] == 8 ? 3 : t.rho[a] == 4 ? 2 : t.rho[a] == 2 ? 1 : 0;
+        t.irho[a] = 1.0f / (float)t.rho[a];
         t.invh[a] = (float)(1.0 / img->h[a]);
         t.invh_rel[a] = (float)(1.0 - img->h[a] * (double)t.invh[a]);
         t.inv2h[a] = (float)(1.0 / (2.0 * img->h[a]));
     }
-    t.TY = 16;
-    t.nxt = (kTileX + 3) / t.rho[0] + 3;
+    t.TXI = 28 - 28 % t.rho[0];
+    t.TY = TY;
+    // z chunk: 32 voxels, fewer (whole cells) while the per-CTA row sums of all
+    // node planes ((TZ / rho_z + 1) x TY x (TXI / rho_x + 1) x 3 floats, twice) exceed 64 KB
+    t.TZ = 32 - 32 % t.rho[2];
+    while (t.TZ > t.rho[2] &&
+           2L * (t.TZ / t.rho[2] + 1) * t.TY * (t.TXI / t.rho[0] + 1) * 3 * 4 > 64 * 1024)
+        t.TZ -= t.rho[2];
+    t.nxt = (t.TXI + 3) / t.rho[0] + 3;
     t.nyt = (t.TY + 3) / t.rho[1] + 3;
-    t.C[0] = kTileX / t.rho[0];
+    t.C[0] = t.TXI / t.rho[0];
     t.C[1] = t.TY / t.rho[1];
-    t.nb[0] = (t.n[0] + kTileX - 1) / kTileX;
+    t.C[2] = t.TZ / t.rho[2];
+    t.box = (t.C[0] + 1) * (t.C[1] + 1) * (t.C[2] + 1);
+    t.nb[0] = (t.n[0] + t.TXI - 1) / t.TXI;
     t.nb[1] = (t.n[1] + t.TY - 1) / t.TY;
-    // z chunk: 32 voxels, shrunk (in whole cells) while the shared memory of
-    // the gradient kernel would exceed 110 KB (fine grids: large node boxes)
-    int tz = 32 - 32 % t.rho[2];
-    if (tz < t.rho[2]) tz = t.rho[2];
-    for (;;) {
-        t.TZ = tz;
-        t.C[2] = tz / t.rho[2];
-        t.box = (t.C[0] + 1) * (t.C[1] + 1) * (t.C[2] + 1);
-        if (tile_smem_bytes(t, MODE_GRAD) <= 110 * 1024 || tz <= t.rho[2]) break;
-        tz -= t.rho[2];
-    }
     t.nb[2] = (t.n[2] + t.TZ - 1) / t.TZ;
+    t.tma = 0;
+    // node planes of the chunk and its 2-plane halo, preloaded once per CTA if they fit in 48 KB
+    t.nzt = (t.TZ + 3) / t.rho[2] + 3;
+    if ((long)t.nzt * 3 * t.nxt * t.nyt > 12 * 1024) t.nzt = 0;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// TMA maps over a stored [3][n3][n2][n1] float field as the 4-D tensor
+// {x, y, z, component}; box {kTmaBoxX, TY + 4, 1, 3}.  Returns false (and the
+// kernels read with plain loads) when the driver entry point is unavailable or
+// the row pitch is not a multiple of 16 bytes.
+static bool encode_field_map(CUtensorMap *map, const int *n, int TY, float *base) {
+    if (n[0] % 4 != 0 || n[0] < kTmaBoxX || n[1] < TY + 4) return false;
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f) {
+            cudaGetLastError();
+            return false;
+        }
+        fn = (EncodeTiledFn)f;
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2], 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4,
+                                   (cuuint64_t)n[0] * n[1] * n[2] * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)kTmaBoxX, (cuuint32_t)(TY + 4), 1, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
 }
 
 // Tile geometry for callers outside this file (the no-allocation entry point).
@@ -173,10 +213,10 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->lin_dT = cv.take<float>(3 * N);
     c->lin_a = cv.take<float>(3 * N);
     c->lin_u = cv.take<float>(3 * M);
-    c->boxA = cv.take<float>((size_t)c->nA * 3 * c->bA.box);
+    c->boxA = cv.take<float>((size_t)c->boxA_cap);
     c->boxB = cv.take<float>((size_t)c->nB * 3 * c->bB.box);
     c->curv_w = cv.take<float>(3 * M);
-    c->dpart = cv.take<double>(c->nA);
+    c->dpart = cv.take<double>(c->nA_cap);
     c->rpart = cv.take<double>(c->nR);
     c->vpart = cv.take<double>(c->nB);
     c->kpart = cv.take<double>(c->nKb);
@@ -198,6 +238,7 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->tu = cv.take<float>(3 * M);
     c->ts = cv.take<float>(3 * M);
     c->sc = cv.take<PcgScalars>(1);
+    c->tma_err = cv.take<int>(1);
 }
 
 static void derive(rg_ctx *c) {
@@ -206,7 +247,16 @@ static void derive(rg_ctx *c) {
     for (int a = 0; a < 3; ++a) c->g[a] = c->img.n[a] * c->img.h[a] / (c->grid.m[a] - 1);
     c->hbar = c->img.h[0] * c->img.h[1] * c->img.h[2];
     c->ghat = c->g[0] * c->g[1] * c->g[2];
-    tile_geom(&c->img, &c->grid, c->tg);
+    c->nA_cap = 0;
+    c->boxA_cap = 0;
+    for (int ty : {8, 16}) {
+        TileGeom t;
+        tile_geom(&c->img, &c->grid, t, ty);
+        const long n = (long)t.nb[0] * t.nb[1] * t.nb[2];
+        if (n > c->nA_cap) c->nA_cap = n;
+        if (n * 3 * t.box > c->boxA_cap) c->boxA_cap = n * 3 * t.box;
+    }
+    tile_geom(&c->img, &c->grid, c->tg, 16);
     c->nA = c->tg.nb[0] * c->tg.nb[1] * c->tg.nb[2];
     for (int a = 0; a < 3; ++a) {
         c->bA.m[a] = c->grid.m[a];
@@ -264,6 +314,10 @@ extern "C" int rg_ctx_create(rg_ctx **out, const rg_image_geom *img, const rg_gr
     Carver cv{(char *)ws, 0};
     layout(c, cv);
     c->tg.eta2 = (float)(params->eta * params->eta);
+    c->tg.tma = (encode_field_map(&c->map_dT, c->tg.n, c->tg.TY, c->lin_dT) &&
+                 encode_field_map(&c->map_a, c->tg.n, c->tg.TY, c->lin_a))
+                    ? 1
+                    : 0;
     c->ev_pool = new std::vector<cudaEvent_t>();
     c->ev_used = new std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>();
     *out = c;
@@ -338,6 +392,26 @@ extern "C" int rg_set_stream(rg_ctx *c, void *stream) {
     return RG_OK;
 }
 
+extern "C" int rg_set_tile(rg_ctx *c, int32_t tile_y) {
+    if (!c) return RG_EINVAL;
+    if (tile_y != 8 && tile_y != 16) return set_err(c, RG_EINVAL, "rg_set_tile: tile height %d not in {8, 16}", tile_y);
+    const float eta2 = c->tg.eta2;
+    tile_geom(&c->img, &c->grid, c->tg, tile_y);
+    c->tg.eta2 = eta2;
+    c->nA = c->tg.nb[0] * c->tg.nb[1] * c->tg.nb[2];
+    for (int a = 0; a < 3; ++a) {
+        c->bA.nb[a] = c->tg.nb[a];
+        c->bA.C[a] = c->tg.C[a];
+    }
+    c->bA.box = c->tg.box;
+    c->tg.tma = (encode_field_map(&c->map_dT, c->tg.n, c->tg.TY, c->lin_dT) &&
+                 encode_field_map(&c->map_a, c->tg.n, c->tg.TY, c->lin_a))
+                    ? 1
+                    : 0;
+    c->minv_valid = false;
+    return RG_OK;
+}
+
 extern "C" int rg_set_images(rg_ctx *c, const void *R, const void *T) {
     if (!c || !R || !T) return set_err(c, RG_EINVAL, "rg_set_images: NULL image");
     c->R = R;
@@ -360,32 +434,36 @@ extern "C" int rg_set_keypoints(rg_ctx *c, int32_t nk, const float *x, const flo
 // ---------------------------------------------------------------- internals
 static int run_tile(rg_ctx *c, int mode, const float *field) {
     if (!c->R || !c->T) return set_err(c, RG_EINVAL, "images not set");
+    if (!c->err_zeroed) {
+        CK(cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->st));
+        c->err_zeroed = true;
+    }
+    auto fill = [&](auto &a) {
+        a.g = c->tg;
+        a.u = field;
+        a.lin_dT = c->lin_dT;
+        a.lin_a = c->lin_a;
+        a.st_dT = c->lin_dT;
+        a.st_a = c->lin_a;
+        a.boxes = c->boxA;
+        a.dpart = c->dpart;
+        a.map_dT = c->map_dT;
+        a.map_a = c->map_a;
+        a.err = c->tma_err;
+    };
+    const int pid = mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1));
     if (c->dtype == RG_F32) {
         TileArgs<float> a;
-        a.g = c->tg;
+        fill(a);
         a.R = (const float *)c->R;
         a.T = (const float *)c->T;
-        a.u = field;
-        a.lin_dT = c->lin_dT;
-        a.lin_a = c->lin_a;
-        a.st_dT = c->lin_dT;
-        a.st_a = c->lin_a;
-        a.boxes = c->boxA;
-        a.dpart = c->dpart;
-        LAUNCH((mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1))), launch_ngf_tile(mode, a, c->st));
+        LAUNCH(pid, launch_ngf_tile(mode, a, c->st));
     } else {
         TileArgs<__half> a;
-        a.g = c->tg;
+        fill(a);
         a.R = (const __half *)c->R;
         a.T = (const __half *)c->T;
-        a.u = field;
-        a.lin_dT = c->lin_dT;
-        a.lin_a = c->lin_a;
-        a.st_dT = c->lin_dT;
-        a.st_a = c->lin_a;
-        a.boxes = c->boxA;
-        a.dpart = c->dpart;
-        LAUNCH((mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1))), launch_ngf_tile(mode, a, c->st));
+        LAUNCH(pid, launch_ngf_tile(mode, a, c->st));
     }
     return RG_OK;
 }
@@ -662,8 +740,11 @@ extern "C" int gn_pcg_solve(rg_ctx *c, const float *g, float *p, int32_t iters, 
 }
 
 static int read_terms(rg_ctx *c, double *terms_dev, double *host5) {
+    int err = 0;
     CK(cudaMemcpyAsync(host5, terms_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(&err, c->tma_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    if (err) return set_err(c, RG_ETIMEOUT, "a kernel gave up waiting for a TMA transfer");
     return RG_OK;
 }
 

@@ -1,14 +1,13 @@
 // Shared device helpers and launch descriptors of the ngfreg kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace ngf {
 
-constexpr int kThreads = 256;          // threads per CTA of the voxel-tile kernels
-constexpr int kTileX = 32;             // voxels per tile along x (one warp lane per column)
 
 // Image element loads: float32, or IEEE half storing (HU + 1024).  The NGF
 // distance only sees differences, so the offset cancels (Eq. (1)).
@@ -25,17 +24,22 @@ __device__ __forceinline__ float lerp_fixed(float a, float b, float w0, float w1
 struct TileGeom {
     int n[3];          // voxels
     int m[3];          // nodes
-    int rho[3];        // n / (m - 1)
+    int rho[3];        // n / (m - 1), a power of two
+    int lrho[3];       // log2(rho)
+    float irho[3];     // 1 / rho
     float invh[3];     // float(1 / h), used for the FP32 cell decision
     float invh_rel[3]; // 1 - h * float(1 / h): relative error of invh
     float inv2h[3];    // 1 / (2 h) for central differences
     float eta2;        // eta^2
+    int TXI;           // voxels per tile along x (multiple of rho[0]; tile + 2-voxel halo <= 32 lanes)
+    int TY;            // voxels per tile along y (one warp per row, plus 4 halo rows)
     int TZ;            // voxels per z chunk (multiple of rho[2])
-    int TY;            // voxels per tile along y
     int nb[3];         // tiles per axis
     int C[3];          // cells per tile per axis (box = C + 1 nodes)
     int nxt, nyt;      // node-tile extent loaded for the prolongation
+    int nzt;           // node planes preloaded per CTA (0: two planes streamed as needed)
     int box;           // floats per box per component: (C0+1)(C1+1)(C2+1)
+    int tma;           // 1: stream the stored linearisation with TMA (tensor maps valid)
 };
 
 template <typename TImg>
@@ -50,7 +54,15 @@ struct TileArgs {
     float *st_a;            // linearisation output dr/dg [3][N]
     float *boxes;           // per-CTA node partials [cta][3][C2+1][C1+1][C0+1]
     double *dpart;          // per-CTA partial sums of (1 - r^2)
+    // Stored linearisation streamed by TMA (GN product and diagonal): tensor
+    // maps over lin_dT and lin_a as 4-D {x, y, z, component}, box
+    // {kTmaBoxX, TY + 4, 1, 3} starting at (x0 - 4, y0 - 2, plane, 0).
+    CUtensorMap map_dT, map_a;
+    int *err;               // set to 1 if a bounded wait on a TMA barrier gave up
 };
+
+constexpr int kTmaBoxX = 36;      // floats per TMA box row: tile columns x0-4 .. x0+31
+constexpr int kTmaStages = 5;     // planes in flight: 3 ahead of the one being used
 
 // Node-box finaliser: out[c][k] = scale * sum over the CTA boxes holding k.
 struct BoxGeom {

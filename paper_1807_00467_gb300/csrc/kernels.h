@@ -40,7 +40,7 @@ struct VccArgs {
     int *fold;             // per-CTA count of d <= 0
     float *dmin, *dmax;    // per-CTA min / max of d
 };
-constexpr int kVccTile[3] = {8, 8, 4};
+constexpr int kVccTile[3] = {8, 4, 4};
 cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st);
 
 // Sum node boxes of up to two box sets and optionally the curvature adjoint.

@@ -1,26 +1,29 @@
-// Fused voxel-tile kernel for the NGF term of Eq. (1): trilinear warp of the
-// template, central-difference gradients, per-voxel NGF residual, the adjoint
-// of the central difference, and the gather of voxel contributions onto the
-// grid nodes (P^T), in one pass over the volume.
+// Fused voxel-column kernel for the NGF term of Eq. (1): trilinear warp of
+// the template, central-difference gradients, per-voxel NGF residual, the
+// adjoint of the central difference, and the gather of voxel contributions
+// onto the grid nodes (P^T), in one pass over the volume.
 //
-// One CTA owns a tile of 32 x TY voxels in x-y (aligned to grid cells) and a
-// chunk of TZ voxel planes along z, and marches through the chunk plane by
-// plane with three pipelined stages:
-//   W (plane p+2): y = x + P u, sample T(y) and dT/dy           (halo 2 in x-y)
-//   C (plane p+1): f = grad R, g = grad T(y), r, c = d(1-r^2)/dg (halo 1)
-//   A (plane p)  : b = -div-like adjoint of the central difference of c,
-//                  z = b dT/dy, then P^T onto the CTA's node box.
-// Shared-memory rings hold three planes of each stage's output, so every
-// voxel is sampled once per CTA (plus the 2-voxel x-y halo) and R, T are read
-// from HBM once.  Node contributions are reduced along x with warp shuffles
-// (one lane per voxel column), along y through shared memory, and along z
-// into a per-CTA node box in shared memory; boxes of neighbouring CTAs that
-// share boundary nodes are summed by finalize_nodes (gather, no atomics).
+// A CTA owns an x-y tile of TXI x TY voxels (aligned to grid cells) and a
+// chunk of TZ voxel planes.  Each thread owns one voxel column (x, y) of the
+// tile plus a 2-voxel halo (lane = x, warp = y) and marches through the chunk
+// plane by plane with three pipelined stages:
+//   W (plane p+2): y = x + P u, sample T(y) and dT/dy   (all columns)
+//   C (plane p+1): f = grad R, g = grad T(y), r, c = d(1 - r^2)/dg (halo 1)
+//   A (plane p)  : adjoint of the central difference of c, times dT/dy,
+//                  then P^T onto the CTA's nodes (interior columns)
+// z-neighbours stay in the thread's registers (three-plane rings),
+// x-neighbours come from warp shuffles, y-neighbours through a
+// double-buffered shared-memory plane (two barriers per plane).  The P^T
+// gather reduces along x with warp shuffles, along z in registers of one lane
+// per cell, and along y through shared memory once per node plane; each CTA
+// writes its node box once, and boxes of neighbouring CTAs sharing boundary
+// nodes are summed by finalize_nodes (gather, no atomics).
 //
-// The same kernel, with different MODE, evaluates the objective only
-// (line search), stores the Gauss-Newton linearisation, or applies the NGF
-// Gauss-Newton matrix 2 hbar J^T J (stage W then forms dT . P v from the
-// stored dT/dy, stage C forms 2 (a . G(dT . P v)) a from the stored a).
+// MODE selects: the objective only (line search), the stored Gauss-Newton
+// linearisation, the gradient, the NGF Gauss-Newton product 2 hbar J^T J v
+// (stage W forms dT . P v from the stored dT/dy, stage C forms 2 (a . G w) a
+// from the stored a), or the Jacobi diagonal of that product with the
+// cross terms of the central-difference adjoint dropped.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -28,42 +31,47 @@ namespace ngf {
 
 template <int MODE>
 struct Mode {
-    static constexpr bool grad = MODE == MODE_GRAD || MODE == MODE_GRADLIN || MODE == MODE_MATVEC;
+    static constexpr bool adj = MODE == MODE_GRAD || MODE == MODE_GRADLIN || MODE == MODE_MATVEC;
     static constexpr bool store = MODE == MODE_LIN || MODE == MODE_GRADLIN;
     static constexpr bool matvec = MODE == MODE_MATVEC;
     static constexpr bool diag = MODE == MODE_DIAG;
-    static constexpr bool reduce = grad || diag;   // stage A and the node box
-    static constexpr int HW = grad ? 2 : 1;       // halo of stage W
-    static constexpr int HC = HW - 1;             // halo of stage C
+    static constexpr bool warp = !matvec && !diag;   // samples T(y), sums 1 - r^2
+    static constexpr bool reduce = adj || diag;      // P^T onto nodes
+    static constexpr int HZ = adj ? 2 : 1;           // z halo of stage W
+    static constexpr int LAG = adj ? 2 : 1;          // planes between W and A
 };
 
 // Shared-memory carve-up (floats).  Host and device agree on it.
-struct TileSmem {
-    int tw, rr, cr, dtr, nodes, rows, box, total;
+struct ColSmem {
+    int tma, tma_stage, tma_a, ex1, ex2, ex3, nodes, rowA, rowB, total;
 };
 
-__host__ __device__ inline TileSmem tile_smem(const TileGeom &g, int mode) {
-    const bool grad = mode == MODE_GRAD || mode == MODE_GRADLIN || mode == MODE_MATVEC;
-    const bool matvec = mode == MODE_MATVEC, diag = mode == MODE_DIAG, reduce = grad || diag;
-    const int HW = grad ? 2 : 1;
-    TileSmem s;
-    int RW = kTileX + 2 * HW, RH = g.TY + 2 * HW;
-    int CW = kTileX + 2 * (HW - 1), CH = g.TY + 2 * (HW - 1);
+__host__ __device__ inline ColSmem col_smem(const TileGeom &g, int mode) {
+    const bool adj = mode == MODE_GRAD || mode == MODE_GRADLIN || mode == MODE_MATVEC;
+    const bool diag = mode == MODE_DIAG, warpm = !(mode == MODE_MATVEC) && !diag, reduce = adj || diag;
+    const int NW = g.TY + 4;
+    ColSmem s;
     int off = 0;
-    s.tw = off; off += diag ? 0 : 3 * RW * RH;
-    s.rr = off; off += (matvec || diag) ? 0 : 3 * RW * RH;
-    s.cr = off; off += grad ? 9 * CW * CH : (diag ? 9 * RW * RH : 0);
-    s.dtr = off; off += reduce ? 9 * kTileX * g.TY : 0;
-    s.nodes = off; off += diag ? 0 : 2 * 3 * g.nxt * g.nyt;
-    s.rows = off; off += reduce ? 2 * g.TY * g.C[0] * 3 : 0;
-    s.box = off; off += reduce ? 3 * g.box : 0;
+    // TMA stages first (128-byte aligned): per plane a dT box and an a box,
+    // each kTmaBoxX x NW x 3 floats, padded to 128 bytes
+    const int box_f = ((kTmaBoxX * NW * 3 * 4 + 127) / 128) * 32;
+    const bool tma = g.tma && (mode == MODE_MATVEC || diag);
+    s.tma = off;
+    s.tma_a = box_f;
+    s.tma_stage = 2 * box_f;
+    off += tma ? kTmaStages * 2 * box_f + 32 : 0;   // + 128 bytes to align the base
+    s.ex1 = off; off += 2 * NW * 32;                       // W value (diag: a_y^2) at plane C (A)
+    s.ex2 = off; off += warpm ? 2 * NW * 32 : 0;           // R at plane C
+    s.ex3 = off; off += adj ? 2 * NW * 32 : 0;             // c_y at plane A
+    s.nodes = off; off += diag ? 0 : (g.nzt > 0 ? g.nzt : 2) * 3 * g.nxt * g.nyt;
+    // x- and z-reduced row sums of every node plane of the chunk (y-reduced at the end)
+    s.rowA = off; off += reduce ? (g.C[2] + 1) * g.TY * (g.C[0] + 1) * 3 : 0;
+    s.rowB = off; off += reduce ? (g.C[2] + 1) * g.TY * (g.C[0] + 1) * 3 : 0;
     s.total = off;
     return s;
 }
 
-size_t tile_smem_bytes(const TileGeom &g, int mode) { return sizeof(float) * (size_t)tile_smem(g, mode).total; }
-
-__device__ __forceinline__ int ring3(int p) { return (p + 6) % 3; }
+size_t tile_smem_bytes(const TileGeom &g, int mode) { return sizeof(float) * (size_t)col_smem(g, mode).total; }
 
 // Per-axis placement of the template sample from the FP32 cell decision k.
 // The sample is taken from voxel c0 and its neighbour c0 + step at fraction f
@@ -80,380 +88,520 @@ __device__ __forceinline__ void place_axis(int k, float fr, int n, int &c0, int 
     }
 }
 
-template <int TY, int MODE, typename TImg>
-__global__ void __launch_bounds__(kThreads) ngf_tile_kernel(const TileArgs<TImg> a) {
-    using M = Mode<MODE>;
-    constexpr int HW = M::HW, HC = M::HC;
-    constexpr int RW = kTileX + 2 * HW, RH = TY + 2 * HW;
-    constexpr int CW = kTileX + 2 * HC, CH = TY + 2 * HC;
-    constexpr int PPT = (RW * RH + kThreads - 1) / kThreads;   // W-stage points per thread
-    extern __shared__ float smem[];
-    const TileGeom &g = a.g;
-    const TileSmem L = tile_smem(g, MODE);
-    float *s_tw = smem + L.tw, *s_rr = smem + L.rr, *s_cr = smem + L.cr, *s_dt = smem + L.dtr;
-    float *s_nodes = smem + L.nodes, *s_rows = smem + L.rows, *s_box = smem + L.box;
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// ---- TMA and mbarrier helpers (inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// 4-D tiled TMA load of box (x, y, z, c) into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z,
+                                            int c) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for a TMA plane: gives up after a fixed number of polls and
+// raises the error flag instead of hanging.
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err) {
+    for (int it = 0; !mbar_try_wait(bar, phase); ++it) {
+        if (it > (1 << 20)) {
+            atomicExch(err, 1);
+            break;
+        }
+    }
+}
+
+// y-reduce the row sums of node planes 0..nplanes-1 and write the CTA's box.
+template <int TY, bool SQ>
+__device__ __forceinline__ void write_box(const TileGeom &g, const float *rowA, const float *rowB, float *boxes,
+                                          int cta, int nplanes, int tid, int nt) {
+    const int CX = g.C[0], CY = g.C[1], ry = g.rho[1], lry = g.lrho[1];
+    const float iry = g.irho[1];
+    const int per = (CX + 1) * (CY + 1);
+    for (int e = tid; e < 3 * nplanes * per; e += nt) {
+        const int jx = e % (CX + 1), t2 = e / (CX + 1), jy = t2 % (CY + 1), t3 = t2 / (CY + 1);
+        const int jz = t3 % nplanes, comp = t3 / nplanes;
+        float v = 0.f;
+        const int ty_lo = max(0, (jy - 1) * ry), ty_hi = min(TY, (jy + 1) * ry);
+        const float *ra = rowA + (long)jz * TY * (CX + 1) * 3, *rb = rowB + (long)jz * TY * (CX + 1) * 3;
+        for (int ty = ty_lo; ty < ty_hi; ++ty) {
+            float wy = ((ty & (ry - 1)) + 0.5f) * iry;
+            if ((ty >> lry) == jy) wy = 1.f - wy;
+            if (SQ) wy *= wy;
+            v = fmaf(wy, ra[(ty * (CX + 1) + jx) * 3 + comp] + rb[(ty * (CX + 1) + jx) * 3 + comp], v);
+        }
+        boxes[((long)cta * 3 + comp) * g.box + (jz * (CY + 1) + jy) * (CX + 1) + jx] = v;
+    }
+}
+
+template <int TY, int MODE, typename TImg>
+__global__ void __launch_bounds__(32 * (TY + 4), TY == 8 ? 2 : 1) ngf_tile_kernel(const __grid_constant__ TileArgs<TImg> a) {
+    using M = Mode<MODE>;
+    constexpr int NW = TY + 4, NT = 32 * NW;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bars[kTmaStages];
+    const TileGeom &g = a.g;
+    const ColSmem S = col_smem(g, MODE);
+    const bool tma = (M::matvec || M::diag) && g.tma;
+    float *ex1 = smem + S.ex1, *ex2 = smem + S.ex2, *ex3 = smem + S.ex3;
+    float *s_nodes = smem + S.nodes, *rowA = smem + S.rowA, *rowB = smem + S.rowB;
+
+    const int tid = threadIdx.x, L = tid & 31, w = tid >> 5;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const long sxy = (long)nx * ny, N = sxy * nz;
-    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * TY, z0 = blockIdx.z * g.TZ;
+    const int TXI = g.TXI;
+    const int x0 = blockIdx.x * TXI, y0 = blockIdx.y * TY, z0 = blockIdx.z * g.TZ;
     const int TZc = min(g.TZ, nz - z0);
-    const int rx = g.rho[0], ry = g.rho[1], rz = g.rho[2];
-    const int mx = g.m[0], my = g.m[1];
-    const long mxy = (long)mx * my, Mn = mxy * g.m[2];
-    const int CX = g.C[0], CY = g.C[1];
-    const int kx_lo = max(x0 - HW, 0) / rx, ky_lo = max(y0 - HW, 0) / ry;
-    const int nxt = g.nxt, nyt = g.nyt, nplane = nxt * nyt;
+    const int rx = g.rho[0], rz = g.rho[2];
+    const int lrx = g.lrho[0], lry = g.lrho[1], lrz = g.lrho[2];
+    const float irx = g.irho[0], iry = g.irho[1], irz = g.irho[2];
+    const int gx = x0 - 2 + L, gy = y0 - 2 + w;
+    const bool colin = L < TXI + 4 && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    const bool inC = L >= 1 && L <= TXI + 2 && w >= 1 && w <= TY + 2;
+    const bool inA = L >= 2 && L <= TXI + 1 && w >= 2 && w <= TY + 1;
+    const bool intxy = colin && gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2;
+    const long col = colin ? (long)gy * nx + gx : 0;
+    const int CX = g.C[0];
+    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+
+    // ---- plane-invariant per-column constants
+    const int kx_lo = max(x0 - 2, 0) >> lrx, ky_lo = max(y0 - 2, 0) >> lry;
+    int nlx = 0, nly = 0;
+    float fxw = 0.f, fyw = 0.f;
+    if (colin) {
+        const int cxg = gx >> lrx, cyg = gy >> lry;
+        fxw = ((gx - (cxg << lrx)) + 0.5f) * irx;
+        fyw = ((gy - (cyg << lry)) + 0.5f) * iry;
+        nlx = cxg - kx_lo;
+        nly = cyg - ky_lo;
+    }
+    const int nxt = g.nxt, nplane = g.nxt * g.nyt;
+    // P^T along x: this column's cell within the tile and its two weights
+    const int xl = L - 2;
+    const int cxl = inA ? (xl >> lrx) : 0;
+    float wx1 = inA ? ((xl & (rx - 1)) + 0.5f) * irx : 0.f, wx0 = inA ? 1.f - wx1 : 0.f;
+    if (M::diag) { wx0 *= wx0; wx1 *= wx1; }
+    const bool leader = inA && ((xl & (rx - 1)) == 0);
 
     if (M::reduce)
-        for (int i = tid; i < 3 * g.box; i += kThreads) s_box[i] = 0.f;
+        for (int i = tid; i < (g.C[2] + 1) * TY * (CX + 1) * 3; i += NT) { rowA[i] = 0.f; rowB[i] = 0.f; }
+    // the node planes this CTA interpolates from, loaded once (if they fit)
+    const int kz_lo = max(z0 - M::HZ, 0) >> lrz;
+    if (!M::diag && g.nzt > 0) {
+        const long mxy = (long)g.m[0] * g.m[1], Mn = mxy * g.m[2];
+        for (int i = tid; i < g.nzt * 3 * nplane; i += NT) {
+            const int pl = i / nplane, r = i - pl * nplane;          // pl = plane * 3 + comp
+            const int kz = kz_lo + pl / 3, comp = pl - (pl / 3) * 3;
+            const int ly = r / nxt, lx = r - ly * nxt;
+            const int ux = kx_lo + lx, uy = ky_lo + ly;
+            float v = 0.f;
+            if (ux < g.m[0] && uy < g.m[1] && kz < g.m[2]) v = __ldg(a.u + comp * Mn + (long)kz * mxy + (long)uy * g.m[0] + ux);
+            s_nodes[i] = v;
+        }
+    }
 
-    // Per-thread W-stage points and their x-y interpolated node values at the
-    // two node planes bracketing the current voxel plane.
-    float U[PPT][2][3];
+    // ---- state carried between planes
+    float U0[3] = {0.f, 0.f, 0.f}, U1[3] = {0.f, 0.f, 0.f};   // x-y interpolated node values, planes cz, cz+1
     int cur_cz = -1000;
-    float dsum = 0.f, dcomp = 0.f;   // Kahan sum of (1 - r^2) over own voxels
+    float t_m = 0.f, t_0 = 0.f, t_p = 0.f;                     // W value at planes pW-2, pW-1, pW
+    float r_m = 0.f, r_0 = 0.f, r_p = 0.f;                     // R at the same planes
+    float d_2[3] = {0.f, 0.f, 0.f}, d_1[3] = {0.f, 0.f, 0.f}, d_0[3] = {0.f, 0.f, 0.f};   // dT/dy
+    float cx_p = 0.f, cy_p = 0.f, cz_mm = 0.f, cz_m = 0.f;     // adjoint inputs of plane A
+    float q0_1 = 0.f, q1_1 = 0.f, q2_2 = 0.f, q2_1 = 0.f;      // diag: a^2 of planes pW-1, pW-2
+    float acc[2][2][3] = {};                                    // leader: [x node lo/hi][z plane P0/P1][comp]
+    float dsum = 0.f, dcomp = 0.f;
+    // matvec / diag prefetch: dT at the next W plane, a at the next C (diag: W) plane
+    float dnx[3] = {0.f, 0.f, 0.f}, anx[3] = {0.f, 0.f, 0.f};
+    const int nsteps = TZc + 2 * M::HZ;
+    constexpr uint32_t kPlaneBytes = 2u * kTmaBoxX * NW * 3 * 4;
+    // 128-byte aligned base of the TMA stages
+    float *tma_base = smem + S.tma + ((128u - (smem_u32(smem + S.tma) & 127u)) & 127u) / 4;
+    // plane j of this CTA's sequence: TMA into stage j % kTmaStages, or (outside
+    // the volume) a plain arrive so that the barrier's phase still advances
+    auto issue_plane = [&](int j) {
+        uint64_t *bar = &bars[j % kTmaStages];
+        const int p = z0 - M::HZ + j;
+        if (p >= 0 && p < nz) {
+            float *st = tma_base + (j % kTmaStages) * S.tma_stage;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, kPlaneBytes);
+            tma_load_4d(st, &a.map_dT, bar, x0 - 4, y0 - 2, p, 0);
+            tma_load_4d(st + S.tma_a, &a.map_a, bar, x0 - 4, y0 - 2, p, 0);
+        } else {
+            mbar_arrive(bar);
+        }
+    };
+    if (tma && tid == 0) {
+        for (int i = 0; i < kTmaStages; ++i) mbar_init(&bars[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int j = 0; j < kTmaStages - 2 && j < nsteps; ++j) issue_plane(j);
+    }
+    if ((M::matvec || M::diag) && !tma) {
+        const int p = z0 - M::HZ;
+        if (colin && p >= 0 && p < nz) {
+            const long v = (long)p * sxy + col;
+            dnx[0] = __ldg(a.lin_dT + v); dnx[1] = __ldg(a.lin_dT + N + v); dnx[2] = __ldg(a.lin_dT + 2 * N + v);
+            if (M::diag) { anx[0] = __ldg(a.lin_a + v); anx[1] = __ldg(a.lin_a + N + v); anx[2] = __ldg(a.lin_a + 2 * N + v); }
+        }
+        if (M::matvec && inC && colin && p - 1 >= 0 && p - 1 < nz) {
+            const long v = (long)(p - 1) * sxy + col;
+            anx[0] = __ldg(a.lin_a + v); anx[1] = __ldg(a.lin_a + N + v); anx[2] = __ldg(a.lin_a + 2 * N + v);
+        }
+    }
+    __syncthreads();
 
-    const int nsteps = TZc + 2 * HW;
-    for (int s = 0; s < nsteps; ++s) {
-        const int pW = z0 - HW + s;
-        // ---------------- node planes for the prolongation of plane pW
-        if (!M::diag && pW >= 0 && pW < nz) {
-            const int cz = pW / rz;
+    const int o = w * kTmaBoxX + L + 2;   // this column in a TMA box
+    int stage = 0;                         // s % kTmaStages
+    uint32_t phase = 0;                    // (s / kTmaStages) & 1
+    for (int s = 0; s < nsteps; ++s, stage = stage + 1 == kTmaStages ? 0 : stage + 1, phase ^= (stage == 0)) {
+        const int pW = z0 - M::HZ + s, pC = pW - 1, pA = pW - M::LAG;
+        const bool zW = pW >= 0 && pW < nz;
+        // ------------------------------------------------ node planes for P of plane pW
+        if (!M::diag && zW && g.nzt > 0) {
+            const int cz = pW >> lrz;
+            if (cz != cur_cz && colin) {
+                const bool both = cz != cur_cz + 1;
+                const float *qa = s_nodes + ((cz - kz_lo) * 3) * nplane + nly * nxt + nlx;
+                const float *qb = qa + 3 * nplane;
+#pragma unroll
+                for (int comp = 0; comp < 3; ++comp) {
+                    if (both) {
+                        const float *q = qa + comp * nplane;
+                        U0[comp] = lerp_fixed(lerp_fixed(q[0], q[1], 1.f - fxw, fxw),
+                                              lerp_fixed(q[nxt], q[nxt + 1], 1.f - fxw, fxw), 1.f - fyw, fyw);
+                    } else {
+                        U0[comp] = U1[comp];
+                    }
+                    const float *q = qb + comp * nplane;
+                    U1[comp] = lerp_fixed(lerp_fixed(q[0], q[1], 1.f - fxw, fxw),
+                                          lerp_fixed(q[nxt], q[nxt + 1], 1.f - fxw, fxw), 1.f - fyw, fyw);
+                }
+            }
+            cur_cz = cz;
+        } else if (!M::diag && zW) {
+            const int cz = pW >> lrz;
             if (cz != cur_cz) {
                 const bool both = cz != cur_cz + 1;
+                const long mxy = (long)g.m[0] * g.m[1], Mn = mxy * g.m[2];
                 for (int kz = both ? cz : cz + 1; kz <= cz + 1; ++kz) {
                     float *dst = s_nodes + (kz & 1) * 3 * nplane;
-                    for (int i = tid; i < 3 * nplane; i += kThreads) {
-                        int comp = i / nplane, r = i - comp * nplane;
-                        int ly = r / nxt, lx = r - ly * nxt;
-                        int gx = kx_lo + lx, gy = ky_lo + ly;
+                    for (int i = tid; i < 3 * nplane; i += NT) {
+                        const int comp = i / nplane, r = i - comp * nplane;
+                        const int ly = r / nxt, lx = r - ly * nxt;
+                        const int ux = kx_lo + lx, uy = ky_lo + ly;
                         float v = 0.f;
-                        if (gx < mx && gy < my) v = __ldg(a.u + comp * Mn + (long)kz * mxy + (long)gy * mx + gx);
+                        if (ux < g.m[0] && uy < g.m[1]) v = __ldg(a.u + comp * Mn + (long)kz * mxy + (long)uy * g.m[0] + ux);
                         dst[i] = v;
                     }
                 }
                 __syncthreads();
+                if (colin) {
+                    const float *qa = s_nodes + (cz & 1) * 3 * nplane + nly * nxt + nlx;
+                    const float *qb = s_nodes + ((cz + 1) & 1) * 3 * nplane + nly * nxt + nlx;
 #pragma unroll
-                for (int j = 0; j < PPT; ++j) {
-                    const int pt = tid + j * kThreads;
-                    const int ry_ = pt / RW, rx_ = pt - ry_ * RW;
-                    const int gx = x0 - HW + rx_, gy = y0 - HW + ry_;
-                    if (pt < RW * RH && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-                        const int cx = gx / rx, cy = gy / ry;
-                        const float fx = ((gx - cx * rx) + 0.5f) / rx, fy = ((gy - cy * ry) + 0.5f) / ry;
-                        const int lx = cx - kx_lo, ly = cy - ky_lo;
+                    for (int comp = 0; comp < 3; ++comp) {
                         if (both) {
-                            const float *np_ = s_nodes + (cz & 1) * 3 * nplane;
-#pragma unroll
-                            for (int comp = 0; comp < 3; ++comp) {
-                                const float *q = np_ + comp * nplane + ly * nxt + lx;
-                                const float ux0 = lerp_fixed(q[0], q[1], 1.f - fx, fx);
-                                const float ux1 = lerp_fixed(q[nxt], q[nxt + 1], 1.f - fx, fx);
-                                U[j][0][comp] = lerp_fixed(ux0, ux1, 1.f - fy, fy);
-                            }
+                            const float *q = qa + comp * nplane;
+                            U0[comp] = lerp_fixed(lerp_fixed(q[0], q[1], 1.f - fxw, fxw),
+                                                  lerp_fixed(q[nxt], q[nxt + 1], 1.f - fxw, fxw), 1.f - fyw, fyw);
                         } else {
-#pragma unroll
-                            for (int comp = 0; comp < 3; ++comp) U[j][0][comp] = U[j][1][comp];
+                            U0[comp] = U1[comp];
                         }
-                        const float *np_ = s_nodes + ((cz + 1) & 1) * 3 * nplane;
-#pragma unroll
-                        for (int comp = 0; comp < 3; ++comp) {
-                            const float *q = np_ + comp * nplane + ly * nxt + lx;
-                            const float ux0 = lerp_fixed(q[0], q[1], 1.f - fx, fx);
-                            const float ux1 = lerp_fixed(q[nxt], q[nxt + 1], 1.f - fx, fx);
-                            U[j][1][comp] = lerp_fixed(ux0, ux1, 1.f - fy, fy);
-                        }
+                        const float *q = qb + comp * nplane;
+                        U1[comp] = lerp_fixed(lerp_fixed(q[0], q[1], 1.f - fxw, fxw),
+                                              lerp_fixed(q[nxt], q[nxt + 1], 1.f - fxw, fxw), 1.f - fyw, fyw);
                     }
                 }
                 cur_cz = cz;
             }
         }
-        // ---------------- stage W: plane pW on the halo-HW region
-        if (M::diag) {
-            // squares of the stored a = dr/dg around the tile, dT/dy on the tile
-            float *ca = s_cr + ring3(pW) * 3 * RW * RH;
-            float *dt = s_dt + ring3(pW) * 3 * kTileX * TY;
-            const bool zin = pW >= 0 && pW < nz;
-            for (int pt = tid; pt < RW * RH; pt += kThreads) {
-                const int ry_ = pt / RW, rx_ = pt - ry_ * RW;
-                const int gx = x0 - HW + rx_, gy = y0 - HW + ry_;
-                const bool in = zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-                float q0 = 0.f, q1 = 0.f, q2 = 0.f;
-                if (in) {
-                    const long vox = (long)pW * sxy + (long)gy * nx + gx;
-                    q0 = __ldg(a.lin_a + vox);
-                    q1 = __ldg(a.lin_a + N + vox);
-                    q2 = __ldg(a.lin_a + 2 * N + vox);
-                    const bool own = rx_ >= HW && rx_ < HW + kTileX && ry_ >= HW && ry_ < HW + TY && pW >= z0 &&
-                                     pW < z0 + TZc;
-                    if (own) {
-                        const int k = (ry_ - HW) * kTileX + (rx_ - HW);
-                        dt[k] = __ldg(a.lin_dT + vox);
-                        dt[kTileX * TY + k] = __ldg(a.lin_dT + N + vox);
-                        dt[2 * kTileX * TY + k] = __ldg(a.lin_dT + 2 * N + vox);
-                    }
+        // ------------------------------------------------ stage W: plane pW
+        float val = 0.f, rv = 0.f, dn[3] = {0.f, 0.f, 0.f}, qn[3] = {0.f, 0.f, 0.f};
+        float acur[3] = {anx[0], anx[1], anx[2]};   // matvec: a at plane pC
+        if (tma) {
+            // issue plane s + 3 into the stage of plane s - 2 (free: its last
+            // reader, stage C of step s - 1, is behind this step's barriers),
+            // then wait for plane s
+            if (tid == 0 && s + kTmaStages - 2 < nsteps) issue_plane(s + kTmaStages - 2);
+            mbar_wait_bounded(&bars[stage], phase, a.err);
+            const float *st = tma_base + stage * S.tma_stage;
+            if (colin && zW) {
+                dn[0] = st[o]; dn[1] = st[NW * kTmaBoxX + o]; dn[2] = st[2 * NW * kTmaBoxX + o];
+                if (M::diag) {
+                    const float *sa = st + S.tma_a;
+                    const float q0 = sa[o], q1 = sa[NW * kTmaBoxX + o], q2 = sa[2 * NW * kTmaBoxX + o];
+                    qn[0] = q0 * q0; qn[1] = q1 * q1; qn[2] = q2 * q2;
                 }
-                ca[pt] = q0 * q0;
-                ca[RW * RH + pt] = q1 * q1;
-                ca[2 * RW * RH + pt] = q2 * q2;
             }
-        } else {
-            float *tw = s_tw + ring3(pW) * RW * RH;
-            float *rr = s_rr + ring3(pW) * RW * RH;
-            float *dt = s_dt + ring3(pW) * 3 * kTileX * TY;
-            const bool zin = pW >= 0 && pW < nz;
-            const int cz = zin ? pW / rz : 0;
-            const float fz = zin ? ((pW - cz * rz) + 0.5f) / rz : 0.f;
+            if (M::matvec && s >= 1 && colin && pC >= 0 && pC < nz) {
+                const float *sa = tma_base + (stage == 0 ? kTmaStages - 1 : stage - 1) * S.tma_stage + S.tma_a;
+                acur[0] = sa[o]; acur[1] = sa[NW * kTmaBoxX + o]; acur[2] = sa[2 * NW * kTmaBoxX + o];
+            }
+        } else if (M::matvec || M::diag) {
+            dn[0] = dnx[0]; dn[1] = dnx[1]; dn[2] = dnx[2];
+            if (M::diag) { qn[0] = anx[0] * anx[0]; qn[1] = anx[1] * anx[1]; qn[2] = anx[2] * anx[2]; }
+            // prefetch the next planes
+            const int p = pW + 1;
+            dnx[0] = dnx[1] = dnx[2] = 0.f;
+            if (colin && p >= 0 && p < nz) {
+                const long v = (long)p * sxy + col;
+                dnx[0] = __ldg(a.lin_dT + v); dnx[1] = __ldg(a.lin_dT + N + v); dnx[2] = __ldg(a.lin_dT + 2 * N + v);
+            }
+            anx[0] = anx[1] = anx[2] = 0.f;
+            const int pa = M::matvec ? pW : pW + 1;
+            if ((M::diag || inC) && colin && pa >= 0 && pa < nz) {
+                const long v = (long)pa * sxy + col;
+                anx[0] = __ldg(a.lin_a + v); anx[1] = __ldg(a.lin_a + N + v); anx[2] = __ldg(a.lin_a + 2 * N + v);
+            }
+        }
+        if (colin && zW && !M::diag) {
+            const float fz = ((pW & (rz - 1)) + 0.5f) * irz;
+            float pu[3];
 #pragma unroll
-            for (int j = 0; j < PPT; ++j) {
-                const int pt = tid + j * kThreads;
-                if (pt >= RW * RH) continue;
-                const int ry_ = pt / RW, rx_ = pt - ry_ * RW;
-                const int gx = x0 - HW + rx_, gy = y0 - HW + ry_;
-                const bool in = zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-                const bool own = in && rx_ >= HW && rx_ < HW + kTileX && ry_ >= HW && ry_ < HW + TY && pW >= z0 &&
-                                 pW < z0 + TZc;
-                float val = 0.f, rv = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-                if (in) {
-                    const long vox = (long)pW * sxy + (long)gy * nx + gx;
-                    float pu[3];
+            for (int comp = 0; comp < 3; ++comp) pu[comp] = lerp_fixed(U0[comp], U1[comp], 1.f - fz, fz);
+            if (M::matvec) {
+                val = dn[0] * pu[0] + dn[1] * pu[1] + dn[2] * pu[2];
+            } else {
+                int c[3], stp[3];
+                float f[3];
+                bool ins[3];
+                const int ii[3] = {gx, gy, pW};
 #pragma unroll
-                    for (int comp = 0; comp < 3; ++comp) pu[comp] = lerp_fixed(U[j][0][comp], U[j][1][comp], 1.f - fz, fz);
-                    if (M::matvec) {
-                        d0 = __ldg(a.lin_dT + vox);
-                        d1 = __ldg(a.lin_dT + N + vox);
-                        d2 = __ldg(a.lin_dT + 2 * N + vox);
-                        val = d0 * pu[0] + d1 * pu[1] + d2 * pu[2];
-                    } else {
-                        int c[3], stp[3];
-                        float f[3];
-                        bool ins[3];
-                        const int ii[3] = {gx, gy, pW};
-#pragma unroll
-                        for (int ax = 0; ax < 3; ++ax) {
-                            // cell decision: fixed-order FP32 product (shared definition with the oracle)
-                            const float q = __fmul_rn(pu[ax], g.invh[ax]);
-                            const float fl = floorf(q);
-                            // fraction: add the exact rounding error of the product and the
-                            // correction for float(1/h) (g.invh_rel = 1 - h * float(1/h))
-                            const float e = __fmaf_rn(pu[ax], g.invh[ax], -q);
-                            const float fr = (q - fl) + __fmaf_rn(q, g.invh_rel[ax], e);
-                            place_axis(ii[ax] + (int)fl, q - fl, g.n[ax], c[ax], stp[ax], f[ax], ins[ax]);
-                            if (stp[ax] > 0 && ins[ax]) f[ax] = fr;
-                        }
-                        const long sx = stp[0], sy = (long)stp[1] * nx, sz = (long)stp[2] * sxy;
-                        const long b = (long)c[2] * sxy + (long)c[1] * nx + c[0];
-                        const float t000 = ldimg(a.T, b), t100 = ldimg(a.T, b + sx);
-                        const float t010 = ldimg(a.T, b + sy), t110 = ldimg(a.T, b + sy + sx);
-                        const float t001 = ldimg(a.T, b + sz), t101 = ldimg(a.T, b + sz + sx);
-                        const float t011 = ldimg(a.T, b + sz + sy), t111 = ldimg(a.T, b + sz + sy + sx);
-                        const float dx00 = t100 - t000, dx10 = t110 - t010, dx01 = t101 - t001, dx11 = t111 - t011;
-                        const float v00 = fmaf(f[0], dx00, t000), v10 = fmaf(f[0], dx10, t010);
-                        const float v01 = fmaf(f[0], dx01, t001), v11 = fmaf(f[0], dx11, t011);
-                        const float dy0 = v10 - v00, dy1 = v11 - v01;
-                        const float w0 = fmaf(f[1], dy0, v00), w1 = fmaf(f[1], dy1, v01);
-                        const float dz = w1 - w0;
-                        val = fmaf(f[2], dz, w0);
-                        const float ax0 = fmaf(f[1], dx10 - dx00, dx00), ax1 = fmaf(f[1], dx11 - dx01, dx01);
-                        d0 = ins[0] ? fmaf(f[2], ax1 - ax0, ax0) * g.invh[0] * (float)stp[0] : 0.f;
-                        d1 = ins[1] ? fmaf(f[2], dy1 - dy0, dy0) * g.invh[1] * (float)stp[1] : 0.f;
-                        d2 = ins[2] ? dz * g.invh[2] * (float)stp[2] : 0.f;
-                        rv = ldimg(a.R, vox);
-                    }
-                    if (M::store && own) {
-                        a.st_dT[vox] = d0;
-                        a.st_dT[N + vox] = d1;
-                        a.st_dT[2 * N + vox] = d2;
-                    }
+                for (int ax = 0; ax < 3; ++ax) {
+                    // cell decision: fixed-order FP32 product (shared definition with the oracle)
+                    const float q = __fmul_rn(pu[ax], g.invh[ax]);
+                    const float fl = floorf(q);
+                    // fraction: add the exact rounding error of the product and the
+                    // correction for float(1/h) (g.invh_rel = 1 - h * float(1/h))
+                    const float e = __fmaf_rn(pu[ax], g.invh[ax], -q);
+                    const float fr = (q - fl) + __fmaf_rn(q, g.invh_rel[ax], e);
+                    place_axis(ii[ax] + (int)fl, q - fl, g.n[ax], c[ax], stp[ax], f[ax], ins[ax]);
+                    if (stp[ax] > 0 && ins[ax]) f[ax] = fr;
                 }
-                tw[pt] = val;
-                if (!M::matvec) rr[pt] = rv;
-                if (M::grad && own) {
-                    const int k = (ry_ - HW) * kTileX + (rx_ - HW);
-                    dt[k] = d0;
-                    dt[kTileX * TY + k] = d1;
-                    dt[2 * kTileX * TY + k] = d2;
+                const long sx = stp[0], sy = (long)stp[1] * nx, sz = (long)stp[2] * sxy;
+                const long b = (long)c[2] * sxy + (long)c[1] * nx + c[0];
+                const float t000 = ldimg(a.T, b), t100 = ldimg(a.T, b + sx);
+                const float t010 = ldimg(a.T, b + sy), t110 = ldimg(a.T, b + sy + sx);
+                const float t001 = ldimg(a.T, b + sz), t101 = ldimg(a.T, b + sz + sx);
+                const float t011 = ldimg(a.T, b + sz + sy), t111 = ldimg(a.T, b + sz + sy + sx);
+                rv = ldimg(a.R, (long)pW * sxy + col);
+                const float dx00 = t100 - t000, dx10 = t110 - t010, dx01 = t101 - t001, dx11 = t111 - t011;
+                const float v00 = fmaf(f[0], dx00, t000), v10 = fmaf(f[0], dx10, t010);
+                const float v01 = fmaf(f[0], dx01, t001), v11 = fmaf(f[0], dx11, t011);
+                const float dy0 = v10 - v00, dy1 = v11 - v01;
+                const float w0 = fmaf(f[1], dy0, v00), w1 = fmaf(f[1], dy1, v01);
+                const float dz = w1 - w0;
+                val = fmaf(f[2], dz, w0);
+                const float ax0 = fmaf(f[1], dx10 - dx00, dx00), ax1 = fmaf(f[1], dx11 - dx01, dx01);
+                dn[0] = ins[0] ? fmaf(f[2], ax1 - ax0, ax0) * g.invh[0] * (float)stp[0] : 0.f;
+                dn[1] = ins[1] ? fmaf(f[2], dy1 - dy0, dy0) * g.invh[1] * (float)stp[1] : 0.f;
+                dn[2] = ins[2] ? dz * g.invh[2] * (float)stp[2] : 0.f;
+                if (M::store && inA && pW >= z0 && pW < z0 + TZc) {
+                    const long v = (long)pW * sxy + col;
+                    a.st_dT[v] = dn[0];
+                    a.st_dT[N + v] = dn[1];
+                    a.st_dT[2 * N + v] = dn[2];
                 }
             }
         }
-        __syncthreads();
-        // ---------------- stage C: plane pC on the halo-HC region
-        const int pC = pW - 1;
-        if (!M::diag && pC >= z0 - HC) {
-            const float *tw_m = s_tw + ring3(pC - 1) * RW * RH, *tw_0 = s_tw + ring3(pC) * RW * RH,
-                        *tw_p = s_tw + ring3(pC + 1) * RW * RH;
-            const float *rr_m = s_rr + ring3(pC - 1) * RW * RH, *rr_0 = s_rr + ring3(pC) * RW * RH,
-                        *rr_p = s_rr + ring3(pC + 1) * RW * RH;
-            float *cr = s_cr + ring3(pC) * 3 * CW * CH;
-            for (int pt = tid; pt < CW * CH; pt += kThreads) {
-                const int cy_ = pt / CW, cx_ = pt - cy_ * CW;
-                const int gx = x0 - HC + cx_, gy = y0 - HC + cy_;
-                const bool interior = gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2 && pC >= 1 && pC <= nz - 2;
-                const int w = (cy_ + HW - HC) * RW + (cx_ + HW - HC);   // index in the W region
-                float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+        // rotate the plane rings
+        t_m = t_0; t_0 = t_p; t_p = val;
+        r_m = r_0; r_0 = r_p; r_p = rv;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { d_2[k] = d_1[k]; d_1[k] = d_0[k]; d_0[k] = dn[k]; }
+
+        float zz[3] = {0.f, 0.f, 0.f};
+        if (M::diag) {
+            // ------------------------------------------ diagonal: A at plane pA = pW - 1
+            float *e1 = ex1 + (s & 1) * NW * 32;
+            e1[w * 32 + L] = q1_1;                       // a_y^2 of plane pA for the y-neighbours
+            __syncthreads();
+            const float q0l = __shfl_up_sync(FULL, q0_1, 1), q0r = __shfl_down_sync(FULL, q0_1, 1);
+            if (pA >= z0 && pA < z0 + TZc && inA && colin) {
+                const float b = (q0l + q0r) * (g.inv2h[0] * g.inv2h[0]) +
+                                (e1[(w - 1) * 32 + L] + e1[(w + 1) * 32 + L]) * (g.inv2h[1] * g.inv2h[1]) +
+                                (q2_2 + qn[2]) * (g.inv2h[2] * g.inv2h[2]);
+                zz[0] = b * d_1[0] * d_1[0];
+                zz[1] = b * d_1[1] * d_1[1];
+                zz[2] = b * d_1[2] * d_1[2];
+            }
+            q2_2 = q2_1; q2_1 = qn[2]; q0_1 = qn[0]; q1_1 = qn[1];
+        } else {
+            // ------------------------------------------ exchange plane pC for C's y-neighbours
+            float *e1 = ex1 + (s & 1) * NW * 32;
+            e1[w * 32 + L] = t_0;
+            if (M::warp) ex2[(s & 1) * NW * 32 + w * 32 + L] = r_0;
+            __syncthreads();
+            // ------------------------------------------ stage C: plane pC
+            const float tl = __shfl_up_sync(FULL, t_0, 1), tr = __shfl_down_sync(FULL, t_0, 1);
+            float rl = 0.f, rr = 0.f;
+            if (M::warp) { rl = __shfl_up_sync(FULL, r_0, 1); rr = __shfl_down_sync(FULL, r_0, 1); }
+            float cc[3] = {0.f, 0.f, 0.f};
+            const bool actC = pC >= z0 - (M::adj ? 1 : 0) && pC < z0 + TZc + (M::adj ? 1 : 0);
+            if (actC && inC) {
+                const bool interior = intxy && pC >= 1 && pC <= nz - 2;
+                const bool own = inA && pC >= z0 && pC < z0 + TZc;
                 if (interior) {
-                    const float g0 = (tw_0[w + 1] - tw_0[w - 1]) * g.inv2h[0];
-                    const float g1 = (tw_0[w + RW] - tw_0[w - RW]) * g.inv2h[1];
-                    const float g2 = (tw_p[w] - tw_m[w]) * g.inv2h[2];
-                    const long vox = (long)pC * sxy + (long)gy * nx + gx;
+                    const float g0 = (tr - tl) * g.inv2h[0];
+                    const float g1 = (e1[(w + 1) * 32 + L] - e1[(w - 1) * 32 + L]) * g.inv2h[1];
+                    const float g2 = (t_p - t_m) * g.inv2h[2];
                     if (M::matvec) {
-                        const float a0 = __ldg(a.lin_a + vox), a1 = __ldg(a.lin_a + N + vox), a2 = __ldg(a.lin_a + 2 * N + vox);
-                        const float dr = 2.f * (a0 * g0 + a1 * g1 + a2 * g2);
-                        c0 = dr * a0; c1 = dr * a1; c2 = dr * a2;
+                        const float dr = 2.f * (acur[0] * g0 + acur[1] * g1 + acur[2] * g2);
+                        cc[0] = dr * acur[0]; cc[1] = dr * acur[1]; cc[2] = dr * acur[2];
                     } else {
-                        const float f0 = (rr_0[w + 1] - rr_0[w - 1]) * g.inv2h[0];
-                        const float f1 = (rr_0[w + RW] - rr_0[w - RW]) * g.inv2h[1];
-                        const float f2 = (rr_p[w] - rr_m[w]) * g.inv2h[2];
+                        const float *e2 = ex2 + (s & 1) * NW * 32;
+                        const float f0 = (rr - rl) * g.inv2h[0];
+                        const float f1 = (e2[(w + 1) * 32 + L] - e2[(w - 1) * 32 + L]) * g.inv2h[1];
+                        const float f2 = (r_p - r_m) * g.inv2h[2];
                         // the same operation order for <f,g>, |f|^2, |g|^2: f = g gives equal values
                         const float fg = __fmaf_rn(f2, g2, __fmaf_rn(f1, g1, __fmaf_rn(f0, g0, g.eta2)));
                         const float ff = __fmaf_rn(f2, f2, __fmaf_rn(f1, f1, __fmaf_rn(f0, f0, g.eta2)));
                         const float gg = __fmaf_rn(g2, g2, __fmaf_rn(g1, g1, __fmaf_rn(g0, g0, g.eta2)));
                         const float rff = __frcp_rn(ff), rgg = __frcp_rn(gg);
-                        // 1 - r^2 = (|f x g|^2 + eta^2 |f - g|^2) / (|f|_eta^2 |g|_eta^2)
-                        // products rounded separately: exactly zero when f = g
+                        // 1 - r^2 = (|f x g|^2 + eta^2 |f - g|^2) / (|f|_eta^2 |g|_eta^2); products
+                        // rounded separately: exactly zero when f = g
                         const float x0_ = __fmul_rn(f1, g2) - __fmul_rn(f2, g1);
                         const float x1_ = __fmul_rn(f2, g0) - __fmul_rn(f0, g2);
                         const float x2_ = __fmul_rn(f0, g1) - __fmul_rn(f1, g0);
-                        const float e0 = f0 - g0, e1 = f1 - g1, e2 = f2 - g2;
-                        const float num = x0_ * x0_ + x1_ * x1_ + x2_ * x2_ + g.eta2 * (e0 * e0 + e1 * e1 + e2 * e2);
-                        const float om = num * rff * rgg;
-                        const bool own = gx >= x0 && gx < x0 + kTileX && gy >= y0 && gy < y0 + TY && pC >= z0 &&
-                                         pC < z0 + TZc;
-                        if (own) {   // Kahan summation
-                            const float yk = om - dcomp;
-                            const float tk = dsum + yk;
-                            dcomp = (tk - dsum) - yk;
-                            dsum = tk;
-                        }
-                        // a = dr/dg = (f |g|^2 - <f,g> g) / (|f| |g|^3) (norms with eta);
-                        // q = f |g|^2 - <f,g> g, each product rounded once: 0 when f = g
+                        const float e0 = f0 - g0, e1_ = f1 - g1, e2_ = f2 - g2;
+                        const float num = x0_ * x0_ + x1_ * x1_ + x2_ * x2_ + g.eta2 * (e0 * e0 + e1_ * e1_ + e2_ * e2_);
+                        if (own) kahan_add(dsum, dcomp, num * rff * rgg);
+                        // a = dr/dg = (f |g|^2 - <f,g> g) / (|f| |g|^3) (norms with eta)
                         const float q0 = __fmul_rn(f0, gg) - __fmul_rn(fg, g0);
                         const float q1 = __fmul_rn(f1, gg) - __fmul_rn(fg, g1);
                         const float q2 = __fmul_rn(f2, gg) - __fmul_rn(fg, g2);
-                        if (M::grad) {   // c = d(1 - r^2)/dg = -2 r a = -2 <f,g> q / (|f|^2 |g|^4)
+                        if (M::adj) {   // c = d(1 - r^2)/dg = -2 r a = -2 <f,g> q / (|f|^2 |g|^4)
                             const float sc = -2.f * fg * rff * rgg * rgg;
-                            c0 = sc * q0; c1 = sc * q1; c2 = sc * q2;
+                            cc[0] = sc * q0; cc[1] = sc * q1; cc[2] = sc * q2;
                         }
                         if (M::store && own) {
                             const float inv = rsqrtf(ff * gg) * rgg;
-                            a.st_a[vox] = q0 * inv;
-                            a.st_a[N + vox] = q1 * inv;
-                            a.st_a[2 * N + vox] = q2 * inv;
+                            const long v = (long)pC * sxy + col;
+                            a.st_a[v] = q0 * inv;
+                            a.st_a[N + v] = q1 * inv;
+                            a.st_a[2 * N + v] = q2 * inv;
                         }
                     }
-                } else if (M::store) {
-                    const bool own = gx >= x0 && gx < x0 + kTileX && gx < nx && gy >= y0 && gy < y0 + TY &&
-                                     gy < ny && pC >= z0 && pC < z0 + TZc;
-                    if (own) {
-                        const long vox = (long)pC * sxy + (long)gy * nx + gx;
-                        a.st_a[vox] = 0.f;
-                        a.st_a[N + vox] = 0.f;
-                        a.st_a[2 * N + vox] = 0.f;
-                    }
-                }
-                if (M::grad) {
-                    cr[pt] = c0;
-                    cr[CW * CH + pt] = c1;
-                    cr[2 * CW * CH + pt] = c2;
+                } else if (M::store && own && colin) {
+                    const long v = (long)pC * sxy + col;
+                    a.st_a[v] = 0.f;
+                    a.st_a[N + v] = 0.f;
+                    a.st_a[2 * N + v] = 0.f;
                 }
             }
-        }
-        __syncthreads();
-        if (!M::reduce) continue;
-        // ---------------- stage A: plane pA, adjoint and P^T
-        // (diagonal mode: beta * dT^2 and P^T with squared weights)
-        const int pA = M::diag ? pW - 1 : pC - 1;
-        if (pA >= z0) {
-            constexpr int AW = M::diag ? RW : CW, AH = M::diag ? RH : CH, AO = M::diag ? HW : HC;
-            const float *c_m = s_cr + ring3(pA - 1) * 3 * AW * AH, *c_0 = s_cr + ring3(pA) * 3 * AW * AH,
-                        *c_p = s_cr + ring3(pA + 1) * 3 * AW * AH;
-            const float *dt = s_dt + ring3(pA) * 3 * kTileX * TY;
-            const int gx = x0 + lane;
-            float fx = ((lane & (rx - 1)) + 0.5f) / rx, fx0 = 1.f - fx;
-            if (M::diag) { fx0 *= fx0; fx *= fx; }
-            for (int ty = warp; ty < TY; ty += kThreads / 32) {
-                const int gy = y0 + ty;
-                float z0_ = 0.f, z1_ = 0.f, z2_ = 0.f;
-                if (gx < nx && gy < ny) {
-                    const int w = (ty + AO) * AW + (lane + AO);
-                    const int k = ty * kTileX + lane;
-                    float b;
-                    if (M::diag) {
-                        b = (c_0[w - 1] + c_0[w + 1]) * (g.inv2h[0] * g.inv2h[0]) +
-                            (c_0[AW * AH + w - AW] + c_0[AW * AH + w + AW]) * (g.inv2h[1] * g.inv2h[1]) +
-                            (c_m[2 * AW * AH + w] + c_p[2 * AW * AH + w]) * (g.inv2h[2] * g.inv2h[2]);
-                        const float d0 = dt[k], d1 = dt[kTileX * TY + k], d2 = dt[2 * kTileX * TY + k];
-                        z0_ = b * d0 * d0;
-                        z1_ = b * d1 * d1;
-                        z2_ = b * d2 * d2;
-                    } else {
-                        b = (c_0[w - 1] - c_0[w + 1]) * g.inv2h[0] +
-                            (c_0[AW * AH + w - AW] - c_0[AW * AH + w + AW]) * g.inv2h[1] +
-                            (c_m[2 * AW * AH + w] - c_p[2 * AW * AH + w]) * g.inv2h[2];
-                        z0_ = b * dt[k];
-                        z1_ = b * dt[kTileX * TY + k];
-                        z2_ = b * dt[2 * kTileX * TY + k];
-                    }
-                }
-                float lo[3] = {fx0 * z0_, fx0 * z1_, fx0 * z2_};
-                float hi[3] = {fx * z0_, fx * z1_, fx * z2_};
-                for (int off = 1; off < rx; off <<= 1)
-                    for (int comp = 0; comp < 3; ++comp) {
-                        lo[comp] += __shfl_xor_sync(0xffffffffu, lo[comp], off);
-                        hi[comp] += __shfl_xor_sync(0xffffffffu, hi[comp], off);
-                    }
-                if ((lane & (rx - 1)) == 0) {
-                    const int cell = lane / rx;
-                    for (int comp = 0; comp < 3; ++comp) {
-                        s_rows[(ty * CX + cell) * 3 + comp] = lo[comp];
-                        s_rows[((TY + ty) * CX + cell) * 3 + comp] = hi[comp];
-                    }
-                }
-            }
+            if (!M::adj) continue;
+            // ------------------------------------------ exchange c_y of plane pA
+            float *e3 = ex3 + (s & 1) * NW * 32;
+            e3[w * 32 + L] = cy_p;
             __syncthreads();
-            const int lz = (pA - z0) / rz;
-            const float fz = (((pA - z0) - lz * rz) + 0.5f) / rz;
-            const int nbx = CX + 1, nby = CY + 1;
-            for (int e = tid; e < 3 * nbx * nby; e += kThreads) {
-                const int jx = e % nbx, t2 = e / nbx, jy = t2 % nby, comp = t2 / nby;
-                float val = 0.f;
-                const int ty_lo = max(0, (jy - 1) * ry), ty_hi = min(TY, (jy + 1) * ry);
-                for (int ty = ty_lo; ty < ty_hi; ++ty) {
-                    const int cyl = ty / ry;
-                    const float fy = ((ty - cyl * ry) + 0.5f) / ry;
-                    float wy = cyl == jy ? 1.f - fy : fy;
-                    if (M::diag) wy *= wy;
-                    float rv = 0.f;
-                    if (jx < CX) rv += s_rows[(ty * CX + jx) * 3 + comp];
-                    if (jx >= 1) rv += s_rows[((TY + ty) * CX + jx - 1) * 3 + comp];
-                    val = fmaf(wy, rv, val);
-                }
-                float *bx = s_box + comp * g.box + (lz * nby + jy) * nbx + jx;
-                const float wz0 = M::diag ? (1.f - fz) * (1.f - fz) : 1.f - fz, wz1 = M::diag ? fz * fz : fz;
-                bx[0] += wz0 * val;
-                bx[nby * nbx] += wz1 * val;
+            // ------------------------------------------ stage A: plane pA
+            const float cxl_ = __shfl_up_sync(FULL, cx_p, 1), cxr_ = __shfl_down_sync(FULL, cx_p, 1);
+            if (pA >= z0 && pA < z0 + TZc && inA && colin) {
+                const float b = (cxl_ - cxr_) * g.inv2h[0] + (e3[(w - 1) * 32 + L] - e3[(w + 1) * 32 + L]) * g.inv2h[1] +
+                                (cz_mm - cc[2]) * g.inv2h[2];
+                zz[0] = b * d_2[0];
+                zz[1] = b * d_2[1];
+                zz[2] = b * d_2[2];
+            }
+            cz_mm = cz_m; cz_m = cc[2]; cx_p = cc[0]; cy_p = cc[1];
+        }
+        if (!(pA >= z0 && pA < z0 + TZc)) continue;
+        // ------------------------------------------------ P^T: x by shuffles, z in the leader's registers
+        float lo[3], hi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { lo[k] = wx0 * zz[k]; hi[k] = wx1 * zz[k]; }
+#pragma unroll
+        for (int lg = 0; lg < 3; ++lg) {
+            if (lg >= lrx) break;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                lo[k] += __shfl_down_sync(FULL, lo[k], 1 << lg);
+                hi[k] += __shfl_down_sync(FULL, hi[k], 1 << lg);
             }
         }
-        __syncthreads();
+        const int zl = pA - z0, czl = zl >> lrz;
+        float wz1 = ((zl & (rz - 1)) + 0.5f) * irz, wz0 = 1.f - wz1;
+        if (M::diag) { wz0 *= wz0; wz1 *= wz1; }
+        if (leader)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                acc[0][0][k] = fmaf(wz0, lo[k], acc[0][0][k]);
+                acc[0][1][k] = fmaf(wz1, lo[k], acc[0][1][k]);
+                acc[1][0][k] = fmaf(wz0, hi[k], acc[1][0][k]);
+                acc[1][1][k] = fmaf(wz1, hi[k], acc[1][1][k]);
+            }
+        if ((zl & (rz - 1)) == rz - 1) {
+            // node plane czl is complete for this row: park it, shift the z window
+            if (leader) {
+                float *ra = rowA + ((long)czl * TY + (w - 2)) * (CX + 1) * 3;
+                float *rb = rowB + ((long)czl * TY + (w - 2)) * (CX + 1) * 3;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    ra[cxl * 3 + k] = acc[0][0][k];
+                    rb[(cxl + 1) * 3 + k] = acc[1][0][k];
+                    acc[0][0][k] = acc[0][1][k]; acc[1][0][k] = acc[1][1][k];
+                    acc[0][1][k] = 0.f; acc[1][1][k] = 0.f;
+                }
+            }
+        }
     }
 
-    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     if (M::reduce) {
+        // the node plane above the last cell of the chunk, then the y-reduction of all planes
+        const int czl = TZc >> lrz;
+        if (leader) {
+            float *ra = rowA + ((long)czl * TY + (w - 2)) * (CX + 1) * 3;
+            float *rb = rowB + ((long)czl * TY + (w - 2)) * (CX + 1) * 3;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ra[cxl * 3 + k] = acc[0][0][k];
+                rb[(cxl + 1) * 3 + k] = acc[1][0][k];
+            }
+        }
         __syncthreads();
-        float *dst = a.boxes + (long)cta * 3 * g.box;
-        for (int i = tid; i < 3 * g.box; i += kThreads) dst[i] = s_box[i];
+        write_box<TY, M::diag>(g, rowA, rowB, a.boxes, cta, czl + 1, tid, NT);
     }
-    if (!M::matvec && !M::diag) {
+    if (M::warp) {
         double v = (double)dsum - (double)dcomp;
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        __shared__ double red[kThreads / 32];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+        __shared__ double red[NW];
         __syncthreads();
-        if (lane == 0) red[warp] = v;
+        if (L == 0) red[w] = v;
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+            for (int i = 0; i < NW; ++i) t += red[i];
             a.dpart[cta] = t;
         }
     }
@@ -468,18 +616,18 @@ static cudaError_t launch_mode(int mode, const TileArgs<TImg> &a, cudaStream_t s
         auto k = ngf_tile_kernel<TYV, MV, TImg>;                                                         \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                  \
-        k<<<grid, kThreads, smem, st>>>(a);                                                              \
+        k<<<grid, 32 * (TYV + 4), smem, st>>>(a);                                                        \
         return cudaGetLastError();                                                                       \
     } while (0)
-#define NGF_TY(TYV)                                     \
-    switch (mode) {                                     \
-        case MODE_OBJ: NGF_LAUNCH(TYV, MODE_OBJ);       \
-        case MODE_LIN: NGF_LAUNCH(TYV, MODE_LIN);       \
-        case MODE_GRAD: NGF_LAUNCH(TYV, MODE_GRAD);     \
+#define NGF_TY(TYV)                                       \
+    switch (mode) {                                       \
+        case MODE_OBJ: NGF_LAUNCH(TYV, MODE_OBJ);         \
+        case MODE_LIN: NGF_LAUNCH(TYV, MODE_LIN);         \
+        case MODE_GRAD: NGF_LAUNCH(TYV, MODE_GRAD);       \
         case MODE_GRADLIN: NGF_LAUNCH(TYV, MODE_GRADLIN); \
-        case MODE_MATVEC: NGF_LAUNCH(TYV, MODE_MATVEC); \
-        case MODE_DIAG: NGF_LAUNCH(TYV, MODE_DIAG);     \
-        default: return cudaErrorInvalidValue;          \
+        case MODE_MATVEC: NGF_LAUNCH(TYV, MODE_MATVEC);   \
+        case MODE_DIAG: NGF_LAUNCH(TYV, MODE_DIAG);       \
+        default: return cudaErrorInvalidValue;            \
     }
     switch (a.g.TY) {
         case 8: NGF_TY(8);

@@ -82,6 +82,7 @@ extern "C" int ngf_distance_noalloc(const rg_image_geom *img, const rg_grid_geom
     a.st_dT = a.st_a = nullptr;
     a.boxes = nullptr;
     a.dpart = partials;
+    a.err = nullptr;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (launch_ngf_tile(MODE_OBJ, a, s) != cudaSuccess) return RG_ECUDA;
     const double hbar = img->h[0] * img->h[1] * img->h[2];

@@ -93,19 +93,26 @@ __device__ __forceinline__ void cross3(const float *a, const float *b, float *c)
 // VM = 0: gradient of sum psi(d) (+ energy, folds, min/max d); VM = 1: GN
 // product sum psi''(d) (grad d . v) grad d; VM = 2: diagonal of the GN matrix
 // sum psi''(d) (d d / d u_{k,c})^2.
+//
+// Four threads per grid cell, one per z-edge c of the cell: each evaluates the
+// 16 bounds d_abc of its c (a, b over the x- and y-edges).  Gradients with
+// respect to the x- and y-edges are summed over the four threads with warp
+// shuffles; the first thread of the cell scatters the cell's contributions to
+// its 8 corners in shared memory, and nodes gather them per CTA box.
 template <int VM>
-__global__ void __launch_bounds__(256) vcc_kernel(const VccArgs a) {
+__global__ void __launch_bounds__(4 * kVccTile[0] * kVccTile[1] * kVccTile[2], 1) vcc_kernel(const VccArgs a) {
     constexpr bool GN = VM == 1, DG = VM == 2;
-    constexpr int TX = kVccTile[0], TY = kVccTile[1], TZ = kVccTile[2];
+    constexpr int TX = kVccTile[0], TY = kVccTile[1], TZ = kVccTile[2], NC = TX * TY * TZ, NT = 4 * NC;
     constexpr int BX = TX + 1, BY = TY + 1, BZ = TZ + 1, NB = BX * BY * BZ;
+    constexpr unsigned FULL = 0xffffffffu;
     __shared__ float su[3][NB];
     __shared__ float sv[GN ? 3 : 1][GN ? NB : 1];
-    __shared__ float scell[TX * TY * TZ][8][3];
-    const int tid = threadIdx.x;
+    __shared__ float scell[NC][8][3];
+    const int tid = threadIdx.x, lane = tid & 31;
     const int mx = a.m[0], my = a.m[1], mz = a.m[2];
     const long mxy = (long)mx * my, M = mxy * mz;
     const int cx0 = blockIdx.x * TX, cy0 = blockIdx.y * TY, cz0 = blockIdx.z * TZ;
-    for (int i = tid; i < NB; i += 256) {
+    for (int i = tid; i < NB; i += NT) {
         const int lz = i / (BX * BY), r = i - lz * BX * BY, ly = r / BX, lx = r - ly * BX;
         const int gx = cx0 + lx, gy = cy0 + ly, gz = cz0 + lz;
         const bool ok = gx < mx && gy < my && gz < mz;
@@ -116,160 +123,200 @@ __global__ void __launch_bounds__(256) vcc_kernel(const VccArgs a) {
         }
     }
     __syncthreads();
-    const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+    const int cell = tid >> 2, cz_e = tid & 3;   // z-edge index of this thread
+    const int lx = cell % TX, ly = (cell / TX) % TY, lz = cell / (TX * TY);
     const bool valid = cx0 + lx < mx - 1 && cy0 + ly < my - 1 && cz0 + lz < mz - 1;
-    float E[3][4][3], DE[GN ? 3 : 1][4][3], G[3][4][3];
+    const int base = (lz * BY + ly) * BX + lx;
+    auto corner = [&](int o) { return base + (o & 1) + ((o >> 1) & 1) * BX + (o >> 2) * BX * BY; };
+    // edge vectors: x-edges (4), y-edges (4), this thread's z-edge
+    float E1[4][3], E2[4][3], E3[3], D1[GN ? 4 : 1][3], D2[GN ? 4 : 1][3], D3[3];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int x0c = corner(edge_corner(0, e, 0)), x1c = corner(edge_corner(0, e, 1));
+        const int y0c = corner(edge_corner(1, e, 0)), y1c = corner(edge_corner(1, e, 1));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            E1[e][k] = (k == 0 ? 1.f : 0.f) + (su[k][x1c] - su[k][x0c]) * a.ig[0];
+            E2[e][k] = (k == 1 ? 1.f : 0.f) + (su[k][y1c] - su[k][y0c]) * a.ig[1];
+            if (GN) {
+                D1[e][k] = (sv[k][x1c] - sv[k][x0c]) * a.ig[0];
+                D2[e][k] = (sv[k][y1c] - sv[k][y0c]) * a.ig[1];
+            }
+        }
+    }
+    {
+        const int z0c = corner(edge_corner(2, cz_e, 0)), z1c = corner(edge_corner(2, cz_e, 1));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            E3[k] = (k == 2 ? 1.f : 0.f) + (su[k][z1c] - su[k][z0c]) * a.ig[2];
+            D3[k] = GN ? (sv[k][z1c] - sv[k][z0c]) * a.ig[2] : 0.f;
+        }
+    }
+    float G1[4][3] = {}, G2[4][3] = {}, G3[3] = {0.f, 0.f, 0.f};
+    float acc[DG ? 8 : 1][3] = {};
     int fold = 0;
     float dmn = 3.4e38f, dmx = -3.4e38f;
     Kahan en;
-    for (int c = 0; c < 8; ++c)
-        for (int k = 0; k < 3; ++k) scell[tid][c][k] = 0.f;
     if (valid) {
-        const int base = (lz * BY + ly) * BX + lx;
-        auto corner = [&](int o) { return base + (o & 1) + ((o >> 1) & 1) * BX + (o >> 2) * BX * BY; };
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int n0 = corner(edge_corner(ax, e, 0)), n1 = corner(edge_corner(ax, e, 1));
-                for (int k = 0; k < 3; ++k) {
-                    E[ax][e][k] = (k == ax ? 1.f : 0.f) + (su[k][n1] - su[k][n0]) * a.ig[ax];
-                    if (GN) DE[ax][e][k] = (sv[k][n1] - sv[k][n0]) * a.ig[ax];
-                    G[ax][e][k] = 0.f;
-                }
+        for (int b = 0; b < 4; ++b) {
+            float x23[3], y23[3], W1[3] = {0.f, 0.f, 0.f};
+            cross3(E2[b], E3, x23);
+            if (GN) {
+                float p[3], q[3];
+                cross3(D2[b], E3, p);
+                cross3(E2[b], D3, q);
+                y23[0] = p[0] + q[0]; y23[1] = p[1] + q[1]; y23[2] = p[2] + q[2];
             }
-        if (DG) {
-            float acc[8][3];
 #pragma unroll
-            for (int o = 0; o < 8; ++o) acc[o][0] = acc[o][1] = acc[o][2] = 0.f;
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float x23[3];
-                    cross3(E[1][b], E[2][c], x23);
-#pragma unroll
-                    for (int aa = 0; aa < 4; ++aa) {
-                        const float *e1 = E[0][aa];
-                        const float d = e1[0] * x23[0] + e1[1] * x23[1] + e1[2] * x23[2];
-                        if (!(d > 0.f)) continue;
-                        const float rd = __frcp_rn(d);
-                        const float w = 2.f * rd * rd * rd;     // psi''(d)
-                        float x31[3], x12[3];
-                        cross3(E[2][c], e1, x31);
-                        cross3(e1, E[1][b], x12);
-                        const int xo0 = edge_corner(0, aa, 0), xo1 = edge_corner(0, aa, 1);
-                        const int yo0 = edge_corner(1, b, 0), yo1 = edge_corner(1, b, 1);
-                        const int zo0 = edge_corner(2, c, 0), zo1 = edge_corner(2, c, 1);
-#pragma unroll
-                        for (int o = 0; o < 8; ++o) {
-                            const float sx = (o == xo1 ? 1.f : 0.f) - (o == xo0 ? 1.f : 0.f);
-                            const float sy = (o == yo1 ? 1.f : 0.f) - (o == yo0 ? 1.f : 0.f);
-                            const float sz = (o == zo1 ? 1.f : 0.f) - (o == zo0 ? 1.f : 0.f);
-                            if (sx == 0.f && sy == 0.f && sz == 0.f) continue;
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const float gd = sx * a.ig[0] * x23[k] + sy * a.ig[1] * x31[k] + sz * a.ig[2] * x12[k];
-                                acc[o][k] = fmaf(w * gd, gd, acc[o][k]);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-            for (int o = 0; o < 8; ++o)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) scell[tid][o][k] = acc[o][k];
-        } else {
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float x23[3], y23[3], W1[3] = {0.f, 0.f, 0.f};
-                cross3(E[1][b], E[2][c], x23);
-                if (GN) {
-                    float p[3], q[3];
-                    cross3(DE[1][b], E[2][c], p);
-                    cross3(E[1][b], DE[2][c], q);
-                    y23[0] = p[0] + q[0]; y23[1] = p[1] + q[1]; y23[2] = p[2] + q[2];
-                }
-#pragma unroll
-                for (int aa = 0; aa < 4; ++aa) {
-                    const float *e1 = E[0][aa];
-                    const float d = e1[0] * x23[0] + e1[1] * x23[1] + e1[2] * x23[2];
+            for (int aa = 0; aa < 4; ++aa) {
+                const float *e1 = E1[aa];
+                const float d = e1[0] * x23[0] + e1[1] * x23[1] + e1[2] * x23[2];
+                if (VM == 0) {
                     dmn = fminf(dmn, d);
                     dmx = fmaxf(dmx, d);
-                    if (!(d > 0.f)) { ++fold; continue; }
-                    const float rd = __frcp_rn(d);
-                    en.add(d - 2.f + rd);                       // psi(d) = (d - 1)^2 / d
-                    float w;
-                    if (GN) {
-                        const float *de1 = DE[0][aa];
-                        const float dd = de1[0] * x23[0] + de1[1] * x23[1] + de1[2] * x23[2] +
-                                         e1[0] * y23[0] + e1[1] * y23[1] + e1[2] * y23[2];
-                        w = 2.f * rd * rd * rd * dd;            // psi''(d) (grad d . v)
-                    } else {
-                        w = 1.f - rd * rd;                      // psi'(d)
-                    }
-                    for (int k = 0; k < 3; ++k) {
-                        G[0][aa][k] = fmaf(w, x23[k], G[0][aa][k]);
-                        W1[k] = fmaf(w, e1[k], W1[k]);
-                    }
                 }
-                float t2[3], t3[3];
-                cross3(E[2][c], W1, t2);   // sum_a w (e3_c x e1_a)
-                cross3(W1, E[1][b], t3);   // sum_a w (e1_a x e2_b)
+                if (!(d > 0.f)) {
+                    ++fold;
+                    continue;
+                }
+                if (DG) {
+                    const float rd = __fdividef(1.f, d);
+                    const float w = 2.f * rd * rd * rd;     // psi''(d)
+                    float x31[3], x12[3];
+                    cross3(E3, e1, x31);
+                    cross3(e1, E2[b], x12);
+                    const int xo0 = edge_corner(0, aa, 0), xo1 = edge_corner(0, aa, 1);
+                    const int yo0 = edge_corner(1, b, 0), yo1 = edge_corner(1, b, 1);
+                    const int zo0 = edge_corner(2, cz_e, 0), zo1 = edge_corner(2, cz_e, 1);
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) {
+                        const float sx = (o == xo1 ? 1.f : 0.f) - (o == xo0 ? 1.f : 0.f);
+                        const float sy = (o == yo1 ? 1.f : 0.f) - (o == yo0 ? 1.f : 0.f);
+                        const float sz = (o == zo1 ? 1.f : 0.f) - (o == zo0 ? 1.f : 0.f);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float gd = sx * a.ig[0] * x23[k] + sy * a.ig[1] * x31[k] + sz * a.ig[2] * x12[k];
+                            acc[o][k] = fmaf(w * gd, gd, acc[o][k]);
+                        }
+                    }
+                    continue;
+                }
+                float w;
+                if (GN) {
+                    const float rd = __fdividef(1.f, d);
+                    const float *de1 = D1[aa];
+                    const float dd = de1[0] * x23[0] + de1[1] * x23[1] + de1[2] * x23[2] + e1[0] * y23[0] +
+                                     e1[1] * y23[1] + e1[2] * y23[2];
+                    w = 2.f * rd * rd * rd * dd;            // psi''(d) (grad d . v)
+                } else {
+                    const float rd = __frcp_rn(d);
+                    const float dm = d - 1.f;
+                    en.add(dm * dm * rd);                   // psi(d) = (d - 1)^2 / d
+                    w = dm * (d + 1.f) * rd * rd;           // psi'(d) = 1 - 1/d^2
+                }
+#pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    G[1][b][k] += t2[k];
-                    G[2][c][k] += t3[k];
+                    G1[aa][k] = fmaf(w, x23[k], G1[aa][k]);
+                    W1[k] = fmaf(w, e1[k], W1[k]);
                 }
             }
+            if (!DG) {
+                float t2[3], t3[3];
+                cross3(E3, W1, t2);       // sum_a w (e3_c x e1_a)
+                cross3(W1, E2[b], t3);    // sum_a w (e1_a x e2_b)
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int o0 = edge_corner(ax, e, 0), o1 = edge_corner(ax, e, 1);
                 for (int k = 0; k < 3; ++k) {
-                    const float gval = G[ax][e][k] * a.ig[ax];
-                    scell[tid][o1][k] += gval;
-                    scell[tid][o0][k] -= gval;
+                    G2[b][k] += t2[k];
+                    G3[k] += t3[k];
                 }
             }
         }
     }
+    // sum over the four z-edge threads of the cell (aligned lane groups of 4)
+    float out[8][3];
+    if (DG) {
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float v = acc[o][k];
+                v += __shfl_xor_sync(FULL, v, 1);
+                v += __shfl_xor_sync(FULL, v, 2);
+                out[o][k] = v;
+            }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                G1[e][k] += __shfl_xor_sync(FULL, G1[e][k], 1);
+                G1[e][k] += __shfl_xor_sync(FULL, G1[e][k], 2);
+                G2[e][k] += __shfl_xor_sync(FULL, G2[e][k], 1);
+                G2[e][k] += __shfl_xor_sync(FULL, G2[e][k], 2);
+            }
+        float G3a[4][3];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) G3a[e][k] = __shfl_sync(FULL, G3[k], (lane & ~3) | e);
+#pragma unroll
+        for (int o = 0; o < 8; ++o) out[o][0] = out[o][1] = out[o][2] = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float g1 = G1[e][k] * a.ig[0], g2 = G2[e][k] * a.ig[1], g3 = G3a[e][k] * a.ig[2];
+                out[edge_corner(0, e, 1)][k] += g1;
+                out[edge_corner(0, e, 0)][k] -= g1;
+                out[edge_corner(1, e, 1)][k] += g2;
+                out[edge_corner(1, e, 0)][k] -= g2;
+                out[edge_corner(2, e, 1)][k] += g3;
+                out[edge_corner(2, e, 0)][k] -= g3;
+            }
+    }
+    if (cz_e == 0)
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) scell[cell][o][k] = valid ? out[o][k] : 0.f;
     __syncthreads();
     // gather per node of the box from the (up to) 8 cells of this tile
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     float *dst = a.boxes + (long)cta * 3 * a.box;
-    for (int i = tid; i < NB; i += 256) {
+    for (int i = tid; i < NB; i += NT) {
         const int bz = i / (BX * BY), r = i - bz * BX * BY, by = r / BX, bx = r - by * BX;
-        float acc[3] = {0.f, 0.f, 0.f};
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
         for (int o = 0; o < 8; ++o) {
             const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
             const int qx = bx - ox, qy = by - oy, qz = bz - oz;
             if (qx < 0 || qy < 0 || qz < 0 || qx >= TX || qy >= TY || qz >= TZ) continue;
-            const int cell = (qz * TY + qy) * TX + qx;
-            for (int k = 0; k < 3; ++k) acc[k] += scell[cell][o][k];
+            const int c = (qz * TY + qy) * TX + qx;
+            s0 += scell[c][o][0];
+            s1 += scell[c][o][1];
+            s2 += scell[c][o][2];
         }
-        for (int k = 0; k < 3; ++k) dst[k * a.box + i] = acc[k] * a.wscale;
+        dst[i] = s0 * a.wscale;
+        dst[a.box + i] = s1 * a.wscale;
+        dst[2 * a.box + i] = s2 * a.wscale;
     }
     if (VM == 0) {
         double t = block_sum(en.value());
         __shared__ int sfold;
-        __shared__ float smn, smx;
-        if (tid == 0) { sfold = 0; smn = 3.4e38f; smx = -3.4e38f; }
+        if (tid == 0) sfold = 0;
         __syncthreads();
         if (fold) atomicAdd(&sfold, fold);
-        // float min/max through the ordered-int trick is not needed: use a warp reduction
         for (int off = 16; off > 0; off >>= 1) {
-            dmn = fminf(dmn, __shfl_xor_sync(0xffffffffu, dmn, off));
-            dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, off));
+            dmn = fminf(dmn, __shfl_xor_sync(FULL, dmn, off));
+            dmx = fmaxf(dmx, __shfl_xor_sync(FULL, dmx, off));
         }
-        __shared__ float wmn[8], wmx[8];
+        __shared__ float wmn[NT / 32], wmx[NT / 32];
         if ((tid & 31) == 0) { wmn[tid >> 5] = dmn; wmx[tid >> 5] = dmx; }
         __syncthreads();
         if (tid == 0) {
             float mn = wmn[0], mxv = wmx[0];
-            for (int i = 1; i < 8; ++i) { mn = fminf(mn, wmn[i]); mxv = fmaxf(mxv, wmx[i]); }
+            for (int i = 1; i < NT / 32; ++i) { mn = fminf(mn, wmn[i]); mxv = fmaxf(mxv, wmx[i]); }
             a.epart[cta] = t;
             a.fold[cta] = sfold;
             a.dmin[cta] = mn;
@@ -280,35 +327,43 @@ __global__ void __launch_bounds__(256) vcc_kernel(const VccArgs a) {
 
 cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st) {
     dim3 grid(a.nb[0], a.nb[1], a.nb[2]);
-    if (a.diag) vcc_kernel<2><<<grid, 256, 0, st>>>(a);
-    else if (a.v) vcc_kernel<1><<<grid, 256, 0, st>>>(a);
-    else vcc_kernel<0><<<grid, 256, 0, st>>>(a);
+    constexpr int NT = 4 * kVccTile[0] * kVccTile[1] * kVccTile[2];
+    if (a.diag) vcc_kernel<2><<<grid, NT, 0, st>>>(a);
+    else if (a.v) vcc_kernel<1><<<grid, NT, 0, st>>>(a);
+    else vcc_kernel<0><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ finalize
-__device__ __forceinline__ float gather_boxes(const float *boxes, const BoxGeom &b, int comp, int kx, int ky, int kz) {
+// Sum, per component, the entries of node k in the (up to 8) CTA boxes holding it.
+__device__ __forceinline__ void sum_boxes(const float *boxes, const BoxGeom &b, int kx, int ky, int kz, float *out) {
     const int k[3] = {kx, ky, kz};
-    int cand[3][2], nc[3];
+    int c0[3], l0[3], nc[3];
+#pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        nc[ax] = 0;
+        // boxes hi - 1 and hi hold node k when 0 <= k - bb C <= C
         const int hi = k[ax] / b.C[ax];
-        for (int bb = hi - 1; bb <= hi; ++bb) {
-            const int l = k[ax] - bb * b.C[ax];
-            if (bb >= 0 && bb < b.nb[ax] && l >= 0 && l <= b.C[ax]) cand[ax][nc[ax]++] = bb;
-        }
+        const int lo = (hi - 1 >= 0 && k[ax] - (hi - 1) * b.C[ax] <= b.C[ax]) ? hi - 1 : hi;
+        const int top = min(hi, b.nb[ax] - 1);
+        c0[ax] = lo;
+        l0[ax] = k[ax] - lo * b.C[ax];
+        nc[ax] = top - lo + 1;
     }
     const int BX = b.C[0] + 1, BY = b.C[1] + 1;
-    float s = 0.f;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     for (int iz = 0; iz < nc[2]; ++iz)
         for (int iy = 0; iy < nc[1]; ++iy)
             for (int ix = 0; ix < nc[0]; ++ix) {
-                const int bx = cand[0][ix], by = cand[1][iy], bz = cand[2][iz];
-                const long cta = ((long)bz * b.nb[1] + by) * b.nb[0] + bx;
-                const int lx = kx - bx * b.C[0], ly = ky - by * b.C[1], lz = kz - bz * b.C[2];
-                s += boxes[(cta * 3 + comp) * b.box + (lz * BY + ly) * BX + lx];
+                const long cta = ((long)(c0[2] + iz) * b.nb[1] + (c0[1] + iy)) * b.nb[0] + (c0[0] + ix);
+                const long off = cta * 3 * b.box + ((l0[2] - iz * b.C[2]) * BY + (l0[1] - iy * b.C[1])) * BX +
+                                 (l0[0] - ix * b.C[0]);
+                s0 += boxes[off];
+                s1 += boxes[off + b.box];
+                s2 += boxes[off + 2 * (long)b.box];
             }
-    return s;
+    out[0] = s0;
+    out[1] = s1;
+    out[2] = s2;
 }
 
 __global__ void finalize_kernel(const FinalizeArgs a) {
@@ -316,25 +371,27 @@ __global__ void finalize_kernel(const FinalizeArgs a) {
     const long mxy = (long)mx * my, M = mxy * mz;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < M; k += (long)gridDim.x * blockDim.x) {
         const int kz = (int)(k / mxy), rem = (int)(k - kz * mxy), ky = rem / mx, kx = rem - ky * mx;
+        float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
+        if (a.boxA) sum_boxes(a.boxA, a.gA, kx, ky, kz, sa);
+        if (a.boxB) sum_boxes(a.boxB, a.gB, kx, ky, kz, sb);
+        const int kk[3] = {kx, ky, kz}, mm[3] = {mx, my, mz};
+        const long st[3] = {1, mx, mxy};
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float v = 0.f;
-            if (a.boxA) v += a.sA * gather_boxes(a.boxA, a.gA, c, kx, ky, kz);
-            if (a.boxB) v += a.sB * gather_boxes(a.boxB, a.gB, c, kx, ky, kz);
+            float v = a.sA * sa[c] + a.sB * sb[c];
             if (a.curv_w) {
                 // L^T w: rows of L that reference node k along each axis
                 const float *w = a.curv_w + c * M;
-                const int kk[3] = {kx, ky, kz}, mm[3] = {mx, my, mz};
-                const long st[3] = {1, mx, mxy};
-                float s = 0.f;
+                float t2 = 0.f;
+#pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
-                    const bool in0 = kk[ax] >= 1 && kk[ax] <= mm[ax] - 2;
                     float t = 0.f;
-                    if (in0) t -= 2.f * w[k];
+                    if (kk[ax] >= 1 && kk[ax] <= mm[ax] - 2) t -= 2.f * w[k];
                     if (kk[ax] - 1 >= 1) t += w[k - st[ax]];
                     if (kk[ax] + 1 <= mm[ax] - 2) t += w[k + st[ax]];
-                    s = fmaf(t, a.ig2[ax], s);
+                    t2 = fmaf(t, a.ig2[ax], t2);
                 }
-                v = fmaf(a.sC, s, v);
+                v = fmaf(a.sC, t2, v);
             }
             a.out[c * M + k] = v;
         }
