@@ -13,6 +13,10 @@ enum TileMode { MODE_OBJ = 0, MODE_LIN = 1, MODE_GRAD = 2, MODE_GRADLIN = 3, MOD
 size_t tile_smem_bytes(const TileGeom &g, int mode);
 cudaError_t launch_ngf_tile(int mode, const TileArgs<float> &a, cudaStream_t st);
 cudaError_t launch_ngf_tile(int mode, const TileArgs<__half> &a, cudaStream_t st);
+// Dedicated GN-product kernel (stored linearisation streamed by TMA); same
+// tile and node-box layout as MODE_MATVEC of the general kernel.
+bool gn_matvec_supported(const TileGeom &g);
+cudaError_t launch_gn_matvec(const TileArgs<float> &a, cudaStream_t st);
 
 // Curvature, Eq. (5): w = L u on nodes (and per-CTA partial sums of |w|^2).
 struct CurvArgs {

@@ -1,0 +1,56 @@
+// TMA and mbarrier helpers (inline PTX) shared by the NGF tile kernels.
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+namespace ngf {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a TMA plane: gives up after a fixed number of polls and
+// raises the error flag (when given) instead of hanging.
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err) {
+    for (int it = 0; !mbar_try_wait(bar, phase); ++it) {
+        if (it > (1 << 20)) {
+            if (err) atomicExch(err, 1);
+            break;
+        }
+    }
+}
+
+// 4-D tiled TMA load of box (x, y, z, c) into shared memory, completing on bar.
+// x * 4 bytes must be a multiple of 16; the other coordinates may lie outside
+// the tensor (zero fill).
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z,
+                                            int c) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace ngf

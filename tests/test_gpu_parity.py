@@ -74,6 +74,21 @@ def test_gn_matvec_random_vectors_tiny(tiny):
         assert rel_l2(Hv, L.matvec(v)) <= TOL_MV, seed
 
 
+@pytest.mark.parametrize("n,h,m", [((64, 64, 48), (1.0, 1.0, 2.5), (17, 17, 13)),
+                                   ((96, 48, 36), (0.8, 0.8, 2.5), (25, 13, 19))])
+def test_gn_matvec_dedicated_kernel_matches_general_kernel(n, h, m):
+    """Tile height 16 runs the dedicated GN-product kernel, height 8 the general one."""
+    ph = small_phantom(n, h, seed=4)
+    ctx = gpu_context(ph, m, gamma=0.001)
+    ctx.gn_linearize(to_dev(_u0(ph, m, 0.6)))
+    v = to_dev(phantom.random_grid_field(m, 21))
+    ctx.set_tile(8)
+    h8 = ctx.gn_matvec(v).cpu().numpy()
+    ctx.set_tile(16)
+    h16 = ctx.gn_matvec(v).cpu().numpy()
+    assert rel_l2(h16, h8) <= 1e-6
+
+
 def test_linearize_gradient_matches_plain_gradient(tiny):
     u = to_dev(_u0(tiny, TINY_M))
     ctx = gpu_context(tiny, TINY_M, gamma=0.001)
