@@ -154,10 +154,12 @@ int regularizer_apply(rg_ctx *ctx, int32_t which, const float *u_dev, const floa
  * linearisation, p0 = 0, iters <= pcg_max; stops early only if r.z or p.Hp
  * stop being positive.  Each new residual is reorthogonalised against all
  * earlier preconditioned residuals (classical Gram-Schmidt): the iterates of
- * plain PCG in exact arithmetic, kept so in FP32.  Preconditioner: the diagonal of H, with the NGF part taken
+ * plain PCG in exact arithmetic, kept so in FP32.  Preconditioner: the
+ * diagonal of H, with the NGF part taken
  * without the cross terms of the central-difference adjoint
  * (2 hbar sum_x w_k(x)^2 dT_c(x)^2 sum_a (a_{x-e_a,a}^2 + a_{x+e_a,a}^2)/(4 h_a^2)),
- * plus tau; non-positive entries use 1.
+ * plus tau; non-positive entries use 1.  g_dev and p_dev must be 16-byte
+ * aligned (cudaMalloc and PyTorch allocations are), else RG_EINVAL.
  * stats_dev: double[3] = {steps, |r0|, |r_end|} (may be NULL). */
 int gn_pcg_solve(rg_ctx *ctx, const float *g_dev, float *p_dev, int32_t iters, double *stats_dev);
 

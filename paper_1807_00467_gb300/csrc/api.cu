@@ -39,11 +39,11 @@ struct rg_ctx {
     int *fold;
     float *dmin, *dmax;
     float *minv, *d, *q, *tg_, *tu, *ts;
-    float *Rh, *Zh;           // PCG residual / preconditioned residual history, pcg_max + 1 slots
-    int *tma_err;             // set by the kernels if a bounded TMA wait gave up
+    float *Rh;                // PCG residual history, pcg_max + 1 slots of pcg_stride(3 M) floats
+    int *tma_err;             // [0]: set by the kernels if a bounded TMA wait gave up; [1]: PCG ticket
     bool err_zeroed;
     CUtensorMap map_dT, map_a;
-    double *rzh, *coef, *mdpart;
+    double *rzh, *coef, *pcgpart;
     PcgScalars *sc;
     bool has_lin, minv_valid;
     char err[512];
@@ -227,18 +227,17 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->dmin = cv.take<float>(c->nB);
     c->dmax = cv.take<float>(c->nB);
     c->minv = cv.take<float>(3 * M);
-    c->Rh = cv.take<float>(3 * M * (size_t)(c->pcg_max + 1));
-    c->Zh = cv.take<float>(3 * M * (size_t)(c->pcg_max + 1));
+    c->Rh = cv.take<float>(pcg_stride(3 * M) * (size_t)(c->pcg_max + 1));
     c->rzh = cv.take<double>(c->pcg_max + 1);
     c->coef = cv.take<double>(c->pcg_max + 1);
-    c->mdpart = cv.take<double>((size_t)c->nV * (c->pcg_max + 1));
+    c->pcgpart = cv.take<double>((size_t)pcg_blocks(3 * M) * (c->pcg_max + 2));
     c->d = cv.take<float>(3 * M);
     c->q = cv.take<float>(3 * M);
     c->tg_ = cv.take<float>(3 * M);
     c->tu = cv.take<float>(3 * M);
     c->ts = cv.take<float>(3 * M);
     c->sc = cv.take<PcgScalars>(1);
-    c->tma_err = cv.take<int>(1);
+    c->tma_err = cv.take<int>(2);
 }
 
 static void derive(rg_ctx *c) {
@@ -435,7 +434,7 @@ extern "C" int rg_set_keypoints(rg_ctx *c, int32_t nk, const float *x, const flo
 static int run_tile(rg_ctx *c, int mode, const float *field) {
     if (!c->R || !c->T) return set_err(c, RG_EINVAL, "images not set");
     if (!c->err_zeroed) {
-        CK(cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->st));
+        CK(cudaMemsetAsync(c->tma_err, 0, 2 * sizeof(int), c->st));
         c->err_zeroed = true;
     }
     auto fill = [&](auto &a) {
@@ -703,35 +702,42 @@ __global__ void pcg_stats_kernel(const PcgScalars *sc, double *stats) {
     stats[2] = sc->rend;
 }
 
-// PCG with full reorthogonalisation (classical Gram-Schmidt against all
-// earlier preconditioned residuals); same iterates as plain PCG in exact
-// arithmetic, kept so in FP32.  Scalars, dots and coefficients in FP64.
+// PCG with full reorthogonalisation (classical Gram-Schmidt of each new
+// residual against all earlier ones in the preconditioner's inner product);
+// same iterates as plain PCG in exact arithmetic, kept so in FP32.  Scalars,
+// dots and coefficients in FP64.
 static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
     if (iters > c->pcg_max)
         return set_err(c, RG_EINVAL, "PCG: %d steps requested, the workspace holds %d (pcg_max)", iters, c->pcg_max);
+    if (((uintptr_t)g | (uintptr_t)p) & 15)
+        return set_err(c, RG_EINVAL, "PCG: g and p must be 16-byte aligned");
     int st;
     if ((st = ensure_minv(c))) return st;
-    const long n = 3 * c->M;
-    const long stride = 3 * c->M;
-    const int nb = vec_blocks(n);
-    LAUNCH(9, launch_pcg_scalar(5, nullptr, 0, c->sc, c->st));
-    LAUNCH(9, launch_dot(n, g, g, c->vecpart, c->st));
-    LAUNCH(9, launch_pcg_scalar(3, c->vecpart, nb, c->sc, c->st));
-    LAUNCH(9, launch_pcg_init(n, g, c->minv, p, c->Rh, c->Zh, c->d, c->vecpart, c->st));
-    LAUNCH(9, launch_pcg_scalar(0, c->vecpart, nb, c->sc, c->st, c->rzh));
-    for (int k = 0; k < iters; ++k) {
-        float *rk = c->Rh + k * stride, *rn = c->Rh + (k + 1) * stride, *zn = c->Zh + (k + 1) * stride;
-        if ((st = matvec(c, c->d, c->q))) return st;
-        LAUNCH(9, launch_dot(n, c->d, c->q, c->vecpart, c->st));
-        LAUNCH(9, launch_pcg_scalar(1, c->vecpart, nb, c->sc, c->st));
-        LAUNCH(9, launch_pcg_step(n, c->sc, c->d, c->q, rk, p, rn, c->st));
-        LAUNCH(9, launch_multidot(n, rn, c->Zh, stride, k + 1, c->mdpart, c->st));
-        LAUNCH(9, launch_reorth_coef(c->mdpart, nb, k + 1, c->rzh, c->sc, c->coef, c->st));
-        LAUNCH(9, launch_reorth_update(n, rn, c->Rh, stride, k + 1, c->coef, c->minv, zn, c->vecpart, c->st));
-        LAUNCH(9, launch_pcg_scalar(2, c->vecpart, nb, c->sc, c->st, c->rzh));
-        LAUNCH(9, launch_pcg_dir(n, c->sc, zn, c->d, c->st));
+    if (!c->err_zeroed) {
+        CK(cudaMemsetAsync(c->tma_err, 0, 2 * sizeof(int), c->st));
+        c->err_zeroed = true;
     }
-    LAUNCH(9, launch_dot_slot(n, c->Rh, stride, c->sc, c->vecpart, c->st));
+    PcgArgs a;
+    a.n = 3 * c->M;
+    a.stride = pcg_stride(a.n);
+    a.minv = c->minv;
+    a.Rh = c->Rh;
+    a.d = c->d;
+    a.part = c->pcgpart;
+    a.ticket = reinterpret_cast<unsigned *>(c->tma_err + 1);
+    a.sc = c->sc;
+    a.rzh = c->rzh;
+    a.coef = c->coef;
+    LAUNCH(9, launch_pcg_start(a, g, p, c->st));
+    for (int k = 0; k < iters; ++k) {
+        if ((st = matvec(c, c->d, c->q))) return st;
+        LAUNCH(9, launch_pcg_alpha(a, c->q, c->st));
+        LAUNCH(9, launch_pcg_step(a, c->q, p, k, c->st));
+        LAUNCH(9, launch_pcg_reorth(a, k, c->st));
+        LAUNCH(9, launch_pcg_dir(a, k, c->st));
+    }
+    const int nb = vec_blocks(a.n);
+    LAUNCH(9, launch_dot_slot(a.n, c->Rh, a.stride, c->sc, c->vecpart, c->st));
     LAUNCH(9, launch_pcg_scalar(4, c->vecpart, nb, c->sc, c->st));
     if (stats) {
         ProfScope ps_(c, 9);

@@ -95,26 +95,32 @@ cudaError_t launch_jacobi_diag(int alpha_on, const int *m, const float *ig2, dou
 cudaError_t launch_kp_diag(const int *m, const float *ig, int nk, const float *kx, double two_delta, float *diag,
                            cudaStream_t st);
 cudaError_t launch_invert(long n, float *d, cudaStream_t st);
-cudaError_t launch_pcg_init(long n, const float *g, const float *minv, float *s, float *r, float *z, float *d,
-                            double *part, cudaStream_t st);
 cudaError_t launch_dot(long n, const float *x, const float *y, double *part, cudaStream_t st);
 cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScalars *sc, cudaStream_t st,
                               double *rzh = nullptr);
-// Reorthogonalised PCG: residual history R_j, preconditioned residuals Z_j
-// (slots of `stride` floats), coefficients c_j = r.z_j / r_j.z_j.
-cudaError_t launch_pcg_step(long n, const PcgScalars *sc, const float *d, const float *q, const float *r, float *s,
-                            float *rn, cudaStream_t st);
-cudaError_t launch_multidot(long n, const float *r, const float *Z, long stride, int count, double *part,
-                            cudaStream_t st);
-cudaError_t launch_reorth_coef(const double *part, int nb, int count, const double *rzh, const PcgScalars *sc,
-                               double *coef, cudaStream_t st);
-cudaError_t launch_reorth_update(long n, float *r, const float *Rh, long stride, int count, const double *coef,
-                                 const float *minv, float *z, double *part, cudaStream_t st);
 cudaError_t launch_dot_slot(long n, const float *Rh, long stride, const PcgScalars *sc, double *part,
                             cudaStream_t st);
-cudaError_t launch_pcg_update(long n, const PcgScalars *sc, const float *d, const float *q, const float *minv,
-                              float *s, float *r, float *z, double *part, cudaStream_t st);
-cudaError_t launch_pcg_dir(long n, const PcgScalars *sc, const float *z, float *d, cudaStream_t st);
+
+// Reorthogonalised PCG (float4 streams, FP64 partials reduced by the last
+// block).  Residual history r_0..r_k in slots of `stride` floats.
+struct PcgArgs {
+    long n, stride;        // vector length, history slot stride (pcg_stride(n))
+    const float *minv;     // inverse preconditioner diagonal
+    float *Rh;             // residual history
+    float *d;              // search direction
+    double *part;          // partials: (RG_PCG_MAX + 2) x pcg_blocks(n)
+    unsigned *ticket;      // last-block ticket (zero between launches)
+    PcgScalars *sc;
+    double *rzh;           // r_j . z_j
+    double *coef;          // Gram-Schmidt coefficients
+};
+int pcg_blocks(long n);
+long pcg_stride(long n);
+cudaError_t launch_pcg_start(const PcgArgs &a, const float *g, float *s, cudaStream_t st);
+cudaError_t launch_pcg_alpha(const PcgArgs &a, const float *q, cudaStream_t st);
+cudaError_t launch_pcg_step(const PcgArgs &a, const float *q, float *s, int k, cudaStream_t st);
+cudaError_t launch_pcg_reorth(const PcgArgs &a, int k, cudaStream_t st);
+cudaError_t launch_pcg_dir(const PcgArgs &a, int k, cudaStream_t st);
 cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, float *y, cudaStream_t st);
 
 // Pyramid.

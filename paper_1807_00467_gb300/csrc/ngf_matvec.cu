@@ -11,10 +11,16 @@
 // The layout follows the general NGF tile kernel (lane = x column, warp = y
 // row, 2-voxel halo, a chunk of TZ planes marched in z) with the GN-product
 // specialisation:
-//  - dT/dy and a of every plane arrive by TMA into a 6-stage ring (3 planes
+//  - dT/dy and a of every plane arrive by TMA into a 4-stage ring (3 planes
 //    ahead); planes outside the volume are zero-filled by the TMA unit, and a
 //    is zero on the volume's boundary voxels, so no voxel needs a predicate:
 //    zeros propagate to exactly the terms the adjoint leaves out;
+//  - stage W reads both fields of its plane once; stages C and A take them
+//    from registers one and two planes later, so a stage is free as soon as
+//    stage W is done with it;
+//  - the plane loop is unrolled by the ring depth: stage offsets, exchange
+//    buffers and (for rho_z <= 4) the prolongation weights are constants, and
+//    the per-plane register rings are renamings;
 //  - one barrier per plane: the y-neighbour exchanges of t (for stage C) and
 //    of c_y (for stage A) both use a double-buffered row written at the end of
 //    the previous plane;
@@ -36,38 +42,33 @@ namespace {
 constexpr int kTY = 16;                   // voxel rows per tile
 constexpr int kNW = kTY + 4;              // warps (rows incl. the 2-row halos)
 constexpr int kNT = 32 * kNW;
-constexpr int kStages = 6;                // TMA ring depth (planes)
+constexpr int kStages = 4;                // TMA ring depth (planes) = loop unroll
 constexpr int kAhead = 3;                 // planes in flight ahead of stage W
 constexpr int kBoxF = ((kTmaBoxX * kNW * 3 * 4 + 127) / 128) * 32;   // floats per box, 128-byte padded
 constexpr int kStageF = 2 * kBoxF;        // dT/dy box, then a box
 constexpr int kComp = kNW * kTmaBoxX;     // floats between components in a box
+constexpr int kEx = kNW * 32;             // floats per exchange row buffer
 constexpr uint32_t kPlaneBytes = 2u * kTmaBoxX * kNW * 3 * 4;
 
 struct MvSmem {
-    int tma, ext, exc, nodes, rows, xr, total;
+    int tma, ext, exc, wtab, nodes, rows, xr, total;
 };
 
 __host__ __device__ inline MvSmem mv_smem(const TileGeom &g) {
     MvSmem s;
     int off = 0;
     s.tma = off; off += kStages * kStageF + 32;          // + 128 bytes to align the base
-    s.ext = off; off += 2 * kNW * 32;                     // t of plane C, double-buffered
-    s.exc = off; off += 2 * kNW * 32;                     // c_y of plane A, double-buffered
-    s.nodes = off; off += g.nzt * 3 * g.nxt * g.nyt;      // node planes of P v
+    s.ext = off; off += 2 * kEx;                          // t of plane C, double-buffered
+    s.exc = off; off += 2 * kEx;                          // c'_y of plane A, double-buffered
+    s.wtab = off; off += 32;                              // hat weights along x [0, 16) and y [16, 32)
+    s.nodes = off; off += g.nzt * g.nyt * g.nxt * 4;      // node planes of v, [plane][y][x][xyz_]
     s.rows = off; off += (g.C[2] + 1) * kTY * g.TXI * 3;  // z-reduced column sums per node plane
     s.xr = (g.C[2] + 1) * kTY * (g.C[0] + 1) * 3;         // x-reduced sums (reuse the TMA ring)
     s.total = off;
     return s;
 }
 
-}  // namespace
-
-bool gn_matvec_supported(const TileGeom &g) {
-    if (!g.tma || g.TY != kTY || g.nzt <= 0 || g.rho[0] < 2) return false;
-    const MvSmem s = mv_smem(g);
-    return s.xr <= kStages * kStageF && (size_t)s.total * sizeof(float) <= 227u * 1024u;
-}
-
+template <int RZ>
 __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant__ TileArgs<float> a) {
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) float smem[];
@@ -86,11 +87,12 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 
     float *tma_base = smem + S.tma + ((128u - (smem_u32(smem + S.tma) & 127u)) & 127u) / 4;
-    float *ext = smem + S.ext, *exc = smem + S.exc, *s_nodes = smem + S.nodes, *rows = smem + S.rows;
+    float *rows = smem + S.rows, *wtab = smem + S.wtab;
+    float4 *s_nodes = reinterpret_cast<float4 *>(smem + S.nodes);
 
     // plane j of the chunk's sequence (voxel plane z0 - 2 + j) into stage j % kStages
     auto issue_plane = [&](int j) {
-        const int st = j % kStages;
+        const int st = j & (kStages - 1);
         float *dst = tma_base + st * kStageF;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bars[st], kPlaneBytes);
@@ -103,20 +105,30 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
         for (int j = 0; j < kAhead && j < nsteps; ++j) issue_plane(j);
     }
 
-    // node planes of v for P v (zero beyond the grid)
-    const int nxt = g.nxt, nyt = g.nyt, nzt = g.nzt, nplane = nxt * nyt;
-    const int kx_lo = max(x0 - 2, 0) >> lrx, ky_lo = max(y0 - 2, 0) >> lry, kz_lo = max(z0 - 2, 0) >> lrz;
+    // node planes of v for P v, from floor((z0 - 2) / rho_z) on (zero outside the grid)
+    const int nxt = g.nxt, nyt = g.nyt, nplane = nxt * nyt;
+    const int kx_lo = max(x0 - 2, 0) >> lrx, ky_lo = max(y0 - 2, 0) >> lry, kz_lo = (z0 - 2) >> lrz;
     {
         const long mxy = (long)g.m[0] * g.m[1], Mn = mxy * g.m[2];
-        for (int i = tid; i < nzt * 3 * nplane; i += kNT) {
-            const int pl = i / nplane, r = i - pl * nplane;   // pl = plane * 3 + comp
-            const int kz = kz_lo + pl / 3, comp = pl - (pl / 3) * 3;
+        for (int i = tid; i < g.nzt * nplane; i += kNT) {
+            const int pl = i / nplane, r = i - pl * nplane;
             const int ly = r / nxt, lx = r - ly * nxt;
-            const int ux = kx_lo + lx, uy = ky_lo + ly;
-            float v = 0.f;
-            if (ux < g.m[0] && uy < g.m[1] && kz < g.m[2]) v = __ldg(a.u + comp * Mn + (long)kz * mxy + (long)uy * g.m[0] + ux);
+            const int ux = kx_lo + lx, uy = ky_lo + ly, kz = kz_lo + pl;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ux < g.m[0] && uy < g.m[1] && kz >= 0 && kz < g.m[2]) {
+                const long q = (long)kz * mxy + (long)uy * g.m[0] + ux;
+                v.x = __ldg(a.u + q);
+                v.y = __ldg(a.u + Mn + q);
+                v.z = __ldg(a.u + 2 * Mn + q);
+            }
             s_nodes[i] = v;
         }
+    }
+    // hat weight of node j for the column (row) (j - 1) rho + i, i in [0, 2 rho)
+    if (tid < 32) {
+        const int ax = tid >> 4, i = tid & 15, r = g.rho[ax];
+        const float f = ((i & (r - 1)) + 0.5f) * g.irho[ax];
+        wtab[tid] = i < r ? f : (i < 2 * r ? 1.f - f : 0.f);
     }
 
     // this column's bilinear position in the node tile (clamped: columns
@@ -125,151 +137,168 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
     const int cxg = gx >> lrx, cyg = gy >> lry;
     const float fx = ((gx - (cxg << lrx)) + 0.5f) * g.irho[0];
     const float fy = ((gy - (cyg << lry)) + 0.5f) * g.irho[1];
-    const float *qcol = s_nodes + min(max(cyg - ky_lo, 0), nyt - 2) * nxt + min(max(cxg - kx_lo, 0), nxt - 2);
-    auto bilinear = [&](int kz, int comp) {
-        const float *q = qcol + ((kz - kz_lo) * 3 + comp) * nplane;
-        const float lo = fmaf(fx, q[1] - q[0], q[0]);
-        const float hi = fmaf(fx, q[nxt + 1] - q[nxt], q[nxt]);
-        return fmaf(fy, hi - lo, lo);
+    const float4 *qcol = s_nodes + min(max(cyg - ky_lo, 0), nyt - 2) * nxt + min(max(cxg - kx_lo, 0), nxt - 2);
+    auto bilinear = [&](int kz, float *U) {
+        const float4 *q = qcol + (kz - kz_lo) * nplane;
+        const float4 n00 = q[0], n10 = q[1], n01 = q[nxt], n11 = q[nxt + 1];
+        float lo = fmaf(fx, n10.x - n00.x, n00.x), hi = fmaf(fx, n11.x - n01.x, n01.x);
+        U[0] = fmaf(fy, hi - lo, lo);
+        lo = fmaf(fx, n10.y - n00.y, n00.y); hi = fmaf(fx, n11.y - n01.y, n01.y);
+        U[1] = fmaf(fy, hi - lo, lo);
+        lo = fmaf(fx, n10.z - n00.z, n00.z); hi = fmaf(fx, n11.z - n01.z, n01.z);
+        U[2] = fmaf(fy, hi - lo, lo);
     };
 
     const float i2h0 = g.inv2h[0], i2h1 = g.inv2h[1], i2h2 = g.inv2h[2];
-    const bool rowC = w >= 1 && w < kNW - 1;          // rows whose c is needed
-    const bool rowA = w >= 2 && w < kTY + 2;          // rows owned by the tile
-    const bool colA = L >= 2 && L < TXI + 2;          // columns owned by the tile
-    const int o = w * kTmaBoxX + L + 2;               // this column in a TMA box
-    const int ex_me = w * 32 + L;
+    const bool own_col = w >= 2 && w < kTY + 2 && L >= 2 && L < TXI + 2;   // tile-owned column
+    const float *sbase = tma_base + w * kTmaBoxX + L + 2;                  // this column in a TMA box
+    // y-neighbours in the exchange rows (the outermost rows read themselves; unused)
+    float *ex_t = smem + S.ext + w * 32 + L, *ex_c = smem + S.exc + w * 32 + L;
+    const int up = w > 0 ? -32 : 0, dn = w < kNW - 1 ? 32 : 0;
+    float *rowp = rows + ((w - 2) * TXI + (L - 2)) * 3;    // + node plane * kTY * TXI * 3
 
-    float U0[3] = {0.f, 0.f, 0.f}, D[3] = {0.f, 0.f, 0.f};   // P v at node planes cz, cz + 1 (x-y interpolated)
-    int cur_cz = -1000;
-    float tm = 0.f, t0 = 0.f;          // t at planes pC - 1, pC
-    float cxp = 0.f;                   // c'_x at plane pA (from the previous plane's stage C)
-    float czm2 = 0.f, czm1 = 0.f;      // c'_z at planes pA - 1, pA
+    __syncthreads();
+
+    float U0[3], U1[3], D[3];   // P v at node planes cz, cz + 1 (x-y interpolated), D = U1 - U0
+    {
+        const int cz = (z0 - 2) >> lrz;
+        bilinear(cz, U0);
+        bilinear(cz + 1, U1);
+        for (int k = 0; k < 3; ++k) D[k] = U1[k] - U0[k];
+    }
+    float tm = 0.f, t0 = 0.f;                  // t at planes pC - 1, pC
+    float a1[3] = {0.f, 0.f, 0.f};             // a' at plane pC (read by stage W one plane earlier)
+    float d1[3] = {0.f, 0.f, 0.f}, d2[3] = {0.f, 0.f, 0.f};   // dT/dy at planes pW - 1 (= pC), pW - 2 (= pA)
+    float cxp = 0.f;                           // c'_x at plane pA (from the previous plane's stage C)
+    float czm2 = 0.f, czm1 = 0.f;              // c'_z at planes pA - 1, pA
     float acc0[3] = {0.f, 0.f, 0.f}, acc1[3] = {0.f, 0.f, 0.f};   // z-node planes czl, czl + 1
 
-    int stW = 0;            // stage of plane s
-    uint32_t phW = 0;       // its phase parity
-    for (int s = 0; s < nsteps; ++s) {
-        const int pW = z0 - 2 + s, pA = pW - 2;
-        const int b = s & 1;
-        const int stC = stW == 0 ? kStages - 1 : stW - 1;
-        const int stA = stC == 0 ? kStages - 1 : stC - 1;
-        // the stage of plane s - 3 was last read before this barrier (at s = 0 it
-        // publishes the barrier initialisation and the node planes)
-        __syncthreads();
-        if (tid == 0 && s + kAhead < nsteps) issue_plane(s + kAhead);
-
-        // ------------------------------------------------ P v at plane pW (node planes on change)
-        const int cz = min(max(pW >> lrz, kz_lo), kz_lo + nzt - 2);
-        if (cz != cur_cz) {
+    uint32_t phase = 0;
+    for (int s0 = 0; s0 < nsteps; s0 += kStages, phase ^= 1u) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float u0 = cz == cur_cz + 1 ? U0[k] + D[k] : bilinear(cz, k);
-                const float u1 = bilinear(cz + 1, k);
-                U0[k] = u0;
-                D[k] = u1 - u0;
+        for (int j = 0; j < kStages; ++j) {
+            const int s = s0 + j;
+            if (s >= nsteps) break;
+            const int pW = z0 - 2 + s;
+            // z phase of planes pW and pA = pW - 2 within their cells (z0 is a
+            // multiple of rho_z; so is s0 when rho_z divides the ring depth)
+            const int phW = RZ ? ((j - 2) & (RZ - 1)) : (pW & rzm);
+            const int phA = RZ ? (j & (RZ - 1)) : ((pW - 2) & rzm);
+            const float fz = RZ ? (phW + 0.5f) / (float)(RZ ? RZ : 1) : (phW + 0.5f) * irz;
+            const float wz1 = RZ ? (phA + 0.5f) / (float)(RZ ? RZ : 1) : (phA + 0.5f) * irz;
+
+            // the stage of plane s - 1 was last read before this barrier
+            __syncthreads();
+            if (tid == 0 && s + kAhead < nsteps) issue_plane(s + kAhead);
+
+            // ------------------------------------------------ P v: next node plane at a cell start
+            if (phW == 0 && s > 0) {
+                U0[0] = U1[0]; U0[1] = U1[1]; U0[2] = U1[2];
+                bilinear((pW >> lrz) + 1, U1);
+                D[0] = U1[0] - U0[0]; D[1] = U1[1] - U0[1]; D[2] = U1[2] - U0[2];
             }
-            cur_cz = cz;
-        }
-        const float fz = ((pW & rzm) + 0.5f) * irz;
 
-        mbar_wait_bounded(&bars[stW], phW, a.err);
-        const float *sW = tma_base + stW * kStageF;
-        // ------------------------------------------------ stage W: t at plane pW
-        const float tp = sW[o] * fmaf(fz, D[0], U0[0]) + sW[kComp + o] * fmaf(fz, D[1], U0[1]) +
-                         sW[2 * kComp + o] * fmaf(fz, D[2], U0[2]);
+            mbar_wait_bounded(&bars[j], phase, a.err);
+            // ------------------------------------------------ stage W: t at plane pW
+            const float *sW = sbase + j * kStageF;
+            const float dw0 = sW[0], dw1 = sW[kComp], dw2 = sW[2 * kComp];
+            const float aw0 = sW[kBoxF] * i2h0, aw1 = sW[kBoxF + kComp] * i2h1, aw2 = sW[kBoxF + 2 * kComp] * i2h2;
+            const float tp = fmaf(dw2, fmaf(fz, D[2], U0[2]), fmaf(dw1, fmaf(fz, D[1], U0[1]), dw0 * fmaf(fz, D[0], U0[0])));
 
-        // ------------------------------------------------ stage C: c' at plane pC = pW - 1
-        float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-        {
+            // ------------------------------------------------ stage C: c' at plane pC = pW - 1
+            const int b = (j & 1) * kEx;
             const float txl = __shfl_up_sync(FULL, t0, 1), txr = __shfl_down_sync(FULL, t0, 1);
-            if (rowC) {
-                const float *e = ext + b * kNW * 32 + ex_me;
-                const float *sC = tma_base + stC * kStageF + kBoxF;
-                const float a0 = sC[o] * i2h0, a1 = sC[kComp + o] * i2h1, a2 = sC[2 * kComp + o] * i2h2;
-                const float dr = fmaf(a2, tp - tm, fmaf(a1, e[32] - e[-32], a0 * (txr - txl)));
-                c0 = dr * a0;
-                c1 = dr * a1;
-                c2 = dr * a2;
-            }
-        }
-        // ------------------------------------------------ stage A: G^T c at plane pA, times dT/dy
-        {
+            const float dr = fmaf(a1[2], tp - tm, fmaf(a1[1], ex_t[b + dn] - ex_t[b + up], a1[0] * (txr - txl)));
+            const float c0 = dr * a1[0], c1 = dr * a1[1], c2 = dr * a1[2];
+
+            // ------------------------------------------------ stage A: G^T c at plane pA = pW - 2, times dT/dy
             const float cxl = __shfl_up_sync(FULL, cxp, 1), cxr = __shfl_down_sync(FULL, cxp, 1);
-            if (rowA && pA >= z0) {
-                const float *e = exc + b * kNW * 32 + ex_me;
-                const float bsum = (cxl - cxr) + (e[-32] - e[32]) + (czm2 - c2);
-                const float *sA = tma_base + stA * kStageF;
-                const int zl = pA - z0, ph = zl & rzm;
-                const float wz1 = (ph + 0.5f) * irz;
+            if (j >= 4 || s0 > 0) {   // planes of the chunk (pA >= z0)
+                const float bsum = (cxl - cxr) + (ex_c[b + up] - ex_c[b + dn]) + (czm2 - c2);
                 const float b1 = wz1 * bsum, b0 = bsum - b1;
-                const float d0 = sA[o], d1 = sA[kComp + o], d2 = sA[2 * kComp + o];
-                acc0[0] = fmaf(b0, d0, acc0[0]); acc0[1] = fmaf(b0, d1, acc0[1]); acc0[2] = fmaf(b0, d2, acc0[2]);
-                acc1[0] = fmaf(b1, d0, acc1[0]); acc1[1] = fmaf(b1, d1, acc1[1]); acc1[2] = fmaf(b1, d2, acc1[2]);
-                if (ph == rzm) {
-                    // node plane zl >> lrz is complete for this column: park it
-                    if (colA) {
-                        float *r = rows + (((zl >> lrz) * kTY + (w - 2)) * TXI + (L - 2)) * 3;
+                acc0[0] = fmaf(b0, d2[0], acc0[0]); acc0[1] = fmaf(b0, d2[1], acc0[1]); acc0[2] = fmaf(b0, d2[2], acc0[2]);
+                acc1[0] = fmaf(b1, d2[0], acc1[0]); acc1[1] = fmaf(b1, d2[1], acc1[1]); acc1[2] = fmaf(b1, d2[2], acc1[2]);
+                if (phA == (RZ ? RZ - 1 : rzm)) {
+                    // node plane (pA - z0) / rho_z is complete for this column: park it
+                    if (own_col) {
+                        float *r = rowp + ((s - 4) >> lrz) * (kTY * TXI * 3);
                         r[0] = acc0[0]; r[1] = acc0[1]; r[2] = acc0[2];
                     }
                     acc0[0] = acc1[0]; acc0[1] = acc1[1]; acc0[2] = acc1[2];
                     acc1[0] = acc1[1] = acc1[2] = 0.f;
                 }
             }
+            // ------------------------------------------------ hand over to the next plane
+            ex_t[kEx - b] = tp;
+            ex_c[kEx - b] = c1;
+            tm = t0; t0 = tp;
+            czm2 = czm1; czm1 = c2;
+            cxp = c0;
+            d2[0] = d1[0]; d2[1] = d1[1]; d2[2] = d1[2];
+            d1[0] = dw0; d1[1] = dw1; d1[2] = dw2;
+            a1[0] = aw0; a1[1] = aw1; a1[2] = aw2;
         }
-        // ------------------------------------------------ hand over to the next plane
-        ext[(b ^ 1) * kNW * 32 + ex_me] = tp;
-        exc[(b ^ 1) * kNW * 32 + ex_me] = c1;
-        tm = t0; t0 = tp;
-        czm2 = czm1; czm1 = c2;
-        cxp = c0;
-        if (++stW == kStages) { stW = 0; phW ^= 1u; }
     }
     // the node plane above the chunk's last cell
-    if (rowA && colA) {
-        float *r = rows + (((TZc >> lrz) * kTY + (w - 2)) * TXI + (L - 2)) * 3;
+    if (own_col) {
+        float *r = rowp + (TZc >> lrz) * (kTY * TXI * 3);
         r[0] = acc0[0]; r[1] = acc0[1]; r[2] = acc0[2];
     }
     __syncthreads();
 
     // ---------------------------------------------------- x then y reduction onto the CTA's node box
-    const int CX = g.C[0], CY = g.C[1], rxm = g.rho[0] - 1, rym = g.rho[1] - 1;
+    const int CX = g.C[0], CY = g.C[1], rx = g.rho[0], ry = g.rho[1];
     const int nplanes = (TZc >> lrz) + 1;
     float *xr = tma_base;   // [plane][ty][jx][comp]; every TMA copy has completed
-    for (int e = tid; e < nplanes * kTY * (CX + 1) * 3; e += kNT) {
-        const int k = e % 3, t1 = e / 3, jx = t1 % (CX + 1), t2 = t1 / (CX + 1);   // t2 = plane * kTY + ty
-        const int lo = max(0, (jx - 1) << lrx), hi = min(TXI, (jx + 1) << lrx);
-        const float *r = rows + (long)t2 * TXI * 3 + k;
-        float v = 0.f;
-        for (int tx = lo; tx < hi; ++tx) {
-            float wx = ((tx & rxm) + 0.5f) * g.irho[0];
-            if ((tx >> lrx) == jx) wx = 1.f - wx;
-            v = fmaf(wx, r[tx * 3], v);
+    for (int r = w; r < nplanes * kTY; r += kNW) {
+        const float *src = rows + r * TXI * 3;
+        for (int o = L; o < (CX + 1) * 3; o += 32) {
+            const int jx = o / 3, k = o - 3 * jx;
+            const int ilo = jx == 0 ? rx : 0, ihi = jx == CX ? rx : 2 * rx;
+            const float *p = src + ((jx - 1) * rx) * 3 + k;
+            float v = 0.f;
+            for (int i = ilo; i < ihi; ++i) v = fmaf(wtab[i], p[3 * i], v);
+            xr[r * (CX + 1) * 3 + o] = v;
         }
-        xr[e] = v;
     }
     __syncthreads();
-    for (int e = tid; e < 3 * nplanes * (CY + 1) * (CX + 1); e += kNT) {
-        const int jx = e % (CX + 1), t1 = e / (CX + 1), jy = t1 % (CY + 1), t2 = t1 / (CY + 1);
-        const int jz = t2 % nplanes, comp = t2 / nplanes;
-        const int lo = max(0, (jy - 1) << lry), hi = min(kTY, (jy + 1) << lry);
-        float v = 0.f;
-        for (int ty = lo; ty < hi; ++ty) {
-            float wy = ((ty & rym) + 0.5f) * g.irho[1];
-            if ((ty >> lry) == jy) wy = 1.f - wy;
-            v = fmaf(wy, xr[((jz * kTY + ty) * (CX + 1) + jx) * 3 + comp], v);
+    for (int r = w; r < 3 * nplanes * (CY + 1); r += kNW) {
+        const int jy = r % (CY + 1), t1 = r / (CY + 1), jz = t1 % nplanes, comp = t1 / nplanes;
+        const int ilo = jy == 0 ? ry : 0, ihi = jy == CY ? ry : 2 * ry;
+        float *dst = a.boxes + ((long)cta * 3 + comp) * g.box + (jz * (CY + 1) + jy) * (CX + 1);
+        for (int jx = L; jx <= CX; jx += 32) {
+            const float *p = xr + ((jz * kTY + (jy - 1) * ry) * (CX + 1) + jx) * 3 + comp;
+            float v = 0.f;
+            for (int i = ilo; i < ihi; ++i) v = fmaf(wtab[16 + i], p[i * (CX + 1) * 3], v);
+            dst[jx] = 2.f * v;
         }
-        a.boxes[((long)cta * 3 + comp) * g.box + (jz * (CY + 1) + jy) * (CX + 1) + jx] = 2.f * v;
     }
+}
+
+}  // namespace
+
+bool gn_matvec_supported(const TileGeom &g) {
+    if (!g.tma || g.TY != kTY || g.nzt <= 0 || g.rho[0] < 2) return false;
+    const MvSmem s = mv_smem(g);
+    return s.xr <= kStages * kStageF && (size_t)s.total * sizeof(float) <= 227u * 1024u;
 }
 
 cudaError_t launch_gn_matvec(const TileArgs<float> &a, cudaStream_t st) {
     if (!gn_matvec_supported(a.g)) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * (size_t)mv_smem(a.g).total;
-    cudaError_t e = cudaFuncSetAttribute(gn_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    gn_matvec_kernel<<<dim3(a.g.nb[0], a.g.nb[1], a.g.nb[2]), kNT, smem, st>>>(a);
-    return cudaGetLastError();
+    const dim3 grid(a.g.nb[0], a.g.nb[1], a.g.nb[2]);
+    auto run = [&](auto kernel) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, kNT, smem, st>>>(a);
+        return cudaGetLastError();
+    };
+    switch (a.g.rho[2]) {
+        case 1: return run(gn_matvec_kernel<1>);
+        case 2: return run(gn_matvec_kernel<2>);
+        case 4: return run(gn_matvec_kernel<4>);
+        default: return run(gn_matvec_kernel<0>);   // rho_z = 8: phases from the plane index
+    }
 }
 
 }  // namespace ngf

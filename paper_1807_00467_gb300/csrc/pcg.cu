@@ -1,0 +1,371 @@
+// Vector kernels of the reorthogonalised PCG (Sec. II-D: the Gauss-Newton
+// system is solved by preconditioned conjugate gradients).
+//
+// Every kernel streams the node vectors as float4 with the same partition:
+// block b owns quads [b Q, (b + 1) Q), Q = 256 qpt, thread t its quads
+// b Q + i 256 + t (i < qpt <= kQmax), so each thread keeps up to kQmax
+// independent 16-byte loads in flight per stream.  Per-block partial sums are
+// FP64; the block that finishes last (atomic ticket, no waiting) reduces them
+// in a fixed order and updates the device scalars, so no separate scalar
+// kernels run and the result does not depend on block scheduling.
+//
+// The preconditioner is diagonal, so z_j = M^-1 r_j is not stored: the
+// Gram-Schmidt coefficients use r . z_j = (M^-1 r) . r_j.
+#include "ngfreg.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ngf {
+
+namespace {
+
+constexpr int kVT = 256;            // threads per block
+constexpr int kVW = kVT / 32;
+constexpr int kQmax = 8;            // quads per thread at most
+constexpr int kHist = RG_PCG_MAX + 1;
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+
+// Block sum of a per-thread value; the result is valid in thread 0.
+__device__ __forceinline__ double block_total(double v, double *red) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kVW; ++i) t += red[i];
+    __syncthreads();
+    return t;
+}
+
+// Sum of part[0..n) in a fixed order (lane-strided, then a fixed shuffle
+// tree) by one warp; valid in every lane.
+__device__ __forceinline__ double warp_sum_parts(const double *part, int n) {
+    double s = 0.0;
+    for (int i = threadIdx.x & 31; i < n; i += 32) s += __ldcg(part + i);
+    return warp_sum(s);
+}
+
+// True in the block that arrives last (after every block has published its
+// partials); that block resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        is_last = t == gridDim.x - 1;
+        if (is_last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
+struct Part {
+    long n4;   // whole quads
+    int tail;  // trailing floats (n % 4), handled by block 0
+    int qpt;   // quads per thread
+    __device__ __forceinline__ long quad(int i) const {
+        return ((long)blockIdx.x * qpt + i) * kVT + threadIdx.x;
+    }
+};
+
+__device__ __forceinline__ float4 ldg4(const float *p, long q) { return reinterpret_cast<const float4 *>(p)[q]; }
+__device__ __forceinline__ void st4(float *p, long q, float4 v) { reinterpret_cast<float4 *>(p)[q] = v; }
+
+// ---------------------------------------------------------------------------
+// start: s = 0, r_0 = -g, d = z_0 = M^-1 r_0; scalars reset, |g|, r_0 . z_0
+__global__ void __launch_bounds__(kVT) pcg_start_kernel(Part P, const float *g, const float *minv, float *s, float *r,
+                                                        float *d, double *part, unsigned *ticket, PcgScalars *sc,
+                                                        double *rzh) {
+    __shared__ double red[kVW];
+    const int nb = gridDim.x;
+    float gg = 0.f, rz = 0.f;
+#pragma unroll
+    for (int i = 0; i < kQmax; ++i) {
+        const long q = P.quad(i);
+        if (i < P.qpt && q < P.n4) {
+            const float4 gv = ldg4(g, q), m = ldg4(minv, q);
+            const float4 rv = make_float4(-gv.x, -gv.y, -gv.z, -gv.w);
+            const float4 zv = make_float4(m.x * rv.x, m.y * rv.y, m.z * rv.z, m.w * rv.w);
+            st4(s, q, make_float4(0.f, 0.f, 0.f, 0.f));
+            st4(r, q, rv);
+            st4(d, q, zv);
+            gg += dot4(gv, gv);
+            rz += dot4(rv, zv);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < P.tail) {
+        const long e = 4 * P.n4 + threadIdx.x;
+        const float rv = -g[e], zv = minv[e] * rv;
+        s[e] = 0.f; r[e] = rv; d[e] = zv;
+        gg = fmaf(rv, rv, gg);
+        rz = fmaf(rv, zv, rz);
+    }
+    const double tg = block_total((double)gg, red);
+    const double tr = block_total((double)rz, red);
+    if (threadIdx.x == 0) { part[blockIdx.x] = tg; part[nb + blockIdx.x] = tr; }
+    if (!last_block(ticket)) return;
+    if (threadIdx.x < 64) {
+        const double v = warp_sum_parts(part + (threadIdx.x >> 5) * nb, nb);
+        if (threadIdx.x == 0) {
+            sc->pq = sc->alpha = sc->beta = sc->rend = sc->rz_new = 0.0;
+            sc->stop = 0;
+            sc->steps = 0;
+            sc->r0 = sqrt(v);
+        }
+        if (threadIdx.x == 32) {
+            sc->rz = v;
+            rzh[0] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// d . q, then alpha = r.z / d.q (stop on a non-positive curvature d.q or a
+// vanishing r.z)
+__global__ void __launch_bounds__(kVT) pcg_alpha_kernel(Part P, const float *d, const float *q, double *part,
+                                                        unsigned *ticket, PcgScalars *sc) {
+    __shared__ double red[kVW];
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < kQmax; ++i) {
+        const long k = P.quad(i);
+        if (i < P.qpt && k < P.n4) acc += dot4(ldg4(d, k), ldg4(q, k));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < P.tail) {
+        const long e = 4 * P.n4 + threadIdx.x;
+        acc = fmaf(d[e], q[e], acc);
+    }
+    const double t = block_total((double)acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (!last_block(ticket)) return;
+    if (threadIdx.x < 32) {
+        const double v = warp_sum_parts(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            sc->pq = v;
+            if (sc->stop || !(sc->rz != 0.0) || !(v > 0.0)) { sc->stop = 1; sc->alpha = 0.0; }
+            else sc->alpha = sc->rz / v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// s += alpha d;  r_{k+1} = r_k - alpha q;  then the Gram-Schmidt coefficients
+// c_j = (M^-1 r_{k+1}) . r_j / (r_j . z_j), j = 0..k
+__global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars *sc, const float *d, const float *q,
+                                                       const float *minv, float *s, float *Rh, long stride,
+                                                       int k, double *part, unsigned *ticket, const double *rzh,
+                                                       double *coef) {
+    __shared__ double wp[kHist][kVW];
+    const int nb = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float al = (float)sc->alpha;
+    const float *r = Rh + (long)k * stride;
+    float *rn = Rh + (long)(k + 1) * stride;
+    float4 zn[kQmax];
+#pragma unroll
+    for (int i = 0; i < kQmax; ++i) {
+        const long e = P.quad(i);
+        zn[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < P.qpt && e < P.n4) {
+            const float4 dv = ldg4(d, e), qv = ldg4(q, e), rv = ldg4(r, e), m = ldg4(minv, e);
+            float4 sv = ldg4(s, e);
+            sv.x = fmaf(al, dv.x, sv.x); sv.y = fmaf(al, dv.y, sv.y); sv.z = fmaf(al, dv.z, sv.z); sv.w = fmaf(al, dv.w, sv.w);
+            const float4 nv = make_float4(fmaf(-al, qv.x, rv.x), fmaf(-al, qv.y, rv.y), fmaf(-al, qv.z, rv.z),
+                                          fmaf(-al, qv.w, rv.w));
+            st4(s, e, sv);
+            st4(rn, e, nv);
+            zn[i] = make_float4(m.x * nv.x, m.y * nv.y, m.z * nv.z, m.w * nv.w);
+        }
+    }
+    float zt = 0.f;
+    const bool tail = blockIdx.x == 0 && threadIdx.x < P.tail;
+    const long et = 4 * P.n4 + threadIdx.x;
+    if (tail) {
+        s[et] = fmaf(al, d[et], s[et]);
+        const float nv = fmaf(-al, q[et], r[et]);
+        rn[et] = nv;
+        zt = minv[et] * nv;
+    }
+    for (int j = 0; j <= k; ++j) {
+        const float *rj = Rh + (long)j * stride;
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < kQmax; ++i) {
+            const long e = P.quad(i);
+            if (i < P.qpt && e < P.n4) acc += dot4(zn[i], ldg4(rj, e));
+        }
+        if (tail) acc = fmaf(zt, rj[et], acc);
+        const double v = warp_sum((double)acc);
+        if (lane == 0) wp[j][warp] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j <= k; j += kVT) {
+        double t = 0.0;
+        for (int w = 0; w < kVW; ++w) t += wp[j][w];
+        part[(long)j * nb + blockIdx.x] = t;
+    }
+    if (!last_block(ticket)) return;
+    for (int j = warp; j <= k; j += kVW) {
+        const double v = warp_sum_parts(part + (long)j * nb, nb);
+        if (lane == 0) coef[j] = (sc->stop || rzh[j] == 0.0) ? 0.0 : v / rzh[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// r_{k+1} -= sum_j c_j r_j;  then r.z with z = M^-1 r_{k+1} -> beta
+__global__ void __launch_bounds__(kVT, 3) pcg_reorth_kernel(Part P, const float *minv, float *Rh, long stride, int k,
+                                                         const double *coef, double *part, unsigned *ticket,
+                                                         PcgScalars *sc, double *rzh) {
+    __shared__ float c[kHist];
+    __shared__ double red[kVW];
+    for (int j = threadIdx.x; j <= k; j += kVT) c[j] = (float)coef[j];
+    __syncthreads();
+    float *r = Rh + (long)(k + 1) * stride;
+    float4 rv[kQmax];
+#pragma unroll
+    for (int i = 0; i < kQmax; ++i) {
+        const long e = P.quad(i);
+        rv[i] = (i < P.qpt && e < P.n4) ? ldg4(r, e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const bool tail = blockIdx.x == 0 && threadIdx.x < P.tail;
+    const long et = 4 * P.n4 + threadIdx.x;
+    float rt = tail ? r[et] : 0.f;
+    for (int j = 0; j <= k; ++j) {
+        const float *rj = Rh + (long)j * stride;
+        const float cj = c[j];
+#pragma unroll
+        for (int i = 0; i < kQmax; ++i) {
+            const long e = P.quad(i);
+            if (i < P.qpt && e < P.n4) {
+                const float4 x = ldg4(rj, e);
+                rv[i].x = fmaf(-cj, x.x, rv[i].x); rv[i].y = fmaf(-cj, x.y, rv[i].y);
+                rv[i].z = fmaf(-cj, x.z, rv[i].z); rv[i].w = fmaf(-cj, x.w, rv[i].w);
+            }
+        }
+        if (tail) rt = fmaf(-cj, rj[et], rt);
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < kQmax; ++i) {
+        const long e = P.quad(i);
+        if (i < P.qpt && e < P.n4) {
+            const float4 m = ldg4(minv, e);
+            st4(r, e, rv[i]);
+            acc += dot4(rv[i], make_float4(m.x * rv[i].x, m.y * rv[i].y, m.z * rv[i].z, m.w * rv[i].w));
+        }
+    }
+    if (tail) {
+        r[et] = rt;
+        acc = fmaf(rt, minv[et] * rt, acc);
+    }
+    const double t = block_total((double)acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (!last_block(ticket)) return;
+    if (threadIdx.x < 32) {
+        const double v = warp_sum_parts(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            sc->rz_new = v;
+            if (sc->stop) {
+                sc->beta = 0.0;
+            } else {
+                sc->beta = v / sc->rz;
+                sc->rz = v;
+                sc->steps += 1;
+                rzh[sc->steps] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// d = M^-1 r_{k+1} + beta d
+__global__ void __launch_bounds__(kVT) pcg_dir_kernel(Part P, const PcgScalars *sc, const float *minv, const float *r,
+                                                      float *d) {
+    const float be = (float)sc->beta;
+#pragma unroll
+    for (int i = 0; i < kQmax; ++i) {
+        const long e = P.quad(i);
+        if (i < P.qpt && e < P.n4) {
+            const float4 m = ldg4(minv, e), rv = ldg4(r, e), dv = ldg4(d, e);
+            st4(d, e, make_float4(fmaf(be, dv.x, m.x * rv.x), fmaf(be, dv.y, m.y * rv.y), fmaf(be, dv.z, m.z * rv.z),
+                                  fmaf(be, dv.w, m.w * rv.w)));
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < P.tail) {
+        const long e = 4 * P.n4 + threadIdx.x;
+        d[e] = fmaf(be, d[e], minv[e] * r[e]);
+    }
+}
+
+Part make_part(long n, int *nb) {
+    Part P;
+    P.n4 = n / 4;
+    P.tail = (int)(n % 4);
+    // blocks: a multiple of the SM count with at most kQmax quads per thread
+    const long per_wave = 152L * kVT * kQmax;
+    const long waves = P.n4 > 0 ? (P.n4 + per_wave - 1) / per_wave : 1;
+    *nb = (int)(152 * waves);
+    P.qpt = (int)((P.n4 + (long)*nb * kVT - 1) / ((long)*nb * kVT));
+    if (P.qpt < 1) P.qpt = 1;
+    return P;
+}
+
+}  // namespace
+
+int pcg_blocks(long n) {
+    int nb;
+    make_part(n, &nb);
+    return nb;
+}
+
+long pcg_stride(long n) { return (n + 63) / 64 * 64; }
+
+cudaError_t launch_pcg_start(const PcgArgs &a, const float *g, float *s, cudaStream_t st) {
+    int nb;
+    const Part P = make_part(a.n, &nb);
+    pcg_start_kernel<<<nb, kVT, 0, st>>>(P, g, a.minv, s, a.Rh, a.d, a.part, a.ticket, a.sc, a.rzh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_alpha(const PcgArgs &a, const float *q, cudaStream_t st) {
+    int nb;
+    const Part P = make_part(a.n, &nb);
+    pcg_alpha_kernel<<<nb, kVT, 0, st>>>(P, a.d, q, a.part, a.ticket, a.sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_step(const PcgArgs &a, const float *q, float *s, int k, cudaStream_t st) {
+    if (k < 0 || k + 1 >= kHist) return cudaErrorInvalidValue;
+    int nb;
+    const Part P = make_part(a.n, &nb);
+    pcg_step_kernel<<<nb, kVT, 0, st>>>(P, a.sc, a.d, q, a.minv, s, a.Rh, a.stride, k, a.part, a.ticket, a.rzh,
+                                        a.coef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_reorth(const PcgArgs &a, int k, cudaStream_t st) {
+    if (k < 0 || k + 1 >= kHist) return cudaErrorInvalidValue;
+    int nb;
+    const Part P = make_part(a.n, &nb);
+    pcg_reorth_kernel<<<nb, kVT, 0, st>>>(P, a.minv, a.Rh, a.stride, k, a.coef, a.part, a.ticket, a.sc, a.rzh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_dir(const PcgArgs &a, int k, cudaStream_t st) {
+    int nb;
+    const Part P = make_part(a.n, &nb);
+    pcg_dir_kernel<<<nb, kVT, 0, st>>>(P, a.sc, a.minv, a.Rh + (long)(k + 1) * a.stride, a.d);
+    return cudaGetLastError();
+}
+
+}  // namespace ngf

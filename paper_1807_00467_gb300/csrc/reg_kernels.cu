@@ -593,28 +593,6 @@ cudaError_t launch_invert(long n, float *d, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-__global__ void pcg_init_kernel(long n, const float *g, const float *minv, float *s, float *r, float *z, float *d,
-                                double *part) {
-    Kahan acc;
-    GRID_STRIDE(i, n) {
-        const float ri = -g[i];
-        const float zi = minv[i] * ri;
-        s[i] = 0.f;
-        r[i] = ri;
-        z[i] = zi;
-        d[i] = zi;
-        acc.add(ri * zi);
-    }
-    double t = block_sum(acc.value());
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-cudaError_t launch_pcg_init(long n, const float *g, const float *minv, float *s, float *r, float *z, float *d,
-                            double *part, cudaStream_t st) {
-    pcg_init_kernel<<<vec_blocks(n), 256, 0, st>>>(n, g, minv, s, r, z, d, part);
-    return cudaGetLastError();
-}
-
 __global__ void dot_kernel(long n, const float *x, const float *y, double *part) {
     Kahan acc;
     GRID_STRIDE(i, n) acc.add(x[i] * y[i]);
@@ -668,99 +646,6 @@ cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScal
     return cudaGetLastError();
 }
 
-__global__ void pcg_update_kernel(long n, const PcgScalars *sc, const float *d, const float *q, const float *minv,
-                                  float *s, float *r, float *z, double *part) {
-    const float al = (float)sc->alpha;
-    Kahan acc;
-    GRID_STRIDE(i, n) {
-        const float ri = fmaf(-al, q[i], r[i]);
-        const float zi = minv[i] * ri;
-        s[i] = fmaf(al, d[i], s[i]);
-        r[i] = ri;
-        z[i] = zi;
-        acc.add(ri * zi);
-    }
-    double t = block_sum(acc.value());
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-cudaError_t launch_pcg_update(long n, const PcgScalars *sc, const float *d, const float *q, const float *minv, float *s,
-                              float *r, float *z, double *part, cudaStream_t st) {
-    pcg_update_kernel<<<vec_blocks(n), 256, 0, st>>>(n, sc, d, q, minv, s, r, z, part);
-    return cudaGetLastError();
-}
-
-// s += alpha d; r_next = r - alpha q  (reads alpha from the device scalars)
-__global__ void pcg_step_kernel(long n, const PcgScalars *sc, const float *d, const float *q, const float *r,
-                                float *s, float *rn) {
-    const float al = (float)sc->alpha;
-    GRID_STRIDE(i, n) {
-        s[i] = fmaf(al, d[i], s[i]);
-        rn[i] = fmaf(-al, q[i], r[i]);
-    }
-}
-
-cudaError_t launch_pcg_step(long n, const PcgScalars *sc, const float *d, const float *q, const float *r, float *s,
-                            float *rn, cudaStream_t st) {
-    pcg_step_kernel<<<vec_blocks(n), 256, 0, st>>>(n, sc, d, q, r, s, rn);
-    return cudaGetLastError();
-}
-
-// part[j * gridDim.x + b] = partial of r . Z_j over the chunk of block b, j = blockIdx.y
-__global__ void multidot_kernel(long n, const float *r, const float *Z, long stride, double *part) {
-    const float *z = Z + blockIdx.y * stride;
-    Kahan acc;
-    GRID_STRIDE(i, n) acc.add(r[i] * z[i]);
-    double t = block_sum(acc.value());
-    if (threadIdx.x == 0) part[(long)blockIdx.y * gridDim.x + blockIdx.x] = t;
-}
-
-cudaError_t launch_multidot(long n, const float *r, const float *Z, long stride, int count, double *part,
-                            cudaStream_t st) {
-    dim3 grid(vec_blocks(n), count);
-    multidot_kernel<<<grid, 256, 0, st>>>(n, r, Z, stride, part);
-    return cudaGetLastError();
-}
-
-// c_j = (r . z_j) / (r_j . z_j), j < count; 0 when r_j . z_j = 0 or the solve stopped
-__global__ void reorth_coef_kernel(const double *part, int nb, int count, const double *rzh, const PcgScalars *sc,
-                                   double *coef) {
-    const int j = blockIdx.x;
-    double v = sum_parts(part + (long)j * nb, nb);
-    if (threadIdx.x == 0) coef[j] = (sc->stop || rzh[j] == 0.0) ? 0.0 : v / rzh[j];
-}
-
-cudaError_t launch_reorth_coef(const double *part, int nb, int count, const double *rzh, const PcgScalars *sc,
-                               double *coef, cudaStream_t st) {
-    reorth_coef_kernel<<<count, 256, 0, st>>>(part, nb, count, rzh, sc, coef);
-    return cudaGetLastError();
-}
-
-// r -= sum_j c_j R_j; z = minv r; partial r . z
-__global__ void reorth_update_kernel(long n, float *r, const float *Rh, long stride, int count, const double *coef,
-                                     const float *minv, float *z, double *part) {
-    __shared__ float c[64];
-    for (int j = threadIdx.x; j < count; j += blockDim.x) c[j] = (float)coef[j];
-    __syncthreads();
-    Kahan acc;
-    GRID_STRIDE(i, n) {
-        float ri = r[i];
-        for (int j = 0; j < count; ++j) ri = fmaf(-c[j], Rh[j * stride + i], ri);
-        const float zi = minv[i] * ri;
-        r[i] = ri;
-        z[i] = zi;
-        acc.add(ri * zi);
-    }
-    double t = block_sum(acc.value());
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-cudaError_t launch_reorth_update(long n, float *r, const float *Rh, long stride, int count, const double *coef,
-                                 const float *minv, float *z, double *part, cudaStream_t st) {
-    reorth_update_kernel<<<vec_blocks(n), 256, 0, st>>>(n, r, Rh, stride, count, coef, minv, z, part);
-    return cudaGetLastError();
-}
-
 // |r_steps|^2 partials, the residual of the last completed step
 __global__ void dot_slot_kernel(long n, const float *Rh, long stride, const PcgScalars *sc, double *part) {
     const float *r = Rh + (long)sc->steps * stride;
@@ -773,16 +658,6 @@ __global__ void dot_slot_kernel(long n, const float *Rh, long stride, const PcgS
 cudaError_t launch_dot_slot(long n, const float *Rh, long stride, const PcgScalars *sc, double *part,
                             cudaStream_t st) {
     dot_slot_kernel<<<vec_blocks(n), 256, 0, st>>>(n, Rh, stride, sc, part);
-    return cudaGetLastError();
-}
-
-__global__ void pcg_dir_kernel(long n, const PcgScalars *sc, const float *z, float *d) {
-    const float be = (float)sc->beta;
-    GRID_STRIDE(i, n) d[i] = fmaf(be, d[i], z[i]);
-}
-
-cudaError_t launch_pcg_dir(long n, const PcgScalars *sc, const float *z, float *d, cudaStream_t st) {
-    pcg_dir_kernel<<<vec_blocks(n), 256, 0, st>>>(n, sc, z, d);
     return cudaGetLastError();
 }
 

@@ -74,8 +74,10 @@ def test_gn_matvec_random_vectors_tiny(tiny):
         assert rel_l2(Hv, L.matvec(v)) <= TOL_MV, seed
 
 
-@pytest.mark.parametrize("n,h,m", [((64, 64, 48), (1.0, 1.0, 2.5), (17, 17, 13)),
-                                   ((96, 48, 36), (0.8, 0.8, 2.5), (25, 13, 19))])
+@pytest.mark.parametrize("n,h,m", [((64, 64, 48), (1.0, 1.0, 2.5), (17, 17, 13)),    # rho_z 4
+                                   ((96, 48, 36), (0.8, 0.8, 2.5), (25, 13, 19)),    # rho_z 2, chunk tail
+                                   ((48, 40, 24), (1.2, 1.2, 2.0), (25, 21, 25)),    # rho_z 1
+                                   ((64, 48, 64), (1.0, 1.0, 1.5), (9, 7, 9))])      # rho 8
 def test_gn_matvec_dedicated_kernel_matches_general_kernel(n, h, m):
     """Tile height 16 runs the dedicated GN-product kernel, height 8 the general one."""
     ph = small_phantom(n, h, seed=4)
@@ -137,6 +139,7 @@ def test_keypoint_objective_gradient_matvec():
     ((64, 32, 16), (1.0, 1.3, 2.5), (9, 5, 3)),       # rho 8
     ((12, 12, 8), (2.0, 2.0, 3.0), (13, 13, 9)),      # rho 1
     ((96, 48, 36), (0.8, 0.8, 2.5), (25, 13, 19)),    # rho (4, 4, 2), chunk tail
+    ((48, 40, 24), (1.2, 1.2, 2.0), (25, 21, 25)),    # rho (2, 2, 1)
 ])
 def test_shapes_and_ratios(n, h, m):
     ph = small_phantom(n, h, seed=5)
