@@ -46,6 +46,7 @@ struct VccArgs {
 };
 constexpr int kVccTile[3] = {8, 4, 4};
 cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st);
+cudaError_t launch_vcc_cells(const VccArgs &a, cudaStream_t st);   // gradient / GN product (a.diag == 0)
 
 // Sum node boxes of up to two box sets and optionally the curvature adjoint.
 struct FinalizeArgs {

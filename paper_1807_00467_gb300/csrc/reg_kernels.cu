@@ -328,9 +328,8 @@ __global__ void __launch_bounds__(4 * kVccTile[0] * kVccTile[1] * kVccTile[2], 1
 cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st) {
     dim3 grid(a.nb[0], a.nb[1], a.nb[2]);
     constexpr int NT = 4 * kVccTile[0] * kVccTile[1] * kVccTile[2];
-    if (a.diag) vcc_kernel<2><<<grid, NT, 0, st>>>(a);
-    else if (a.v) vcc_kernel<1><<<grid, NT, 0, st>>>(a);
-    else vcc_kernel<0><<<grid, NT, 0, st>>>(a);
+    if (!a.diag) return launch_vcc_cells(a, st);   // gradient and GN product: one thread per cell
+    vcc_kernel<2><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
