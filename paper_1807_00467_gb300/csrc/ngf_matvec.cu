@@ -51,7 +51,7 @@ constexpr int kEx = kNW * 32;             // floats per exchange row buffer
 constexpr uint32_t kPlaneBytes = 2u * kTmaBoxX * kNW * 3 * 4;
 
 struct MvSmem {
-    int tma, ext, exc, wtab, nodes, rows, xr, total;
+    int tma, ext, exc, nodes, rows, xr, total;
 };
 
 __host__ __device__ inline MvSmem mv_smem(const TileGeom &g) {
@@ -60,12 +60,45 @@ __host__ __device__ inline MvSmem mv_smem(const TileGeom &g) {
     s.tma = off; off += kStages * kStageF + 32;          // + 128 bytes to align the base
     s.ext = off; off += 2 * kEx;                          // t of plane C, double-buffered
     s.exc = off; off += 2 * kEx;                          // c'_y of plane A, double-buffered
-    s.wtab = off; off += 32;                              // hat weights along x [0, 16) and y [16, 32)
     s.nodes = off; off += g.nzt * g.nyt * g.nxt * 4;      // node planes of v, [plane][y][x][xyz_]
     s.rows = off; off += (g.C[2] + 1) * kTY * g.TXI * 3;  // z-reduced column sums per node plane
     s.xr = (g.C[2] + 1) * kTY * (g.C[0] + 1) * 3;         // x-reduced sums (reuse the TMA ring)
     s.total = off;
     return s;
+}
+
+// P^T along one axis for node j and every node plane p < np:
+// dst[p dpl] = scale sum_i w_i src[p spl + (j - 1) R + i] (source index times sstride),
+// i in [0, 2R), with the trilinear hat weights w_i of the ratio R and the
+// source indices outside [0, nsrc) left out.
+template <int R>
+__device__ __forceinline__ void hat_sum(const float *src, int sstride, int spl, int j, int nsrc, float *dst, int dpl,
+                                        int np, float scale) {
+    float w[2 * R];
+    int off[2 * R];
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) {
+        const int c = (j - 1) * R + i;
+        w[i] = (c >= 0 && c < nsrc) ? (i < R ? (i + 0.5f) / R : 1.f - (i - R + 0.5f) / R) : 0.f;
+        off[i] = min(max(c, 0), nsrc - 1) * sstride;
+    }
+    for (int p = 0; p < np; ++p) {
+        const float *q = src + p * spl;
+        float v = 0.f;
+#pragma unroll
+        for (int i = 0; i < 2 * R; ++i) v = fmaf(w[i], q[off[i]], v);
+        dst[p * dpl] = scale * v;
+    }
+}
+
+__device__ __forceinline__ void hat_sum_any(int R, const float *src, int sstride, int spl, int j, int nsrc, float *dst,
+                                            int dpl, int np, float scale) {
+    switch (R) {
+        case 1: hat_sum<1>(src, sstride, spl, j, nsrc, dst, dpl, np, scale); break;
+        case 2: hat_sum<2>(src, sstride, spl, j, nsrc, dst, dpl, np, scale); break;
+        case 4: hat_sum<4>(src, sstride, spl, j, nsrc, dst, dpl, np, scale); break;
+        default: hat_sum<8>(src, sstride, spl, j, nsrc, dst, dpl, np, scale); break;
+    }
 }
 
 template <int RZ>
@@ -87,7 +120,7 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 
     float *tma_base = smem + S.tma + ((128u - (smem_u32(smem + S.tma) & 127u)) & 127u) / 4;
-    float *rows = smem + S.rows, *wtab = smem + S.wtab;
+    float *rows = smem + S.rows;
     float4 *s_nodes = reinterpret_cast<float4 *>(smem + S.nodes);
 
     // plane j of the chunk's sequence (voxel plane z0 - 2 + j) into stage j % kStages
@@ -123,12 +156,6 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
             }
             s_nodes[i] = v;
         }
-    }
-    // hat weight of node j for the column (row) (j - 1) rho + i, i in [0, 2 rho)
-    if (tid < 32) {
-        const int ax = tid >> 4, i = tid & 15, r = g.rho[ax];
-        const float f = ((i & (r - 1)) + 0.5f) * g.irho[ax];
-        wtab[tid] = i < r ? f : (i < 2 * r ? 1.f - f : 0.f);
     }
 
     // this column's bilinear position in the node tile (clamped: columns
@@ -247,30 +274,26 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
     __syncthreads();
 
     // ---------------------------------------------------- x then y reduction onto the CTA's node box
-    const int CX = g.C[0], CY = g.C[1], rx = g.rho[0], ry = g.rho[1];
+    // (each thread keeps one (row, node, component) and walks the node planes)
+    const int CX = g.C[0], CY = g.C[1];
     const int nplanes = (TZc >> lrz) + 1;
     float *xr = tma_base;   // [plane][ty][jx][comp]; every TMA copy has completed
-    for (int r = w; r < nplanes * kTY; r += kNW) {
-        const float *src = rows + r * TXI * 3;
-        for (int o = L; o < (CX + 1) * 3; o += 32) {
-            const int jx = o / 3, k = o - 3 * jx;
-            const int ilo = jx == 0 ? rx : 0, ihi = jx == CX ? rx : 2 * rx;
-            const float *p = src + ((jx - 1) * rx) * 3 + k;
-            float v = 0.f;
-            for (int i = ilo; i < ihi; ++i) v = fmaf(wtab[i], p[3 * i], v);
-            xr[r * (CX + 1) * 3 + o] = v;
-        }
+    for (int e = tid; e < kTY * (CX + 1) * 3; e += kNT) {
+        const int k = e % 3, t = e / 3, jx = t % (CX + 1), ty = t / (CX + 1);
+        const float *src = rows + ty * TXI * 3 + k;
+        float *dst = xr + (ty * (CX + 1) + jx) * 3 + k;
+        hat_sum_any(g.rho[0], src, 3, kTY * TXI * 3, jx, TXI, dst, kTY * (CX + 1) * 3, nplanes, 1.f);
     }
     __syncthreads();
-    for (int r = w; r < 3 * nplanes * (CY + 1); r += kNW) {
-        const int jy = r % (CY + 1), t1 = r / (CY + 1), jz = t1 % nplanes, comp = t1 / nplanes;
-        const int ilo = jy == 0 ? ry : 0, ihi = jy == CY ? ry : 2 * ry;
-        float *dst = a.boxes + ((long)cta * 3 + comp) * g.box + (jz * (CY + 1) + jy) * (CX + 1);
-        for (int jx = L; jx <= CX; jx += 32) {
-            const float *p = xr + ((jz * kTY + (jy - 1) * ry) * (CX + 1) + jx) * 3 + comp;
-            float v = 0.f;
-            for (int i = ilo; i < ihi; ++i) v = fmaf(wtab[16 + i], p[i * (CX + 1) * 3], v);
-            dst[jx] = 2.f * v;
+    {
+        const int nc = (CY + 1) * (CX + 1) * 3, G = max(1, kNT / nc);
+        for (int e = tid; e < nc * G; e += kNT) {
+            const int c = e % nc, pg = e / nc;
+            const int k = c % 3, t = c / 3, jx = t % (CX + 1), jy = t / (CX + 1);
+            const float *src = xr + pg * kTY * (CX + 1) * 3 + jx * 3 + k;
+            float *dst = a.boxes + ((long)cta * 3 + k) * g.box + (pg * (CY + 1) + jy) * (CX + 1) + jx;
+            hat_sum_any(g.rho[1], src, (CX + 1) * 3, G * kTY * (CX + 1) * 3, jy, kTY, dst, G * (CY + 1) * (CX + 1),
+                        (nplanes - pg + G - 1) / G, 2.f);
         }
     }
 }
