@@ -42,7 +42,7 @@ WORKLOAD = "512x512x128 FP32, 0.7x0.7x2.5 mm, grid 129x129x65, eta=10 alpha=1 ga
 
 # kernel ids of rg_profile_read
 K_MATVEC, K_GRADLIN, K_OBJ, K_VCC, K_VCC_GN, K_CURV, K_FIN, K_KP, K_TERMS, K_VEC, K_OTHER = range(11)
-KNAMES = {K_MATVEC: "ngf_tile_matvec", K_GRADLIN: "ngf_tile_grad_lin", K_OBJ: "ngf_tile_obj", K_VCC: "vcc_grad",
+KNAMES = {K_MATVEC: "gn_matvec", K_GRADLIN: "ngf_tile_grad_lin", K_OBJ: "ngf_tile_obj", K_VCC: "vcc_grad",
           K_VCC_GN: "vcc_gn", K_CURV: "curv_L", K_FIN: "finalize_nodes", K_KP: "keypoints", K_TERMS: "terms",
           K_VEC: "pcg_vector", K_OTHER: "other"}
 
@@ -83,12 +83,17 @@ def alg_bytes(kernel, N, M):
     return None
 
 
-def recorded_traffic(kernel_name):
+# source file of each timed kernel (the recorded ncu traffic is used only while it is unchanged)
+KSRC = {K_MATVEC: "ngf_matvec.cu", K_GRADLIN: "ngf_tile.cu", K_OBJ: "ngf_tile.cu", K_VCC: "vcc.cu", K_VCC_GN: "vcc.cu",
+        K_CURV: "reg_kernels.cu", K_FIN: "reg_kernels.cu", K_VEC: "pcg.cu"}
+
+
+def recorded_traffic(kernel):
     """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", f"{kernel_name}_full.md")
-    src = os.path.join(ROOT, "paper_1807_00467_gb300", "csrc", "ngf_tile.cu")
-    if not os.path.exists(path):
+    path = os.path.join(ROOT, "profiles", f"{KNAMES[kernel]}_full.md")
+    if kernel not in KSRC or not os.path.exists(path):
         return None
+    src = os.path.join(ROOT, "paper_1807_00467_gb300", "csrc", KSRC[kernel])
     sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
     traffic, src_sha = None, None
     for line in open(path):
@@ -292,7 +297,7 @@ def run_ours(args):
         if ab is not None:
             ach = ab / (t / cnt / 1e3) / 1e9
             roof = {"bound": "hbm", "kernel": KNAMES[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "peak_source": peak_kind, "traffic": recorded_traffic(KNAMES[dom]),
+                    "frac": ach / peak, "peak_source": peak_kind, "traffic": recorded_traffic(dom),
                     "alg_bytes_per_launch": ab, "avg_launch_us": 1e3 * t / cnt, "share": t / ms}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
