@@ -268,7 +268,7 @@ static void derive(rg_ctx *c) {
     c->bA.box = c->tg.box;
     c->bB.box = (kVccTile[0] + 1) * (kVccTile[1] + 1) * (kVccTile[2] + 1);
     c->nB = c->bB.nb[0] * c->bB.nb[1] * c->bB.nb[2];
-    c->nR = curv_blocks(c->grid.m);
+    c->nR = node_blocks(c->grid.m);
     c->nKb = kp_blocks(c->nk_max > 0 ? c->nk_max : 1);
     c->nV = vec_blocks(3 * c->M);
 }
@@ -496,35 +496,29 @@ static int run_vcc(rg_ctx *c, const float *u, const float *v, int diag = 0) {
     return RG_OK;
 }
 
-static int run_curv(rg_ctx *c, const float *u, bool energy) {
-    CurvArgs a;
+// Node passes: w = L v and its energy partials when v is given (energy: keep
+// the partials), then out = sA (NGF boxes) + sB (VCC boxes) + sC L^T w when
+// out is given.
+static int run_nodes(rg_ctx *c, const float *v, bool energy, float *out, double sA, double sB, double sC, bool useA,
+                     bool useB) {
+    NodeArgs a;
     for (int i = 0; i < 3; ++i) {
         a.m[i] = c->grid.m[i];
         a.ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
     }
-    a.u = u;
-    a.w = c->curv_w;
-    a.part = energy ? c->rpart : nullptr;
-    LAUNCH(5, launch_curv_L(a, c->st));
-    return RG_OK;
-}
-
-static int run_finalize(rg_ctx *c, float *out, double sA, double sB, double sC, bool useA, bool useB, bool useC) {
-    FinalizeArgs f;
-    for (int i = 0; i < 3; ++i) {
-        f.m[i] = c->grid.m[i];
-        f.ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
-    }
-    f.boxA = useA ? c->boxA : nullptr;
-    f.gA = c->bA;
-    f.sA = (float)sA;
-    f.boxB = useB ? c->boxB : nullptr;
-    f.gB = c->bB;
-    f.sB = (float)sB;
-    f.curv_w = useC ? c->curv_w : nullptr;
-    f.sC = (float)sC;
-    f.out = out;
-    LAUNCH(6, launch_finalize(f, c->st));
+    a.boxA = useA ? c->boxA : nullptr;
+    a.gA = c->bA;
+    a.sA = (float)sA;
+    a.boxB = useB ? c->boxB : nullptr;
+    a.gB = c->bB;
+    a.sB = (float)sB;
+    a.v = v;
+    a.w = v ? c->curv_w : nullptr;
+    a.sC = (float)sC;
+    a.rpart = energy ? c->rpart : nullptr;
+    a.out = out;
+    if (v) LAUNCH(5, launch_curv(a, c->st));
+    if (out) LAUNCH(6, launch_nodes(a, c->st));
     return RG_OK;
 }
 
@@ -579,11 +573,7 @@ static int evaluate(rg_ctx *c, const float *u, double *terms, float *grad, bool 
     if ((st = run_tile(c, mode, u))) return st;
     const bool vcc = c->P.gamma != 0.0;
     if (vcc && (st = run_vcc(c, u, nullptr))) return st;
-    if ((st = run_curv(c, u, true))) return st;
-    if (grad) {
-        if ((st = run_finalize(c, grad, c->hbar, c->P.gamma * c->ghat, c->P.alpha * c->ghat, true, vcc, true)))
-            return st;
-    }
+    if ((st = run_nodes(c, u, true, grad, c->hbar, c->P.gamma * c->ghat, c->P.alpha * c->ghat, true, vcc))) return st;
     if ((st = run_kp(c, u, nullptr, c->P.delta, grad, true))) return st;
     if ((st = run_terms(c, terms ? terms : c->terms_tmp, true, true, vcc, true))) return st;
     if (store_lin) {
@@ -614,8 +604,7 @@ static int matvec(rg_ctx *c, const float *v, float *Hv) {
     if ((st = run_tile(c, MODE_MATVEC, v))) return st;
     const bool vcc = c->P.gamma != 0.0;
     if (vcc && (st = run_vcc(c, c->lin_u, v))) return st;
-    if ((st = run_curv(c, v, false))) return st;
-    if ((st = run_finalize(c, Hv, c->hbar, c->P.gamma * c->ghat, c->P.alpha * c->ghat, true, vcc, true))) return st;
+    if ((st = run_nodes(c, v, false, Hv, c->hbar, c->P.gamma * c->ghat, c->P.alpha * c->ghat, true, vcc))) return st;
     if ((st = run_kp(c, c->lin_u, v, c->P.delta, Hv, false))) return st;
     return RG_OK;
 }
@@ -632,14 +621,13 @@ extern "C" int regularizer_apply(rg_ctx *c, int32_t which, const float *u, const
     int st;
     if (which == RG_CURV) {
         if (v) {
-            if ((st = run_curv(c, u, true))) return st;     // energy at u
+            if ((st = run_nodes(c, u, true, nullptr, 0, 0, 0, false, false))) return st;   // energy at u
             if (energy && (st = run_terms(c, c->terms_tmp, false, true, false, false))) return st;
-            if ((st = run_curv(c, v, false))) return st;
+            if ((st = run_nodes(c, v, false, out, 0, 0, c->ghat, false, false))) return st;
         } else {
-            if ((st = run_curv(c, u, true))) return st;
+            if ((st = run_nodes(c, u, true, out, 0, 0, c->ghat, false, false))) return st;
             if (energy && (st = run_terms(c, c->terms_tmp, false, true, false, false))) return st;
         }
-        if ((st = run_finalize(c, out, 0, 0, c->ghat, false, false, true))) return st;
         if (energy) CK(cudaMemcpyAsync(energy, c->terms_tmp + 1, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     } else if (which == RG_VCC) {
         if (v) {
@@ -650,7 +638,7 @@ extern "C" int regularizer_apply(rg_ctx *c, int32_t which, const float *u, const
             if ((st = run_vcc(c, u, nullptr))) return st;
             if (energy && (st = run_terms(c, c->terms_tmp, false, false, true, false))) return st;
         }
-        if ((st = run_finalize(c, out, 0, c->ghat, 0, false, true, false))) return st;
+        if ((st = run_nodes(c, nullptr, false, out, 0, c->ghat, 0, false, true))) return st;
         if (energy) CK(cudaMemcpyAsync(energy, c->terms_tmp + 2, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     } else if (which == RG_KP) {
         CK(cudaMemsetAsync(out, 0, sizeof(float) * 3 * c->M, c->st));
@@ -682,7 +670,7 @@ static int ensure_minv(rg_ctx *c) {
     if ((st = run_tile(c, MODE_DIAG, c->lin_u))) return st;
     const bool vcc = c->P.gamma != 0.0;
     if (vcc && (st = run_vcc(c, c->lin_u, nullptr, 1))) return st;
-    if ((st = run_finalize(c, c->minv, 2.0 * c->hbar, c->P.gamma * c->ghat, 0.0, true, vcc, false))) return st;
+    if ((st = run_nodes(c, nullptr, false, c->minv, 2.0 * c->hbar, c->P.gamma * c->ghat, 0.0, true, vcc))) return st;
     float ig2[3], ig[3];
     for (int i = 0; i < 3; ++i) {
         ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));

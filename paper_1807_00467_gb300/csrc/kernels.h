@@ -18,17 +18,6 @@ cudaError_t launch_ngf_tile(int mode, const TileArgs<__half> &a, cudaStream_t st
 bool gn_matvec_supported(const TileGeom &g);
 cudaError_t launch_gn_matvec(const TileArgs<float> &a, cudaStream_t st);
 
-// Curvature, Eq. (5): w = L u on nodes (and per-CTA partial sums of |w|^2).
-struct CurvArgs {
-    int m[3];
-    float ig2[3];          // 1 / g_a^2
-    const float *u;        // [3][M]
-    float *w;              // [3][M]
-    double *part;          // per-CTA partial sums of |L u|^2
-};
-int curv_blocks(const int *m);
-cudaError_t launch_curv_L(const CurvArgs &a, cudaStream_t st);
-
 // Volume change control, Eqs. (7)-(9): per grid cell the 64 bounds d_abc.
 struct VccArgs {
     int m[3];
@@ -48,15 +37,23 @@ constexpr int kVccTile[3] = {8, 4, 4};
 cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st);
 cudaError_t launch_vcc_cells(const VccArgs &a, cudaStream_t st);   // gradient / GN product (a.diag == 0)
 
-// Sum node boxes of up to two box sets and optionally the curvature adjoint.
-struct FinalizeArgs {
+// Node passes: w = L v with the curvature operator L of Eq. (5) and
+// per-block partials of |L v|^2 (launch_curv); out = sA (NGF boxes) +
+// sB (VCC boxes) + sC L^T w (launch_nodes).
+struct NodeArgs {
     int m[3];
+    float ig2[3];          // 1 / g_a^2
     const float *boxA; BoxGeom gA; float sA;   // NGF boxes (scale hbar), may be NULL
     const float *boxB; BoxGeom gB; float sB;   // VCC boxes (scale gamma ghat), may be NULL
-    const float *curv_w; float ig2[3]; float sC;  // curvature L u, scale alpha ghat, may be NULL
-    float *out;            // [3][M]
+    const float *v;        // curvature input [3][M] (launch_curv)
+    float *w;              // L v [3][M]: written by launch_curv, read by launch_nodes (may be NULL there)
+    float sC;              // scale of L^T w (alpha ghat)
+    double *rpart;         // per-block partial sums of |L v|^2, may be NULL
+    float *out;            // [3][M] (launch_nodes)
 };
-cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st);
+int node_blocks(const int *m);
+cudaError_t launch_curv(const NodeArgs &a, cudaStream_t st);
+cudaError_t launch_nodes(const NodeArgs &a, cudaStream_t st);
 
 // Keypoint penalty, Eq. (10).
 struct KpArgs {

@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars 
         rn[et] = nv;
         zt = minv[et] * nv;
     }
+#pragma unroll 2
     for (int j = 0; j <= k; ++j) {
         const float *rj = Rh + (long)j * stride;
         float acc = 0.f;
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(kVT, 3) pcg_reorth_kernel(Part P, const float 
     const bool tail = blockIdx.x == 0 && threadIdx.x < P.tail;
     const long et = 4 * P.n4 + threadIdx.x;
     float rt = tail ? r[et] : 0.f;
+#pragma unroll 2
     for (int j = 0; j <= k; ++j) {
         const float *rj = Rh + (long)j * stride;
         const float cj = c[j];

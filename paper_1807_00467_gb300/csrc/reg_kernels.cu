@@ -34,44 +34,6 @@ struct Kahan {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// ------------------------------------------------------------------ curvature
-int curv_blocks(const int *m) {
-    long M = (long)m[0] * m[1] * m[2];
-    long b = (M + 4 * 256 - 1) / (4 * 256);
-    return (int)(b < 1 ? 1 : b);
-}
-
-__global__ void curv_L_kernel(const CurvArgs a) {
-    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
-    const long mxy = (long)mx * my, M = mxy * mz;
-    Kahan acc;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < M; k += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(k / mxy), rem = (int)(k - kz * mxy), ky = rem / mx, kx = rem - ky * mx;
-        const bool ix = kx >= 1 && kx <= mx - 2, iy = ky >= 1 && ky <= my - 2, iz = kz >= 1 && kz <= mz - 2;
-        float e = 0.f;
-        for (int c = 0; c < 3; ++c) {
-            const float *u = a.u + c * M;
-            const float u0 = u[k];
-            float s = 0.f;
-            if (ix) s += (u[k + 1] - 2.f * u0 + u[k - 1]) * a.ig2[0];
-            if (iy) s += (u[k + mx] - 2.f * u0 + u[k - mx]) * a.ig2[1];
-            if (iz) s += (u[k + mxy] - 2.f * u0 + u[k - mxy]) * a.ig2[2];
-            a.w[c * M + k] = s;
-            e = fmaf(s, s, e);
-        }
-        acc.add(e);
-    }
-    if (a.part) {
-        double t = block_sum(acc.value());
-        if (threadIdx.x == 0) a.part[blockIdx.x] = t;
-    }
-}
-
-cudaError_t launch_curv_L(const CurvArgs &a, cudaStream_t st) {
-    curv_L_kernel<<<curv_blocks(a.m), 256, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ VCC
 // Edge e of the axis-a edges joins corner offsets o0 -> o1; the two other
 // axes carry (e & 1, e >> 1) in increasing axis order.
@@ -330,77 +292,6 @@ cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st) {
     constexpr int NT = 4 * kVccTile[0] * kVccTile[1] * kVccTile[2];
     if (!a.diag) return launch_vcc_cells(a, st);   // gradient and GN product: one thread per cell
     vcc_kernel<2><<<grid, NT, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ finalize
-// Sum, per component, the entries of node k in the (up to 8) CTA boxes holding it.
-__device__ __forceinline__ void sum_boxes(const float *boxes, const BoxGeom &b, int kx, int ky, int kz, float *out) {
-    const int k[3] = {kx, ky, kz};
-    int c0[3], l0[3], nc[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        // boxes hi - 1 and hi hold node k when 0 <= k - bb C <= C
-        const int hi = k[ax] / b.C[ax];
-        const int lo = (hi - 1 >= 0 && k[ax] - (hi - 1) * b.C[ax] <= b.C[ax]) ? hi - 1 : hi;
-        const int top = min(hi, b.nb[ax] - 1);
-        c0[ax] = lo;
-        l0[ax] = k[ax] - lo * b.C[ax];
-        nc[ax] = top - lo + 1;
-    }
-    const int BX = b.C[0] + 1, BY = b.C[1] + 1;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    for (int iz = 0; iz < nc[2]; ++iz)
-        for (int iy = 0; iy < nc[1]; ++iy)
-            for (int ix = 0; ix < nc[0]; ++ix) {
-                const long cta = ((long)(c0[2] + iz) * b.nb[1] + (c0[1] + iy)) * b.nb[0] + (c0[0] + ix);
-                const long off = cta * 3 * b.box + ((l0[2] - iz * b.C[2]) * BY + (l0[1] - iy * b.C[1])) * BX +
-                                 (l0[0] - ix * b.C[0]);
-                s0 += boxes[off];
-                s1 += boxes[off + b.box];
-                s2 += boxes[off + 2 * (long)b.box];
-            }
-    out[0] = s0;
-    out[1] = s1;
-    out[2] = s2;
-}
-
-__global__ void finalize_kernel(const FinalizeArgs a) {
-    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
-    const long mxy = (long)mx * my, M = mxy * mz;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < M; k += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(k / mxy), rem = (int)(k - kz * mxy), ky = rem / mx, kx = rem - ky * mx;
-        float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
-        if (a.boxA) sum_boxes(a.boxA, a.gA, kx, ky, kz, sa);
-        if (a.boxB) sum_boxes(a.boxB, a.gB, kx, ky, kz, sb);
-        const int kk[3] = {kx, ky, kz}, mm[3] = {mx, my, mz};
-        const long st[3] = {1, mx, mxy};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float v = a.sA * sa[c] + a.sB * sb[c];
-            if (a.curv_w) {
-                // L^T w: rows of L that reference node k along each axis
-                const float *w = a.curv_w + c * M;
-                float t2 = 0.f;
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    float t = 0.f;
-                    if (kk[ax] >= 1 && kk[ax] <= mm[ax] - 2) t -= 2.f * w[k];
-                    if (kk[ax] - 1 >= 1) t += w[k - st[ax]];
-                    if (kk[ax] + 1 <= mm[ax] - 2) t += w[k + st[ax]];
-                    t2 = fmaf(t, a.ig2[ax], t2);
-                }
-                v = fmaf(a.sC, t2, v);
-            }
-            a.out[c * M + k] = v;
-        }
-    }
-}
-
-cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st) {
-    long M = (long)a.m[0] * a.m[1] * a.m[2];
-    int blocks = (int)((M + 255) / 256);
-    finalize_kernel<<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
