@@ -30,7 +30,10 @@
 //    applied once per node;
 //  - P^T: each column accumulates its two z-node planes in registers and parks
 //    a completed node plane in shared memory; the x and y reductions (hat
-//    weights of the trilinear prolongation) run once per chunk.
+//    weights of the trilinear prolongation) run once per chunk as row sweeps;
+//  - persistent CTAs: each CTA walks tiles strided by the grid and its TMA
+//    plane sequence continues into the next tile, whose first planes and node
+//    tile are fetched during the current tile's reduction.
 #include "common.cuh"
 #include "kernels.h"
 #include "tma.cuh"
@@ -62,47 +65,63 @@ __host__ __device__ inline MvSmem mv_smem(const TileGeom &g) {
     s.exc = off; off += 2 * kEx;                          // c'_y of plane A, double-buffered
     s.nodes = off; off += g.nzt * g.nyt * g.nxt * 4;      // node planes of v, [plane][y][x][xyz_]
     s.rows = off; off += (g.C[2] + 1) * kTY * g.TXI * 3;  // z-reduced column sums per node plane
-    s.xr = (g.C[2] + 1) * kTY * (g.C[0] + 1) * 3;         // x-reduced sums (reuse the TMA ring)
+    s.xr = off; off += (g.C[2] + 1) * kTY * (g.C[0] + 1) * 3;   // x-reduced sums
     s.total = off;
     return s;
 }
 
-// P^T along one axis for node j and every node plane p < np:
-// dst[p dpl] = scale sum_i w_i src[p spl + (j - 1) R + i] (source index times sstride),
-// i in [0, 2R), with the trilinear hat weights w_i of the ratio R and the
-// source indices outside [0, nsrc) left out.
-template <int R>
-__device__ __forceinline__ void hat_sum(const float *src, int sstride, int spl, int j, int nsrc, float *dst, int dpl,
-                                        int np, float scale) {
-    float w[2 * R];
-    int off[2 * R];
+// P^T along one axis by a sweep over a row of n = C R source values
+// (stride `ss`): node c receives (1 - f_i) v from its own cell and f_i v from
+// the cell below, f_i = (i + 1/2) / R the trilinear weights of the ratio R;
+// writes the C + 1 node values (stride `ds`) times `scale`.
+template <int R, int C>
+__device__ __forceinline__ void hat_sweep(const float *src, int ss, float *dst, int ds, float scale) {
+    float below = 0.f;
 #pragma unroll
-    for (int i = 0; i < 2 * R; ++i) {
-        const int c = (j - 1) * R + i;
-        w[i] = (c >= 0 && c < nsrc) ? (i < R ? (i + 0.5f) / R : 1.f - (i - R + 0.5f) / R) : 0.f;
-        off[i] = min(max(c, 0), nsrc - 1) * sstride;
+    for (int c = 0; c < C; ++c) {
+        float own = 0.f, up = 0.f;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const float v = src[(c * R + i) * ss];
+            own = fmaf(1.f - (i + 0.5f) / R, v, own);
+            up = fmaf((i + 0.5f) / R, v, up);
+        }
+        dst[c * ds] = scale * (below + own);
+        below = up;
     }
-    for (int p = 0; p < np; ++p) {
-        const float *q = src + p * spl;
-        float v = 0.f;
-#pragma unroll
-        for (int i = 0; i < 2 * R; ++i) v = fmaf(w[i], q[off[i]], v);
-        dst[p * dpl] = scale * v;
+    dst[C * ds] = scale * below;
+}
+
+// x then y reduction of the parked column sums rows[plane][ty][tx][comp] onto
+// the tile's node box [comp][plane][jy][jx] (times 2), through xr[plane][ty][jx][comp]
+template <int RX, int RY>
+__device__ __forceinline__ void node_reduce(const float *rows, float *xr, float *box, int boxsz, int nplanes, int tid) {
+    constexpr int TXI = 28 - 28 % RX, CX = TXI / RX, CY = kTY / RY;
+    for (int r = tid; r < nplanes * kTY * 3; r += kNT) {
+        const int k = r % 3, pr = r / 3;   // pr = plane * kTY + ty
+        hat_sweep<RX, CX>(rows + pr * TXI * 3 + k, 3, xr + pr * (CX + 1) * 3 + k, 3, 1.f);
+    }
+    __syncthreads();
+    for (int r = tid; r < nplanes * (CX + 1) * 3; r += kNT) {
+        const int k = r % 3, q = r / 3, jx = q % (CX + 1), pl = q / (CX + 1);
+        hat_sweep<RY, CY>(xr + (pl * kTY * (CX + 1) + jx) * 3 + k, (CX + 1) * 3,
+                          box + (long)k * boxsz + pl * (CY + 1) * (CX + 1) + jx, CX + 1, 2.f);
     }
 }
 
-__device__ __forceinline__ void hat_sum_any(int R, const float *src, int sstride, int spl, int j, int nsrc, float *dst,
-                                            int dpl, int np, float scale) {
-    switch (R) {
-        case 1: hat_sum<1>(src, sstride, spl, j, nsrc, dst, dpl, np, scale); break;
-        case 2: hat_sum<2>(src, sstride, spl, j, nsrc, dst, dpl, np, scale); break;
-        case 4: hat_sum<4>(src, sstride, spl, j, nsrc, dst, dpl, np, scale); break;
-        default: hat_sum<8>(src, sstride, spl, j, nsrc, dst, dpl, np, scale); break;
+template <int RX>
+__device__ __forceinline__ void node_reduce_ry(int ry, const float *rows, float *xr, float *box, int boxsz,
+                                               int nplanes, int tid) {
+    switch (ry) {
+        case 1: node_reduce<RX, 1>(rows, xr, box, boxsz, nplanes, tid); break;
+        case 2: node_reduce<RX, 2>(rows, xr, box, boxsz, nplanes, tid); break;
+        case 4: node_reduce<RX, 4>(rows, xr, box, boxsz, nplanes, tid); break;
+        default: node_reduce<RX, 8>(rows, xr, box, boxsz, nplanes, tid); break;
     }
 }
 
 template <int RZ>
-__global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant__ TileArgs<float> a) {
+__global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant__ TileArgs<float> a, int chain) {
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bars[kStages];
@@ -111,37 +130,35 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
 
     const int tid = threadIdx.x, L = tid & 31, w = tid >> 5;
     const int TXI = g.TXI;
-    const int x0 = blockIdx.x * TXI, y0 = blockIdx.y * kTY, z0 = blockIdx.z * g.TZ;
-    const int TZc = min(g.TZ, g.n[2] - z0);
-    const int nsteps = TZc + 4;
+    const int ntiles = g.nb[0] * g.nb[1] * g.nb[2];
     const int lrx = g.lrho[0], lry = g.lrho[1], lrz = g.lrho[2];
     const int rzm = g.rho[2] - 1;
     const float irz = g.irho[2];
-    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 
     float *tma_base = smem + S.tma + ((128u - (smem_u32(smem + S.tma) & 127u)) & 127u) / 4;
-    float *rows = smem + S.rows;
+    float *rows = smem + S.rows, *xr = smem + S.xr;
     float4 *s_nodes = reinterpret_cast<float4 *>(smem + S.nodes);
 
-    // plane j of the chunk's sequence (voxel plane z0 - 2 + j) into stage j % kStages
-    auto issue_plane = [&](int j) {
-        const int st = j & (kStages - 1);
+    // tile t: voxel origin (x0, y0, z0); tiles are numbered x fastest, then y, then z
+    auto origin = [&](int t, int &x0, int &y0, int &z0) {
+        const int bx = t % g.nb[0], r = t / g.nb[0];
+        x0 = bx * TXI;
+        y0 = (r % g.nb[1]) * kTY;
+        z0 = (r / g.nb[1]) * g.TZ;
+    };
+    // plane j of tile (x0, y0, z0) (voxel plane z0 - 2 + j) into stage `st`
+    auto issue_plane = [&](int x0, int y0, int z0, int j, int st) {
         float *dst = tma_base + st * kStageF;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bars[st], kPlaneBytes);
         tma_load_4d(dst, &a.map_dT, &bars[st], x0 - 4, y0 - 2, z0 - 2 + j, 0);
         tma_load_4d(dst + kBoxF, &a.map_a, &bars[st], x0 - 4, y0 - 2, z0 - 2 + j, 0);
     };
-    if (tid == 0) {
-        for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int j = 0; j < kAhead && j < nsteps; ++j) issue_plane(j);
-    }
-
-    // node planes of v for P v, from floor((z0 - 2) / rho_z) on (zero outside the grid)
+    // node planes of v for P v on tile (x0, y0, z0), from floor((z0 - 2) / rho_z)
+    // on (zero outside the grid)
     const int nxt = g.nxt, nyt = g.nyt, nplane = nxt * nyt;
-    const int kx_lo = max(x0 - 2, 0) >> lrx, ky_lo = max(y0 - 2, 0) >> lry, kz_lo = (z0 - 2) >> lrz;
-    {
+    auto load_nodes = [&](int x0, int y0, int z0) {
+        const int kx_lo = max(x0 - 2, 0) >> lrx, ky_lo = max(y0 - 2, 0) >> lry, kz_lo = (z0 - 2) >> lrz;
         const long mxy = (long)g.m[0] * g.m[1], Mn = mxy * g.m[2];
         for (int i = tid; i < g.nzt * nplane; i += kNT) {
             const int pl = i / nplane, r = i - pl * nplane;
@@ -156,25 +173,21 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
             }
             s_nodes[i] = v;
         }
-    }
-
-    // this column's bilinear position in the node tile (clamped: columns
-    // outside the volume have dT/dy = 0 and only need finite values)
-    const int gx = x0 - 2 + L, gy = y0 - 2 + w;
-    const int cxg = gx >> lrx, cyg = gy >> lry;
-    const float fx = ((gx - (cxg << lrx)) + 0.5f) * g.irho[0];
-    const float fy = ((gy - (cyg << lry)) + 0.5f) * g.irho[1];
-    const float4 *qcol = s_nodes + min(max(cyg - ky_lo, 0), nyt - 2) * nxt + min(max(cxg - kx_lo, 0), nxt - 2);
-    auto bilinear = [&](int kz, float *U) {
-        const float4 *q = qcol + (kz - kz_lo) * nplane;
-        const float4 n00 = q[0], n10 = q[1], n01 = q[nxt], n11 = q[nxt + 1];
-        float lo = fmaf(fx, n10.x - n00.x, n00.x), hi = fmaf(fx, n11.x - n01.x, n01.x);
-        U[0] = fmaf(fy, hi - lo, lo);
-        lo = fmaf(fx, n10.y - n00.y, n00.y); hi = fmaf(fx, n11.y - n01.y, n01.y);
-        U[1] = fmaf(fy, hi - lo, lo);
-        lo = fmaf(fx, n10.z - n00.z, n00.z); hi = fmaf(fx, n11.z - n01.z, n01.z);
-        U[2] = fmaf(fy, hi - lo, lo);
     };
+
+    int t = blockIdx.x;
+    if (t >= ntiles) return;
+    {
+        int x0, y0, z0;
+        origin(t, x0, y0, z0);
+        if (tid == 0) {
+            for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            const int ns = min(g.TZ, g.n[2] - z0) + 4;
+            for (int j = 0; j < kAhead && j < ns; ++j) issue_plane(x0, y0, z0, j, j);
+        }
+        load_nodes(x0, y0, z0);
+    }
 
     const float i2h0 = g.inv2h[0], i2h1 = g.inv2h[1], i2h2 = g.inv2h[2];
     const bool own_col = w >= 2 && w < kTY + 2 && L >= 2 && L < TXI + 2;   // tile-owned column
@@ -183,118 +196,145 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
     float *ex_t = smem + S.ext + w * 32 + L, *ex_c = smem + S.exc + w * 32 + L;
     const int up = w > 0 ? -32 : 0, dn = w < kNW - 1 ? 32 : 0;
     float *rowp = rows + ((w - 2) * TXI + (L - 2)) * 3;    // + node plane * kTY * TXI * 3
+    uint32_t phase = 0;   // continues across the tiles of this CTA (each has a multiple of kStages planes)
+    for (;;) {
+        int x0, y0, z0, xn = 0, yn = 0, zn = 0;
+        origin(t, x0, y0, z0);
+        const int tn = t + gridDim.x;   // this CTA's next tile
+        const bool has_next = chain && tn < ntiles;
+        if (has_next) origin(tn, xn, yn, zn);
+        const int TZc = min(g.TZ, g.n[2] - z0);
+        const int nsteps = TZc + 4;
+        const int kx_lo = max(x0 - 2, 0) >> lrx, ky_lo = max(y0 - 2, 0) >> lry, kz_lo = (z0 - 2) >> lrz;
 
-    __syncthreads();
+        // this column's bilinear position in the node tile (clamped: columns
+        // outside the volume have dT/dy = 0 and only need finite values)
+        const int gx = x0 - 2 + L, gy = y0 - 2 + w;
+        const int cxg = gx >> lrx, cyg = gy >> lry;
+        const float fx = ((gx - (cxg << lrx)) + 0.5f) * g.irho[0];
+        const float fy = ((gy - (cyg << lry)) + 0.5f) * g.irho[1];
+        const float4 *qcol = s_nodes + min(max(cyg - ky_lo, 0), nyt - 2) * nxt + min(max(cxg - kx_lo, 0), nxt - 2);
+        auto bilinear = [&](int kz, float *U) {
+            const float4 *q = qcol + (kz - kz_lo) * nplane;
+            const float4 n00 = q[0], n10 = q[1], n01 = q[nxt], n11 = q[nxt + 1];
+            float lo = fmaf(fx, n10.x - n00.x, n00.x), hi = fmaf(fx, n11.x - n01.x, n01.x);
+            U[0] = fmaf(fy, hi - lo, lo);
+            lo = fmaf(fx, n10.y - n00.y, n00.y); hi = fmaf(fx, n11.y - n01.y, n01.y);
+            U[1] = fmaf(fy, hi - lo, lo);
+            lo = fmaf(fx, n10.z - n00.z, n00.z); hi = fmaf(fx, n11.z - n01.z, n01.z);
+            U[2] = fmaf(fy, hi - lo, lo);
+        };
 
-    float U0[3], U1[3], D[3];   // P v at node planes cz, cz + 1 (x-y interpolated), D = U1 - U0
-    {
-        const int cz = (z0 - 2) >> lrz;
-        bilinear(cz, U0);
-        bilinear(cz + 1, U1);
-        for (int k = 0; k < 3; ++k) D[k] = U1[k] - U0[k];
-    }
-    float tm = 0.f, t0 = 0.f;                  // t at planes pC - 1, pC
-    float a1[3] = {0.f, 0.f, 0.f};             // a' at plane pC (read by stage W one plane earlier)
-    float d1[3] = {0.f, 0.f, 0.f}, d2[3] = {0.f, 0.f, 0.f};   // dT/dy at planes pW - 1 (= pC), pW - 2 (= pA)
-    float cxp = 0.f;                           // c'_x at plane pA (from the previous plane's stage C)
-    float czm2 = 0.f, czm1 = 0.f;              // c'_z at planes pA - 1, pA
-    float acc0[3] = {0.f, 0.f, 0.f}, acc1[3] = {0.f, 0.f, 0.f};   // z-node planes czl, czl + 1
+        // node tile loaded; the previous tile's reduction is done with rows and xr
+        __syncthreads();
 
-    uint32_t phase = 0;
-    for (int s0 = 0; s0 < nsteps; s0 += kStages, phase ^= 1u) {
+        float U0[3], U1[3], D[3];   // P v at node planes cz, cz + 1 (x-y interpolated), D = U1 - U0
+        {
+            const int cz = (z0 - 2) >> lrz;
+            bilinear(cz, U0);
+            bilinear(cz + 1, U1);
+            for (int k = 0; k < 3; ++k) D[k] = U1[k] - U0[k];
+        }
+        float tm = 0.f, t0 = 0.f;                  // t at planes pC - 1, pC
+        float a1[3] = {0.f, 0.f, 0.f};             // a' at plane pC (read by stage W one plane earlier)
+        float d1[3] = {0.f, 0.f, 0.f}, d2[3] = {0.f, 0.f, 0.f};   // dT/dy at planes pW - 1 (= pC), pW - 2 (= pA)
+        float cxp = 0.f;                           // c'_x at plane pA (from the previous plane's stage C)
+        float czm2 = 0.f, czm1 = 0.f;              // c'_z at planes pA - 1, pA
+        float acc0[3] = {0.f, 0.f, 0.f}, acc1[3] = {0.f, 0.f, 0.f};   // z-node planes czl, czl + 1
+
+        for (int s0 = 0; s0 < nsteps; s0 += kStages, phase ^= 1u) {
 #pragma unroll
-        for (int j = 0; j < kStages; ++j) {
-            const int s = s0 + j;
-            if (s >= nsteps) break;
-            const int pW = z0 - 2 + s;
-            // z phase of planes pW and pA = pW - 2 within their cells (z0 is a
-            // multiple of rho_z; so is s0 when rho_z divides the ring depth)
-            const int phW = RZ ? ((j - 2) & (RZ - 1)) : (pW & rzm);
-            const int phA = RZ ? (j & (RZ - 1)) : ((pW - 2) & rzm);
-            const float fz = RZ ? (phW + 0.5f) / (float)(RZ ? RZ : 1) : (phW + 0.5f) * irz;
-            const float wz1 = RZ ? (phA + 0.5f) / (float)(RZ ? RZ : 1) : (phA + 0.5f) * irz;
+            for (int j = 0; j < kStages; ++j) {
+                const int s = s0 + j;
+                if (s >= nsteps) break;
+                const int pW = z0 - 2 + s;
+                // z phase of planes pW and pA = pW - 2 within their cells (z0 is a
+                // multiple of rho_z; so is s0 when rho_z divides the ring depth)
+                const int phW = RZ ? ((j - 2) & (RZ - 1)) : (pW & rzm);
+                const int phA = RZ ? (j & (RZ - 1)) : ((pW - 2) & rzm);
+                const float fz = RZ ? (phW + 0.5f) / (float)(RZ ? RZ : 1) : (phW + 0.5f) * irz;
+                const float wz1 = RZ ? (phA + 0.5f) / (float)(RZ ? RZ : 1) : (phA + 0.5f) * irz;
 
-            // the stage of plane s - 1 was last read before this barrier
-            __syncthreads();
-            if (tid == 0 && s + kAhead < nsteps) issue_plane(s + kAhead);
-
-            // ------------------------------------------------ P v: next node plane at a cell start
-            if (phW == 0 && s > 0) {
-                U0[0] = U1[0]; U0[1] = U1[1]; U0[2] = U1[2];
-                bilinear((pW >> lrz) + 1, U1);
-                D[0] = U1[0] - U0[0]; D[1] = U1[1] - U0[1]; D[2] = U1[2] - U0[2];
-            }
-
-            mbar_wait_bounded(&bars[j], phase, a.err);
-            // ------------------------------------------------ stage W: t at plane pW
-            const float *sW = sbase + j * kStageF;
-            const float dw0 = sW[0], dw1 = sW[kComp], dw2 = sW[2 * kComp];
-            const float aw0 = sW[kBoxF] * i2h0, aw1 = sW[kBoxF + kComp] * i2h1, aw2 = sW[kBoxF + 2 * kComp] * i2h2;
-            const float tp = fmaf(dw2, fmaf(fz, D[2], U0[2]), fmaf(dw1, fmaf(fz, D[1], U0[1]), dw0 * fmaf(fz, D[0], U0[0])));
-
-            // ------------------------------------------------ stage C: c' at plane pC = pW - 1
-            const int b = (j & 1) * kEx;
-            const float txl = __shfl_up_sync(FULL, t0, 1), txr = __shfl_down_sync(FULL, t0, 1);
-            const float dr = fmaf(a1[2], tp - tm, fmaf(a1[1], ex_t[b + dn] - ex_t[b + up], a1[0] * (txr - txl)));
-            const float c0 = dr * a1[0], c1 = dr * a1[1], c2 = dr * a1[2];
-
-            // ------------------------------------------------ stage A: G^T c at plane pA = pW - 2, times dT/dy
-            const float cxl = __shfl_up_sync(FULL, cxp, 1), cxr = __shfl_down_sync(FULL, cxp, 1);
-            if (j >= 4 || s0 > 0) {   // planes of the chunk (pA >= z0)
-                const float bsum = (cxl - cxr) + (ex_c[b + up] - ex_c[b + dn]) + (czm2 - c2);
-                const float b1 = wz1 * bsum, b0 = bsum - b1;
-                acc0[0] = fmaf(b0, d2[0], acc0[0]); acc0[1] = fmaf(b0, d2[1], acc0[1]); acc0[2] = fmaf(b0, d2[2], acc0[2]);
-                acc1[0] = fmaf(b1, d2[0], acc1[0]); acc1[1] = fmaf(b1, d2[1], acc1[1]); acc1[2] = fmaf(b1, d2[2], acc1[2]);
-                if (phA == (RZ ? RZ - 1 : rzm)) {
-                    // node plane (pA - z0) / rho_z is complete for this column: park it
-                    if (own_col) {
-                        float *r = rowp + ((s - 4) >> lrz) * (kTY * TXI * 3);
-                        r[0] = acc0[0]; r[1] = acc0[1]; r[2] = acc0[2];
-                    }
-                    acc0[0] = acc1[0]; acc0[1] = acc1[1]; acc0[2] = acc1[2];
-                    acc1[0] = acc1[1] = acc1[2] = 0.f;
+                // the stage of plane s - 1 was last read before this barrier
+                __syncthreads();
+                if (tid == 0) {
+                    // 3 planes ahead: of this tile, then the first planes of the next one
+                    if (s + kAhead < nsteps) issue_plane(x0, y0, z0, s + kAhead, (j + kAhead) & (kStages - 1));
+                    else if (has_next) issue_plane(xn, yn, zn, s + kAhead - nsteps, (j + kAhead) & (kStages - 1));
                 }
-            }
-            // ------------------------------------------------ hand over to the next plane
-            ex_t[kEx - b] = tp;
-            ex_c[kEx - b] = c1;
-            tm = t0; t0 = tp;
-            czm2 = czm1; czm1 = c2;
-            cxp = c0;
-            d2[0] = d1[0]; d2[1] = d1[1]; d2[2] = d1[2];
-            d1[0] = dw0; d1[1] = dw1; d1[2] = dw2;
-            a1[0] = aw0; a1[1] = aw1; a1[2] = aw2;
-        }
-    }
-    // the node plane above the chunk's last cell
-    if (own_col) {
-        float *r = rowp + (TZc >> lrz) * (kTY * TXI * 3);
-        r[0] = acc0[0]; r[1] = acc0[1]; r[2] = acc0[2];
-    }
-    __syncthreads();
 
-    // ---------------------------------------------------- x then y reduction onto the CTA's node box
-    // (each thread keeps one (row, node, component) and walks the node planes)
-    const int CX = g.C[0], CY = g.C[1];
-    const int nplanes = (TZc >> lrz) + 1;
-    float *xr = tma_base;   // [plane][ty][jx][comp]; every TMA copy has completed
-    for (int e = tid; e < kTY * (CX + 1) * 3; e += kNT) {
-        const int k = e % 3, t = e / 3, jx = t % (CX + 1), ty = t / (CX + 1);
-        const float *src = rows + ty * TXI * 3 + k;
-        float *dst = xr + (ty * (CX + 1) + jx) * 3 + k;
-        hat_sum_any(g.rho[0], src, 3, kTY * TXI * 3, jx, TXI, dst, kTY * (CX + 1) * 3, nplanes, 1.f);
-    }
-    __syncthreads();
-    {
-        const int nc = (CY + 1) * (CX + 1) * 3, G = max(1, kNT / nc);
-        for (int e = tid; e < nc * G; e += kNT) {
-            const int c = e % nc, pg = e / nc;
-            const int k = c % 3, t = c / 3, jx = t % (CX + 1), jy = t / (CX + 1);
-            const float *src = xr + pg * kTY * (CX + 1) * 3 + jx * 3 + k;
-            float *dst = a.boxes + ((long)cta * 3 + k) * g.box + (pg * (CY + 1) + jy) * (CX + 1) + jx;
-            hat_sum_any(g.rho[1], src, (CX + 1) * 3, G * kTY * (CX + 1) * 3, jy, kTY, dst, G * (CY + 1) * (CX + 1),
-                        (nplanes - pg + G - 1) / G, 2.f);
+                // ------------------------------------------------ P v: next node plane at a cell start
+                if (phW == 0 && s > 0) {
+                    U0[0] = U1[0]; U0[1] = U1[1]; U0[2] = U1[2];
+                    bilinear((pW >> lrz) + 1, U1);
+                    D[0] = U1[0] - U0[0]; D[1] = U1[1] - U0[1]; D[2] = U1[2] - U0[2];
+                }
+
+                mbar_wait_bounded(&bars[j], phase, a.err);
+                // ------------------------------------------------ stage W: t at plane pW
+                const float *sW = sbase + j * kStageF;
+                const float dw0 = sW[0], dw1 = sW[kComp], dw2 = sW[2 * kComp];
+                const float aw0 = sW[kBoxF] * i2h0, aw1 = sW[kBoxF + kComp] * i2h1, aw2 = sW[kBoxF + 2 * kComp] * i2h2;
+                const float tp = fmaf(dw2, fmaf(fz, D[2], U0[2]),
+                                      fmaf(dw1, fmaf(fz, D[1], U0[1]), dw0 * fmaf(fz, D[0], U0[0])));
+
+                // ------------------------------------------------ stage C: c' at plane pC = pW - 1
+                const int b = (j & 1) * kEx;
+                const float txl = __shfl_up_sync(FULL, t0, 1), txr = __shfl_down_sync(FULL, t0, 1);
+                const float dr = fmaf(a1[2], tp - tm, fmaf(a1[1], ex_t[b + dn] - ex_t[b + up], a1[0] * (txr - txl)));
+                const float c0 = dr * a1[0], c1 = dr * a1[1], c2 = dr * a1[2];
+
+                // ------------------------------------------------ stage A: G^T c at plane pA = pW - 2, times dT/dy
+                const float cxl = __shfl_up_sync(FULL, cxp, 1), cxr = __shfl_down_sync(FULL, cxp, 1);
+                if (j >= 4 || s0 > 0) {   // planes of the chunk (pA >= z0)
+                    const float bsum = (cxl - cxr) + (ex_c[b + up] - ex_c[b + dn]) + (czm2 - c2);
+                    const float b1 = wz1 * bsum, b0 = bsum - b1;
+                    acc0[0] = fmaf(b0, d2[0], acc0[0]); acc0[1] = fmaf(b0, d2[1], acc0[1]); acc0[2] = fmaf(b0, d2[2], acc0[2]);
+                    acc1[0] = fmaf(b1, d2[0], acc1[0]); acc1[1] = fmaf(b1, d2[1], acc1[1]); acc1[2] = fmaf(b1, d2[2], acc1[2]);
+                    if (phA == (RZ ? RZ - 1 : rzm)) {
+                        // node plane (pA - z0) / rho_z is complete for this column: park it
+                        if (own_col) {
+                            float *r = rowp + ((s - 4) >> lrz) * (kTY * TXI * 3);
+                            r[0] = acc0[0]; r[1] = acc0[1]; r[2] = acc0[2];
+                        }
+                        acc0[0] = acc1[0]; acc0[1] = acc1[1]; acc0[2] = acc1[2];
+                        acc1[0] = acc1[1] = acc1[2] = 0.f;
+                    }
+                }
+                // ------------------------------------------------ hand over to the next plane
+                ex_t[kEx - b] = tp;
+                ex_c[kEx - b] = c1;
+                tm = t0; t0 = tp;
+                czm2 = czm1; czm1 = c2;
+                cxp = c0;
+                d2[0] = d1[0]; d2[1] = d1[1]; d2[2] = d1[2];
+                d1[0] = dw0; d1[1] = dw1; d1[2] = dw2;
+                a1[0] = aw0; a1[1] = aw1; a1[2] = aw2;
+            }
         }
+        // the node plane above the chunk's last cell
+        if (own_col) {
+            float *r = rowp + (TZc >> lrz) * (kTY * TXI * 3);
+            r[0] = acc0[0]; r[1] = acc0[1]; r[2] = acc0[2];
+        }
+        __syncthreads();
+
+        // the next tile's node planes (no thread reads the node tile any more),
+        // while its first TMA planes are in flight
+        if (has_next) load_nodes(xn, yn, zn);
+
+        // ------------------------------------------------ x then y reduction onto the tile's node box
+        {
+            const int nplanes = (TZc >> lrz) + 1;
+            float *box = a.boxes + (long)t * 3 * g.box;
+            switch (g.rho[0]) {
+                case 2: node_reduce_ry<2>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
+                case 4: node_reduce_ry<4>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
+                default: node_reduce_ry<8>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
+            }
+        }
+        if (!has_next) break;
+        t = tn;
     }
 }
 
@@ -303,17 +343,29 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
 bool gn_matvec_supported(const TileGeom &g) {
     if (!g.tma || g.TY != kTY || g.nzt <= 0 || g.rho[0] < 2) return false;
     const MvSmem s = mv_smem(g);
-    return s.xr <= kStages * kStageF && (size_t)s.total * sizeof(float) <= 227u * 1024u;
+    return (size_t)s.total * sizeof(float) <= 227u * 1024u;
 }
 
 cudaError_t launch_gn_matvec(const TileArgs<float> &a, cudaStream_t st) {
     if (!gn_matvec_supported(a.g)) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * (size_t)mv_smem(a.g).total;
-    const dim3 grid(a.g.nb[0], a.g.nb[1], a.g.nb[2]);
+    const int ntiles = a.g.nb[0] * a.g.nb[1] * a.g.nb[2];
+    // persistent CTAs (one per SM, tiles strided by the grid) when every tile's
+    // plane sequence is a whole number of ring cycles, else one tile per CTA
+    const int tail = a.g.n[2] - (a.g.nb[2] - 1) * a.g.TZ;
+    const int chain = (a.g.TZ + 4) % kStages == 0 && (tail + 4) % kStages == 0;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms <= 0)
+            sms = 1;
+    }
+    const int grid = chain ? (ntiles < sms ? ntiles : sms) : ntiles;
     auto run = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kernel<<<grid, kNT, smem, st>>>(a);
+        kernel<<<grid, kNT, smem, st>>>(a, chain);
         return cudaGetLastError();
     };
     switch (a.g.rho[2]) {
