@@ -75,10 +75,10 @@ __global__ void __launch_bounds__(NT) curv_kernel(const NodeArgs a) {
         }
     }
     if (a.rpart) {
-        double t = (double)e;
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        // FP32 within the warp (a tree of non-negative terms: relative error <= 5 ulp), FP64 across warps
+        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
         __shared__ double red[NT / 32];
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)e;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;

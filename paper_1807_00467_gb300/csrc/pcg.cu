@@ -4,8 +4,8 @@
 // Every kernel streams the node vectors as float4 with the same partition:
 // block b owns quads [b Q, (b + 1) Q), Q = 256 qpt, thread t its quads
 // b Q + i 256 + t (i < qpt <= kQmax), so each thread keeps up to kQmax
-// independent 16-byte loads in flight per stream.  Per-block partial sums are
-// FP64; the block that finishes last (atomic ticket, no waiting) reduces them
+// independent 16-byte loads in flight per stream.  Sums are FP32 within a
+// warp and FP64 across warps and blocks; the block that finishes last (atomic ticket, no waiting) reduces them
 // in a fixed order and updates the device scalars, so no separate scalar
 // kernels run and the result does not depend on block scheduling.
 //
@@ -34,10 +34,18 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) {
     return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
 }
 
-// Block sum of a per-thread value; the result is valid in thread 0.
-__device__ __forceinline__ double block_total(double v, double *red) {
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+// FP32 warp sum (fixed shuffle tree); FP64 is ~1/64 of the FP32 rate on this
+// part, so only the per-warp partials are widened
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+// Block sum of a per-thread value (FP32 within a warp, FP64 across warps);
+// the result is valid in thread 0.
+__device__ __forceinline__ double block_total(float v, double *red) {
+    v = warp_sum_f(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
@@ -111,8 +119,8 @@ __global__ void __launch_bounds__(kVT) pcg_start_kernel(Part P, const float *g, 
         gg = fmaf(rv, rv, gg);
         rz = fmaf(rv, zv, rz);
     }
-    const double tg = block_total((double)gg, red);
-    const double tr = block_total((double)rz, red);
+    const double tg = block_total(gg, red);
+    const double tr = block_total(rz, red);
     if (threadIdx.x == 0) { part[blockIdx.x] = tg; part[nb + blockIdx.x] = tr; }
     if (!last_block(ticket)) return;
     if (threadIdx.x < 64) {
@@ -146,7 +154,7 @@ __global__ void __launch_bounds__(kVT) pcg_alpha_kernel(Part P, const float *d, 
         const long e = 4 * P.n4 + threadIdx.x;
         acc = fmaf(d[e], q[e], acc);
     }
-    const double t = block_total((double)acc, red);
+    const double t = block_total(acc, red);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
     if (!last_block(ticket)) return;
     if (threadIdx.x < 32) {
@@ -206,8 +214,8 @@ __global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars 
             if (i < P.qpt && e < P.n4) acc += dot4(zn[i], ldg4(rj, e));
         }
         if (tail) acc = fmaf(zt, rj[et], acc);
-        const double v = warp_sum((double)acc);
-        if (lane == 0) wp[j][warp] = v;
+        acc = warp_sum_f(acc);
+        if (lane == 0) wp[j][warp] = (double)acc;
     }
     __syncthreads();
     for (int j = threadIdx.x; j <= k; j += kVT) {
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(kVT, 3) pcg_reorth_kernel(Part P, const float 
         r[et] = rt;
         acc = fmaf(rt, minv[et] * rt, acc);
     }
-    const double t = block_total((double)acc, red);
+    const double t = block_total(acc, red);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
     if (!last_block(ticket)) return;
     if (threadIdx.x < 32) {
