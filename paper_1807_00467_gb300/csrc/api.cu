@@ -451,12 +451,12 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
         a.err = c->tma_err;
     };
     const int pid = mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1));
-    if (mode == MODE_MATVEC && gn_matvec_supported(c->tg)) {
-        // the GN product reads only the stored linearisation, not the images
+    if ((mode == MODE_MATVEC || mode == MODE_DIAG) && gn_matvec_supported(c->tg)) {
+        // the GN product and its diagonal read only the stored linearisation, not the images
         TileArgs<float> a;
         fill(a);
         a.R = a.T = nullptr;
-        LAUNCH(pid, launch_gn_matvec(a, c->st));
+        LAUNCH(pid, launch_gn_matvec(a, mode == MODE_DIAG, c->st));
         return RG_OK;
     }
     if (c->dtype == RG_F32) {

@@ -72,9 +72,10 @@ __host__ __device__ inline MvSmem mv_smem(const TileGeom &g) {
 
 // P^T along one axis by a sweep over a row of n = C R source values
 // (stride `ss`): node c receives (1 - f_i) v from its own cell and f_i v from
-// the cell below, f_i = (i + 1/2) / R the trilinear weights of the ratio R;
-// writes the C + 1 node values (stride `ds`) times `scale`.
-template <int R, int C>
+// the cell below, f_i = (i + 1/2) / R the trilinear weights of the ratio R
+// (squared weights for the diagonal, SQ); writes the C + 1 node values
+// (stride `ds`) times `scale`.
+template <int R, int C, bool SQ>
 __device__ __forceinline__ void hat_sweep(const float *src, int ss, float *dst, int ds, float scale) {
     float below = 0.f;
 #pragma unroll
@@ -83,8 +84,8 @@ __device__ __forceinline__ void hat_sweep(const float *src, int ss, float *dst, 
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const float v = src[(c * R + i) * ss];
-            own = fmaf(1.f - (i + 0.5f) / R, v, own);
-            up = fmaf((i + 0.5f) / R, v, up);
+            own = fmaf(SQ ? (1.f - (i + 0.5f) / R) * (1.f - (i + 0.5f) / R) : 1.f - (i + 0.5f) / R, v, own);
+            up = fmaf(SQ ? ((i + 0.5f) / R) * ((i + 0.5f) / R) : (i + 0.5f) / R, v, up);
         }
         dst[c * ds] = scale * (below + own);
         below = up;
@@ -94,33 +95,39 @@ __device__ __forceinline__ void hat_sweep(const float *src, int ss, float *dst, 
 
 // x then y reduction of the parked column sums rows[plane][ty][tx][comp] onto
 // the tile's node box [comp][plane][jy][jx] (times 2), through xr[plane][ty][jx][comp]
-template <int RX, int RY>
+template <int RX, int RY, bool SQ>
 __device__ __forceinline__ void node_reduce(const float *rows, float *xr, float *box, int boxsz, int nplanes, int tid) {
     constexpr int TXI = 28 - 28 % RX, CX = TXI / RX, CY = kTY / RY;
     for (int r = tid; r < nplanes * kTY * 3; r += kNT) {
         const int k = r % 3, pr = r / 3;   // pr = plane * kTY + ty
-        hat_sweep<RX, CX>(rows + pr * TXI * 3 + k, 3, xr + pr * (CX + 1) * 3 + k, 3, 1.f);
+        hat_sweep<RX, CX, SQ>(rows + pr * TXI * 3 + k, 3, xr + pr * (CX + 1) * 3 + k, 3, 1.f);
     }
     __syncthreads();
     for (int r = tid; r < nplanes * (CX + 1) * 3; r += kNT) {
         const int k = r % 3, q = r / 3, jx = q % (CX + 1), pl = q / (CX + 1);
-        hat_sweep<RY, CY>(xr + (pl * kTY * (CX + 1) + jx) * 3 + k, (CX + 1) * 3,
-                          box + (long)k * boxsz + pl * (CY + 1) * (CX + 1) + jx, CX + 1, 2.f);
+        hat_sweep<RY, CY, SQ>(xr + (pl * kTY * (CX + 1) + jx) * 3 + k, (CX + 1) * 3,
+                              box + (long)k * boxsz + pl * (CY + 1) * (CX + 1) + jx, CX + 1, SQ ? 1.f : 2.f);
     }
 }
 
-template <int RX>
+template <int RX, bool SQ>
 __device__ __forceinline__ void node_reduce_ry(int ry, const float *rows, float *xr, float *box, int boxsz,
                                                int nplanes, int tid) {
     switch (ry) {
-        case 1: node_reduce<RX, 1>(rows, xr, box, boxsz, nplanes, tid); break;
-        case 2: node_reduce<RX, 2>(rows, xr, box, boxsz, nplanes, tid); break;
-        case 4: node_reduce<RX, 4>(rows, xr, box, boxsz, nplanes, tid); break;
-        default: node_reduce<RX, 8>(rows, xr, box, boxsz, nplanes, tid); break;
+        case 1: node_reduce<RX, 1, SQ>(rows, xr, box, boxsz, nplanes, tid); break;
+        case 2: node_reduce<RX, 2, SQ>(rows, xr, box, boxsz, nplanes, tid); break;
+        case 4: node_reduce<RX, 4, SQ>(rows, xr, box, boxsz, nplanes, tid); break;
+        default: node_reduce<RX, 8, SQ>(rows, xr, box, boxsz, nplanes, tid); break;
     }
 }
 
-template <int RZ>
+// DG = false: the GN product (stages W, C, A above).  DG = true: the Jacobi
+// diagonal of 2 hbar J^T J with the cross terms of the central-difference
+// adjoint left out: per voxel beta = sum_a (a'_a^2 at x - e_a and x + e_a) with
+// a' = a / (2 h), times (dT/dy)_k^2, onto the nodes with squared hat weights.
+// It reuses the pipeline: stage C forms a'^2 instead of c', stage A sums
+// instead of differencing, and P v is not needed.
+template <int RZ, bool DG>
 __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant__ TileArgs<float> a, int chain) {
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) float smem[];
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
             const int ns = min(g.TZ, g.n[2] - z0) + 4;
             for (int j = 0; j < kAhead && j < ns; ++j) issue_plane(x0, y0, z0, j, j);
         }
-        load_nodes(x0, y0, z0);
+        if (!DG) load_nodes(x0, y0, z0);
     }
 
     const float i2h0 = g.inv2h[0], i2h1 = g.inv2h[1], i2h2 = g.inv2h[2];
@@ -229,11 +236,13 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
         __syncthreads();
 
         float U0[3], U1[3], D[3];   // P v at node planes cz, cz + 1 (x-y interpolated), D = U1 - U0
-        {
+        if (!DG) {
             const int cz = (z0 - 2) >> lrz;
             bilinear(cz, U0);
             bilinear(cz + 1, U1);
             for (int k = 0; k < 3; ++k) D[k] = U1[k] - U0[k];
+        } else {
+            for (int k = 0; k < 3; ++k) U0[k] = U1[k] = D[k] = 0.f;
         }
         float tm = 0.f, t0 = 0.f;                  // t at planes pC - 1, pC
         float a1[3] = {0.f, 0.f, 0.f};             // a' at plane pC (read by stage W one plane earlier)
@@ -264,7 +273,7 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
                 }
 
                 // ------------------------------------------------ P v: next node plane at a cell start
-                if (phW == 0 && s > 0) {
+                if (!DG && phW == 0 && s > 0) {
                     U0[0] = U1[0]; U0[1] = U1[1]; U0[2] = U1[2];
                     bilinear((pW >> lrz) + 1, U1);
                     D[0] = U1[0] - U0[0]; D[1] = U1[1] - U0[1]; D[2] = U1[2] - U0[2];
@@ -281,16 +290,30 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
                 // ------------------------------------------------ stage C: c' at plane pC = pW - 1
                 const int b = (j & 1) * kEx;
                 const float txl = __shfl_up_sync(FULL, t0, 1), txr = __shfl_down_sync(FULL, t0, 1);
-                const float dr = fmaf(a1[2], tp - tm, fmaf(a1[1], ex_t[b + dn] - ex_t[b + up], a1[0] * (txr - txl)));
-                const float c0 = dr * a1[0], c1 = dr * a1[1], c2 = dr * a1[2];
+                float c0, c1, c2;
+                if (DG) {   // a'^2 of plane pC
+                    c0 = a1[0] * a1[0]; c1 = a1[1] * a1[1]; c2 = a1[2] * a1[2];
+                } else {
+                    const float dr = fmaf(a1[2], tp - tm, fmaf(a1[1], ex_t[b + dn] - ex_t[b + up], a1[0] * (txr - txl)));
+                    c0 = dr * a1[0]; c1 = dr * a1[1]; c2 = dr * a1[2];
+                }
 
                 // ------------------------------------------------ stage A: G^T c at plane pA = pW - 2, times dT/dy
                 const float cxl = __shfl_up_sync(FULL, cxp, 1), cxr = __shfl_down_sync(FULL, cxp, 1);
                 if (j >= 4 || s0 > 0) {   // planes of the chunk (pA >= z0)
-                    const float bsum = (cxl - cxr) + (ex_c[b + up] - ex_c[b + dn]) + (czm2 - c2);
-                    const float b1 = wz1 * bsum, b0 = bsum - b1;
-                    acc0[0] = fmaf(b0, d2[0], acc0[0]); acc0[1] = fmaf(b0, d2[1], acc0[1]); acc0[2] = fmaf(b0, d2[2], acc0[2]);
-                    acc1[0] = fmaf(b1, d2[0], acc1[0]); acc1[1] = fmaf(b1, d2[1], acc1[1]); acc1[2] = fmaf(b1, d2[2], acc1[2]);
+                    if (DG) {
+                        // beta (x - e_a and x + e_a terms), times (dT/dy)^2, squared z weights
+                        const float beta = (cxl + cxr) + (ex_c[b + up] + ex_c[b + dn]) + (czm2 + c2);
+                        const float b1 = wz1 * wz1 * beta, b0 = (1.f - wz1) * (1.f - wz1) * beta;
+                        const float q0 = d2[0] * d2[0], q1 = d2[1] * d2[1], q2 = d2[2] * d2[2];
+                        acc0[0] = fmaf(b0, q0, acc0[0]); acc0[1] = fmaf(b0, q1, acc0[1]); acc0[2] = fmaf(b0, q2, acc0[2]);
+                        acc1[0] = fmaf(b1, q0, acc1[0]); acc1[1] = fmaf(b1, q1, acc1[1]); acc1[2] = fmaf(b1, q2, acc1[2]);
+                    } else {
+                        const float bsum = (cxl - cxr) + (ex_c[b + up] - ex_c[b + dn]) + (czm2 - c2);
+                        const float b1 = wz1 * bsum, b0 = bsum - b1;
+                        acc0[0] = fmaf(b0, d2[0], acc0[0]); acc0[1] = fmaf(b0, d2[1], acc0[1]); acc0[2] = fmaf(b0, d2[2], acc0[2]);
+                        acc1[0] = fmaf(b1, d2[0], acc1[0]); acc1[1] = fmaf(b1, d2[1], acc1[1]); acc1[2] = fmaf(b1, d2[2], acc1[2]);
+                    }
                     if (phA == (RZ ? RZ - 1 : rzm)) {
                         // node plane (pA - z0) / rho_z is complete for this column: park it
                         if (own_col) {
@@ -321,16 +344,16 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
 
         // the next tile's node planes (no thread reads the node tile any more),
         // while its first TMA planes are in flight
-        if (has_next) load_nodes(xn, yn, zn);
+        if (!DG && has_next) load_nodes(xn, yn, zn);
 
         // ------------------------------------------------ x then y reduction onto the tile's node box
         {
             const int nplanes = (TZc >> lrz) + 1;
             float *box = a.boxes + (long)t * 3 * g.box;
             switch (g.rho[0]) {
-                case 2: node_reduce_ry<2>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
-                case 4: node_reduce_ry<4>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
-                default: node_reduce_ry<8>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
+                case 2: node_reduce_ry<2, DG>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
+                case 4: node_reduce_ry<4, DG>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
+                default: node_reduce_ry<8, DG>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
             }
         }
         if (!has_next) break;
@@ -346,7 +369,7 @@ bool gn_matvec_supported(const TileGeom &g) {
     return (size_t)s.total * sizeof(float) <= 227u * 1024u;
 }
 
-cudaError_t launch_gn_matvec(const TileArgs<float> &a, cudaStream_t st) {
+cudaError_t launch_gn_matvec(const TileArgs<float> &a, bool diag, cudaStream_t st) {
     if (!gn_matvec_supported(a.g)) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * (size_t)mv_smem(a.g).total;
     const int ntiles = a.g.nb[0] * a.g.nb[1] * a.g.nb[2];
@@ -368,11 +391,15 @@ cudaError_t launch_gn_matvec(const TileArgs<float> &a, cudaStream_t st) {
         kernel<<<grid, kNT, smem, st>>>(a, chain);
         return cudaGetLastError();
     };
-    switch (a.g.rho[2]) {
-        case 1: return run(gn_matvec_kernel<1>);
-        case 2: return run(gn_matvec_kernel<2>);
-        case 4: return run(gn_matvec_kernel<4>);
-        default: return run(gn_matvec_kernel<0>);   // rho_z = 8: phases from the plane index
+    switch (a.g.rho[2] * 2 + (diag ? 1 : 0)) {
+        case 2: return run(gn_matvec_kernel<1, false>);
+        case 3: return run(gn_matvec_kernel<1, true>);
+        case 4: return run(gn_matvec_kernel<2, false>);
+        case 5: return run(gn_matvec_kernel<2, true>);
+        case 8: return run(gn_matvec_kernel<4, false>);
+        case 9: return run(gn_matvec_kernel<4, true>);
+        case 17: return run(gn_matvec_kernel<0, true>);   // rho_z = 8: phases from the plane index
+        default: return run(gn_matvec_kernel<0, false>);
     }
 }
 

@@ -86,9 +86,13 @@ def test_gn_matvec_dedicated_kernel_matches_general_kernel(n, h, m):
     v = to_dev(phantom.random_grid_field(m, 21))
     ctx.set_tile(8)
     h8 = ctx.gn_matvec(v).cpu().numpy()
+    p8, _ = ctx.gn_pcg_solve(v, 5)          # Jacobi diagonal from the general kernel
+    p8 = p8.cpu().numpy()
     ctx.set_tile(16)
     h16 = ctx.gn_matvec(v).cpu().numpy()
+    p16, _ = ctx.gn_pcg_solve(v, 5)         # ... and from the dedicated kernel
     assert rel_l2(h16, h8) <= 1e-6
+    assert rel_l2(p16.cpu().numpy(), p8) <= 1e-5
 
 
 def test_linearize_gradient_matches_plain_gradient(tiny):
