@@ -459,18 +459,22 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
         LAUNCH(pid, launch_gn_matvec(a, mode == MODE_DIAG, c->st));
         return RG_OK;
     }
+    // objective, gradient and linearisation: the persistent pass where the tile shape allows
+    const bool grad_kernel = mode != MODE_MATVEC && mode != MODE_DIAG && ngf_grad_supported(c->tg);
     if (c->dtype == RG_F32) {
         TileArgs<float> a;
         fill(a);
         a.R = (const float *)c->R;
         a.T = (const float *)c->T;
-        LAUNCH(pid, launch_ngf_tile(mode, a, c->st));
+        if (grad_kernel) LAUNCH(pid, launch_ngf_grad(mode, a, c->st));
+        else LAUNCH(pid, launch_ngf_tile(mode, a, c->st));
     } else {
         TileArgs<__half> a;
         fill(a);
         a.R = (const __half *)c->R;
         a.T = (const __half *)c->T;
-        LAUNCH(pid, launch_ngf_tile(mode, a, c->st));
+        if (grad_kernel) LAUNCH(pid, launch_ngf_grad(mode, a, c->st));
+        else LAUNCH(pid, launch_ngf_tile(mode, a, c->st));
     }
     return RG_OK;
 }

@@ -16,6 +16,11 @@ cudaError_t launch_ngf_tile(int mode, const TileArgs<__half> &a, cudaStream_t st
 // Dedicated GN-product kernel (stored linearisation streamed by TMA); same
 // tile and node-box layout as MODE_MATVEC (diag: MODE_DIAG) of the general kernel.
 bool gn_matvec_supported(const TileGeom &g);
+// Objective / gradient / linearisation pass (MODE_OBJ, MODE_GRAD, MODE_GRADLIN,
+// MODE_LIN as GRADLIN) on persistent CTAs; same tile and node-box layout.
+bool ngf_grad_supported(const TileGeom &g);
+cudaError_t launch_ngf_grad(int mode, const TileArgs<float> &a, cudaStream_t st);
+cudaError_t launch_ngf_grad(int mode, const TileArgs<__half> &a, cudaStream_t st);
 cudaError_t launch_gn_matvec(const TileArgs<float> &a, bool diag, cudaStream_t st);
 
 // Volume change control, Eqs. (7)-(9): per grid cell the 64 bounds d_abc.

@@ -36,6 +36,7 @@
 //    tile are fetched during the current tile's reduction.
 #include "common.cuh"
 #include "kernels.h"
+#include "node_sweep.cuh"
 #include "tma.cuh"
 
 namespace ngf {
@@ -68,57 +69,6 @@ __host__ __device__ inline MvSmem mv_smem(const TileGeom &g) {
     s.xr = off; off += (g.C[2] + 1) * kTY * (g.C[0] + 1) * 3;   // x-reduced sums
     s.total = off;
     return s;
-}
-
-// P^T along one axis by a sweep over a row of n = C R source values
-// (stride `ss`): node c receives (1 - f_i) v from its own cell and f_i v from
-// the cell below, f_i = (i + 1/2) / R the trilinear weights of the ratio R
-// (squared weights for the diagonal, SQ); writes the C + 1 node values
-// (stride `ds`) times `scale`.
-template <int R, int C, bool SQ>
-__device__ __forceinline__ void hat_sweep(const float *src, int ss, float *dst, int ds, float scale) {
-    float below = 0.f;
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        float own = 0.f, up = 0.f;
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const float v = src[(c * R + i) * ss];
-            own = fmaf(SQ ? (1.f - (i + 0.5f) / R) * (1.f - (i + 0.5f) / R) : 1.f - (i + 0.5f) / R, v, own);
-            up = fmaf(SQ ? ((i + 0.5f) / R) * ((i + 0.5f) / R) : (i + 0.5f) / R, v, up);
-        }
-        dst[c * ds] = scale * (below + own);
-        below = up;
-    }
-    dst[C * ds] = scale * below;
-}
-
-// x then y reduction of the parked column sums rows[plane][ty][tx][comp] onto
-// the tile's node box [comp][plane][jy][jx] (times 2), through xr[plane][ty][jx][comp]
-template <int RX, int RY, bool SQ>
-__device__ __forceinline__ void node_reduce(const float *rows, float *xr, float *box, int boxsz, int nplanes, int tid) {
-    constexpr int TXI = 28 - 28 % RX, CX = TXI / RX, CY = kTY / RY;
-    for (int r = tid; r < nplanes * kTY * 3; r += kNT) {
-        const int k = r % 3, pr = r / 3;   // pr = plane * kTY + ty
-        hat_sweep<RX, CX, SQ>(rows + pr * TXI * 3 + k, 3, xr + pr * (CX + 1) * 3 + k, 3, 1.f);
-    }
-    __syncthreads();
-    for (int r = tid; r < nplanes * (CX + 1) * 3; r += kNT) {
-        const int k = r % 3, q = r / 3, jx = q % (CX + 1), pl = q / (CX + 1);
-        hat_sweep<RY, CY, SQ>(xr + (pl * kTY * (CX + 1) + jx) * 3 + k, (CX + 1) * 3,
-                              box + (long)k * boxsz + pl * (CY + 1) * (CX + 1) + jx, CX + 1, SQ ? 1.f : 2.f);
-    }
-}
-
-template <int RX, bool SQ>
-__device__ __forceinline__ void node_reduce_ry(int ry, const float *rows, float *xr, float *box, int boxsz,
-                                               int nplanes, int tid) {
-    switch (ry) {
-        case 1: node_reduce<RX, 1, SQ>(rows, xr, box, boxsz, nplanes, tid); break;
-        case 2: node_reduce<RX, 2, SQ>(rows, xr, box, boxsz, nplanes, tid); break;
-        case 4: node_reduce<RX, 4, SQ>(rows, xr, box, boxsz, nplanes, tid); break;
-        default: node_reduce<RX, 8, SQ>(rows, xr, box, boxsz, nplanes, tid); break;
-    }
 }
 
 // DG = false: the GN product (stages W, C, A above).  DG = true: the Jacobi
@@ -350,11 +300,7 @@ __global__ void __launch_bounds__(kNT, 1) gn_matvec_kernel(const __grid_constant
         {
             const int nplanes = (TZc >> lrz) + 1;
             float *box = a.boxes + (long)t * 3 * g.box;
-            switch (g.rho[0]) {
-                case 2: node_reduce_ry<2, DG>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
-                case 4: node_reduce_ry<4, DG>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
-                default: node_reduce_ry<8, DG>(g.rho[1], rows, xr, box, g.box, nplanes, tid); break;
-            }
+            node_reduce_any<kTY, kNT, DG>(g.rho[0], g.rho[1], rows, xr, box, g.box, nplanes, DG ? 1.f : 2.f, tid);
         }
         if (!has_next) break;
         t = tn;
