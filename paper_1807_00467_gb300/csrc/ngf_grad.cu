@@ -14,7 +14,8 @@
 //                 c = d(1 - r^2)/dg scaled by 1/(2h) for the adjoint
 //   A (plane pW - 2): adjoint of the central difference of c, times dT/dy,
 //                 accumulated onto the column's two z-node planes
-// The objective-only mode runs W and C (one plane of z halo).  Samples outside
+// The objective-only pass (ngf_obj_kernel) runs W and C (one plane of z halo)
+// and issues each plane's template samples a plane early.  Samples outside
 // the volume are placed on clamped cells (zero derivative along a clamped
 // axis); voxels that are not interior contribute nothing and get a = 0.
 #include "common.cuh"
@@ -53,7 +54,9 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 
 }  // namespace
 
-// MODE: MODE_OBJ, MODE_GRAD or MODE_GRADLIN (gradient + stored linearisation).
+// MODE: MODE_GRAD or MODE_GRADLIN (gradient + stored linearisation); the
+// objective-only mode of this kernel is kept for reference, the launcher uses
+// ngf_obj_kernel below.
 template <int MODE, typename TImg, int RZ>
 __global__ void __launch_bounds__(kNT, 1) ngf_grad_kernel(const __grid_constant__ TileArgs<TImg> a) {
     constexpr bool ADJ = MODE != MODE_OBJ, STORE = MODE == MODE_GRADLIN;
@@ -306,6 +309,175 @@ __global__ void __launch_bounds__(kNT, 1) ngf_grad_kernel(const __grid_constant_
     }
 }
 
+// Objective only (line search): stages W and C with one plane of z halo.  The
+// template samples of the next W plane (and R) are issued at the end of each
+// plane, so that their latency overlaps the barrier.
+template <typename TImg, int RZ>
+__global__ void __launch_bounds__(kNT, 1) ngf_obj_kernel(const __grid_constant__ TileArgs<TImg> a) {
+    constexpr int HZ = 1;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) float smem[];
+    const TileGeom &g = a.g;
+    const GrSmem S = gr_smem(g, false);
+
+    const int tid = threadIdx.x, L = tid & 31, w = tid >> 5;
+    const int TXI = g.TXI, nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int sxy = nx * ny;
+    const int ntiles = g.nb[0] * g.nb[1] * g.nb[2];
+    const int lrx = g.lrho[0], lry = g.lrho[1], lrz = g.lrho[2];
+    const int rzm = g.rho[2] - 1;
+    const float irz = g.irho[2];
+    const int nxt = g.nxt, nyt = g.nyt, nplane = nxt * nyt;
+    float4 *s_nodes = reinterpret_cast<float4 *>(smem + S.nodes);
+    float *ex_t = smem + S.ext + w * 32 + L, *ex_r = smem + S.exr + w * 32 + L;
+    const int up = w > 0 ? -32 : 0, dn = w < kNW - 1 ? 32 : 0;
+    const bool own_col = w >= 2 && w < kTY + 2 && L >= 2 && L < TXI + 2;
+    const float ih0 = g.invh[0], ih1 = g.invh[1], ih2 = g.invh[2];
+    const float i2h0 = g.inv2h[0], i2h1 = g.inv2h[1], i2h2 = g.inv2h[2], eta2 = g.eta2;
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int bx = t % g.nb[0], rr = t / g.nb[0];
+        const int x0 = bx * TXI, y0 = (rr % g.nb[1]) * kTY, z0 = (rr / g.nb[1]) * g.TZ;
+        const int TZc = min(g.TZ, nz - z0);
+        const int nsteps = TZc + 2 * HZ;
+        const int kx_lo = max(x0 - 2, 0) >> lrx, ky_lo = max(y0 - 2, 0) >> lry, kz_lo = (z0 - HZ) >> lrz;
+
+        __syncthreads();
+        {
+            const int mxy = g.m[0] * g.m[1], Mn = mxy * g.m[2];
+            for (int i = tid; i < g.nzt * nplane; i += kNT) {
+                const int pl = i / nplane, r = i - pl * nplane;
+                const int ly = r / nxt, lx = r - ly * nxt;
+                const int ux = kx_lo + lx, uy = ky_lo + ly, kz = kz_lo + pl;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ux < g.m[0] && uy < g.m[1] && kz >= 0 && kz < g.m[2]) {
+                    const int q = kz * mxy + uy * g.m[0] + ux;
+                    v.x = __ldg(a.u + q);
+                    v.y = __ldg(a.u + Mn + q);
+                    v.z = __ldg(a.u + 2 * Mn + q);
+                }
+                s_nodes[i] = v;
+            }
+        }
+        const int gx = x0 - 2 + L, gy = y0 - 2 + w;
+        const bool colin = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        const bool intxy = colin && gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2;
+        const int col = colin ? gy * nx + gx : 0;
+        const int cxg = gx >> lrx, cyg = gy >> lry;
+        const float fx = ((gx - (cxg << lrx)) + 0.5f) * g.irho[0];
+        const float fy = ((gy - (cyg << lry)) + 0.5f) * g.irho[1];
+        const float4 *qcol = s_nodes + min(max(cyg - ky_lo, 0), nyt - 2) * nxt + min(max(cxg - kx_lo, 0), nxt - 2);
+        auto bilinear = [&](int kz, float *U) {
+            const float4 *q = qcol + (kz - kz_lo) * nplane;
+            const float4 n00 = q[0], n10 = q[1], n01 = q[nxt], n11 = q[nxt + 1];
+            const float wx0 = 1.f - fx, wy0 = 1.f - fy;
+            U[0] = lerp_fixed(lerp_fixed(n00.x, n10.x, wx0, fx), lerp_fixed(n01.x, n11.x, wx0, fx), wy0, fy);
+            U[1] = lerp_fixed(lerp_fixed(n00.y, n10.y, wx0, fx), lerp_fixed(n01.y, n11.y, wx0, fx), wy0, fy);
+            U[2] = lerp_fixed(lerp_fixed(n00.z, n10.z, wx0, fx), lerp_fixed(n01.z, n11.z, wx0, fx), wy0, fy);
+        };
+        __syncthreads();
+
+        float U0[3], U1[3];
+        bilinear((z0 - HZ) >> lrz, U0);
+        bilinear(((z0 - HZ) >> lrz) + 1, U1);
+        float tm = 0.f, t0 = 0.f, rm = 0.f, r0 = 0.f;
+        float dsum = 0.f, dcomp = 0.f;
+        // pending samples of the next W plane: the 8 template values, the
+        // fractions, and R
+        float smp[8], sf[3], srv;
+        auto issue_sample = [&](int pW, float fz) {
+            const float pu[3] = {lerp_fixed(U0[0], U1[0], 1.f - fz, fz), lerp_fixed(U0[1], U1[1], 1.f - fz, fz),
+                                 lerp_fixed(U0[2], U1[2], 1.f - fz, fz)};
+            const float ih[3] = {ih0, ih1, ih2};
+            const int ii[3] = {gx, gy, pW}, nn[3] = {nx, ny, nz};
+            int c[3], st[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                // the same FP32 cell decision and placement as the gradient pass
+                const float q = __fmul_rn(pu[ax], ih[ax]);
+                const float fl = floorf(q);
+                const float e = __fmaf_rn(pu[ax], ih[ax], -q);
+                const float fr = (q - fl) + __fmaf_rn(q, g.invh_rel[ax], e);
+                const int k = ii[ax] + (int)fl;
+                const bool lo = k < 0, hi = k >= nn[ax] - 1;
+                c[ax] = lo ? 0 : (hi ? nn[ax] - 1 : k);
+                st[ax] = hi ? -1 : 1;
+                sf[ax] = (lo || hi) ? 0.f : fr;
+            }
+            const int sx = st[0], sy = st[1] * nx, sz = st[2] * sxy;
+            const TImg *T = a.T + (c[2] * sxy + c[1] * nx + c[0]);
+            smp[0] = ldimg(T, 0); smp[1] = ldimg(T, sx); smp[2] = ldimg(T, sy); smp[3] = ldimg(T, sy + sx);
+            smp[4] = ldimg(T, sz); smp[5] = ldimg(T, sz + sx); smp[6] = ldimg(T, sz + sy); smp[7] = ldimg(T, sz + sy + sx);
+            srv = (colin && pW >= 0 && pW < nz) ? ldimg(a.R, pW * sxy + col) : 0.f;
+        };
+        issue_sample(z0 - HZ, (((z0 - HZ) & rzm) + 0.5f) * irz);
+
+        for (int s0 = 0; s0 < nsteps; s0 += 2) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int s = s0 + j;
+                if (s >= nsteps) break;
+                const int pW = z0 - HZ + s, pC = pW - 1;
+                __syncthreads();
+                // ------------------------------------------------ stage W: plane pW (samples issued before)
+                const float rv = srv;
+                float val;
+                {
+                    const float dx00 = smp[1] - smp[0], dx10 = smp[3] - smp[2], dx01 = smp[5] - smp[4], dx11 = smp[7] - smp[6];
+                    const float v00 = fmaf(sf[0], dx00, smp[0]), v10 = fmaf(sf[0], dx10, smp[2]);
+                    const float v01 = fmaf(sf[0], dx01, smp[4]), v11 = fmaf(sf[0], dx11, smp[6]);
+                    const float w0 = fmaf(sf[1], v10 - v00, v00), w1 = fmaf(sf[1], v11 - v01, v01);
+                    val = fmaf(sf[2], w1 - w0, w0);
+                }
+                // ------------------------------------------------ stage C: 1 - r^2 at plane pC
+                const int b = (j & 1) * kEx;
+                {
+                    const float tl = __shfl_up_sync(FULL, t0, 1), tr = __shfl_down_sync(FULL, t0, 1);
+                    const float rl = __shfl_up_sync(FULL, r0, 1), rr2 = __shfl_down_sync(FULL, r0, 1);
+                    const float g0 = (tr - tl) * i2h0, g1 = (ex_t[b + dn] - ex_t[b + up]) * i2h1, g2 = (val - tm) * i2h2;
+                    const float f0 = (rr2 - rl) * i2h0, f1 = (ex_r[b + dn] - ex_r[b + up]) * i2h1, f2 = (rv - rm) * i2h2;
+                    const float ff = __fmaf_rn(f2, f2, __fmaf_rn(f1, f1, __fmaf_rn(f0, f0, eta2)));
+                    const float gg = __fmaf_rn(g2, g2, __fmaf_rn(g1, g1, __fmaf_rn(g0, g0, eta2)));
+                    const float rff = __frcp_rn(ff), rgg = __frcp_rn(gg);
+                    const bool interior = intxy && pC >= 1 && pC <= nz - 2;
+                    const bool own = own_col && pC >= z0 && pC < z0 + TZc;
+                    const float x0_ = __fmul_rn(f1, g2) - __fmul_rn(f2, g1);
+                    const float x1_ = __fmul_rn(f2, g0) - __fmul_rn(f0, g2);
+                    const float x2_ = __fmul_rn(f0, g1) - __fmul_rn(f1, g0);
+                    const float e0 = f0 - g0, e1 = f1 - g1, e2 = f2 - g2;
+                    const float num = x0_ * x0_ + x1_ * x1_ + x2_ * x2_ + eta2 * (e0 * e0 + e1 * e1 + e2 * e2);
+                    kahan_add(dsum, dcomp, (own && interior) ? num * rff * rgg : 0.f);
+                }
+                // ------------------------------------------------ hand over to the next plane
+                ex_t[kEx - b] = val;
+                ex_r[kEx - b] = rv;
+                tm = t0; t0 = val;
+                rm = r0; r0 = rv;
+                if (s + 1 < nsteps) {
+                    const int phN = RZ ? ((j + 1 - HZ) & (RZ - 1)) : ((pW + 1) & rzm);
+                    if (phN == 0) {
+                        U0[0] = U1[0]; U0[1] = U1[1]; U0[2] = U1[2];
+                        bilinear(((pW + 1) >> lrz) + 1, U1);
+                    }
+                    issue_sample(pW + 1, RZ ? (phN + 0.5f) / (float)(RZ ? RZ : 1) : (phN + 0.5f) * irz);
+                }
+            }
+        }
+        {
+            double v = (double)dsum - (double)dcomp;
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+            __shared__ double red[kNW];
+            if (L == 0) red[w] = v;
+            __syncthreads();
+            if (tid == 0) {
+                double s = 0.0;
+                for (int i = 0; i < kNW; ++i) s += red[i];
+                a.dpart[t] = s;
+            }
+        }
+    }
+}
+
 bool ngf_grad_supported(const TileGeom &g) {
     if (g.TY != kTY || g.nzt <= 0 || g.rho[0] < 2) return false;
     return (size_t)gr_smem(g, true).total * sizeof(float) <= 227u * 1024u;
@@ -333,7 +505,7 @@ static cudaError_t launch_grad(int mode, const TileArgs<TImg> &a, cudaStream_t s
     };
     const bool r2 = a.g.rho[2] == 2;
     switch (mode) {
-        case MODE_OBJ: return r2 ? run(ngf_grad_kernel<MODE_OBJ, TImg, 2>) : run(ngf_grad_kernel<MODE_OBJ, TImg, 0>);
+        case MODE_OBJ: return r2 ? run(ngf_obj_kernel<TImg, 2>) : run(ngf_obj_kernel<TImg, 0>);
         case MODE_GRAD: return r2 ? run(ngf_grad_kernel<MODE_GRAD, TImg, 2>) : run(ngf_grad_kernel<MODE_GRAD, TImg, 0>);
         case MODE_GRADLIN:
         case MODE_LIN:
