@@ -42,7 +42,7 @@ WORKLOAD = "512x512x128 FP32, 0.7x0.7x2.5 mm, grid 129x129x65, eta=10 alpha=1 ga
 
 # kernel ids of rg_profile_read
 K_MATVEC, K_GRADLIN, K_OBJ, K_VCC, K_VCC_GN, K_CURV, K_FIN, K_KP, K_TERMS, K_VEC, K_OTHER = range(11)
-KNAMES = {K_MATVEC: "gn_matvec", K_GRADLIN: "ngf_tile_grad_lin", K_OBJ: "ngf_tile_obj", K_VCC: "vcc_grad",
+KNAMES = {K_MATVEC: "gn_matvec", K_GRADLIN: "ngf_grad_lin", K_OBJ: "ngf_obj", K_VCC: "vcc_grad",
           K_VCC_GN: "vcc_gn", K_CURV: "curv_L", K_FIN: "finalize_nodes", K_KP: "keypoints", K_TERMS: "terms",
           K_VEC: "pcg_vector", K_OTHER: "other"}
 
@@ -84,8 +84,8 @@ def alg_bytes(kernel, N, M):
 
 
 # source file of each timed kernel (the recorded ncu traffic is used only while it is unchanged)
-KSRC = {K_MATVEC: "ngf_matvec.cu", K_GRADLIN: "ngf_tile.cu", K_OBJ: "ngf_tile.cu", K_VCC: "vcc.cu", K_VCC_GN: "vcc.cu",
-        K_CURV: "reg_kernels.cu", K_FIN: "reg_kernels.cu", K_VEC: "pcg.cu"}
+KSRC = {K_MATVEC: "ngf_matvec.cu", K_GRADLIN: "ngf_grad.cu", K_OBJ: "ngf_grad.cu", K_VCC: "vcc.cu", K_VCC_GN: "vcc.cu",
+        K_CURV: "nodes.cu", K_FIN: "nodes.cu", K_VEC: "pcg.cu"}
 
 
 def recorded_traffic(kernel):
