@@ -211,6 +211,64 @@ def cpu_baseline(ph, m, seconds):
             "sample": f"{n} oracle GN products at 512x512x128 ({dt:.1f} s, after one untimed linearisation)"}
 
 
+def small_config_rates(name, reps, dev):
+    """Objective+gradient evaluations/s and GN products/s at a small workload,
+    issued eagerly and replayed from a CUDA graph captured on the context's stream."""
+    import torch
+
+    from paper_1807_00467_gb300 import api, phantom
+    c = phantom.CONFIGS[name]
+    ph = phantom.make_phantom(c["n"], c["h"], seed=0, motion=c["motion"])
+    m = c["m"]
+    s = torch.cuda.Stream(device=dev)
+    R, T = torch.from_numpy(ph.R).to(dev), torch.from_numpy(ph.T).to(dev)
+    ctx = api.Context(R, T, ph.h, m, api.make_params(eta=10.0, alpha=1.0, gamma=0.001), stream=s)
+    u = torch.from_numpy(phantom.motion_on_grid(ph, m, 0.5)).to(dev)
+    v = torch.from_numpy(phantom.random_grid_field(m, 100)).to(dev)
+    g, hv = torch.empty_like(u), torch.empty_like(u)
+    terms = torch.empty(5, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(s):
+        ctx.gn_linearize(u)
+        for _ in range(3):
+            ctx.ngf_gradient(u, g, terms)
+            ctx.gn_matvec(v, hv)
+    s.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    out = {"workload": f"{c['n'][0]}x{c['n'][1]}x{c['n'][2]}, grid {m[0]}x{m[1]}x{m[2]}"}
+    with torch.cuda.stream(s):
+        ev[0].record(s)
+        for _ in range(reps):
+            ctx.ngf_gradient(u, g, terms)
+        ev[1].record(s)
+        for _ in range(reps):
+            ctx.gn_matvec(v, hv)
+        ev[2].record(s)
+    s.synchronize()
+    out["obj_grad_evals_per_s"] = reps / (ev[0].elapsed_time(ev[1]) / 1e3)
+    out["gn_matvec_per_s"] = reps / (ev[1].elapsed_time(ev[2]) / 1e3)
+    graphs = []
+    for call in (lambda: ctx.ngf_gradient(u, g, terms), lambda: ctx.gn_matvec(v, hv)):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=s, capture_error_mode="relaxed"):
+            call()
+        graphs.append(gr)
+    for gr in graphs:
+        gr.replay()
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(s):
+        ev[0].record(s)
+        for _ in range(reps):
+            graphs[0].replay()
+        ev[1].record(s)
+        for _ in range(reps):
+            graphs[1].replay()
+        ev[2].record(s)
+    s.synchronize()
+    out["graph_obj_grad_evals_per_s"] = reps / (ev[0].elapsed_time(ev[1]) / 1e3)
+    out["graph_gn_matvec_per_s"] = reps / (ev[1].elapsed_time(ev[2]) / 1e3)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -365,6 +423,8 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         out["solve_s"] = time.perf_counter() - t0
         out["solve_config"] = "3 levels x 10 GN x 30 PCG, Armijo; 128x128x32 -> 512x512x128"
+        # the small workloads are launch- and latency-bound: eager vs CUDA-graph replay
+        out["small"] = {name: small_config_rates(name, 200, dev) for name in ("tiny", "mid")}
         # precision form: images stored as FP16 (HU + 1024), FP32 per-voxel arithmetic
         with torch.cuda.stream(stream):
             R16 = (R + 1024.0).half()

@@ -361,3 +361,37 @@ def test_full_size_objective_gradient_matvec():
     assert rel(terms[4].item(), ot[4]) <= TOL_OBJ
     assert eg <= TOL_GRAD
     assert em <= TOL_MV
+
+
+def test_entry_points_replay_in_a_cuda_graph(tiny):
+    """Objective+gradient, GN product and PCG solve captured on the context's
+    stream (outputs preallocated, after one eager call) replay to the same bits."""
+    import torch
+
+    from paper_1807_00467_gb300 import api
+    s = torch.cuda.Stream()
+    R, T = torch.from_numpy(tiny.R).cuda(), torch.from_numpy(tiny.T).cuda()
+    ctx = api.Context(R, T, tiny.h, TINY_M, api.make_params(eta=10.0, alpha=1.0, gamma=0.001), stream=s)
+    u = to_dev(_u0(tiny, TINY_M))
+    v = to_dev(phantom.random_grid_field(TINY_M, 23))
+    g, terms, hv, p = (torch.empty_like(u), torch.empty(5, dtype=torch.float64, device="cuda"),
+                       torch.empty_like(u), torch.empty_like(u))
+    with torch.cuda.stream(s):
+        ctx.gn_linearize(u)
+        ctx.ngf_gradient(u, g, terms)
+        ctx.gn_matvec(v, hv)
+        ctx.gn_pcg_solve(v, 10, p)
+    s.synchronize()
+    eager = [x.clone() for x in (g, terms, hv, p)]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s, capture_error_mode="relaxed"):
+        ctx.ngf_gradient(u, g, terms)
+        ctx.gn_matvec(v, hv)
+        ctx.gn_pcg_solve(v, 10, p)
+    for x in (g, terms, hv, p):
+        x.zero_()
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        for a, b in zip((g, terms, hv, p), eager):
+            assert torch.equal(a, b)
