@@ -211,6 +211,23 @@ def cpu_baseline(ph, m, seconds):
             "sample": f"{n} oracle GN products at 512x512x128 ({dt:.1f} s, after one untimed linearisation)"}
 
 
+def replica_seed(rank):
+    """Each rank registers its own phantom pair (replicas: no data-path collective)."""
+    return rank
+
+
+def aggregate_ranks(ms, matvecs, dist=None, device=None):
+    """Whole-job throughput: the slowest rank's time and the products of all ranks."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    mv = torch.tensor([float(matvecs)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(mv, op=dist.ReduceOp.SUM)
+    ms_max, mv_total = float(t.item()), float(mv.item())
+    return ms_max, mv_total, mv_total / (ms_max / 1e3)
+
+
 def small_config_rates(name, reps, dev):
     """Objective+gradient evaluations/s and GN products/s at a small workload,
     issued eagerly and replayed from a CUDA graph captured on the context's stream."""
@@ -286,7 +303,7 @@ def run_ours(args):
 
     c = phantom.CONFIGS["full"]
     n, h, m = c["n"], c["h"], c["m"]
-    ph = phantom.make_phantom(n, h, seed=rank, motion=c["motion"])
+    ph = phantom.make_phantom(n, h, seed=replica_seed(rank), motion=c["motion"])
     N, M = n[0] * n[1] * n[2], m[0] * m[1] * m[2]
     stream = torch.cuda.Stream(device=dev)
     params = api.make_params(eta=10.0, alpha=1.0, gamma=0.001)
@@ -337,13 +354,7 @@ def run_ours(args):
     ctx.profile(False)
     clk = clocks.stop()
 
-    local_ms = torch.tensor([ms], dtype=torch.float64, device=dev)
-    local_mv = torch.tensor([float(matvecs)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(local_ms, op=dist.ReduceOp.MAX)
-        dist.all_reduce(local_mv, op=dist.ReduceOp.SUM)
-    ms_max, mv_total = float(local_ms.item()), float(local_mv.item())
-    value = mv_total / (ms_max / 1e3)
+    ms_max, mv_total, value = aggregate_ranks(ms, matvecs, dist, dev)
 
     # roofline of the dominant kernel (largest share of the timed region)
     peak, peak_kind = peaks()
