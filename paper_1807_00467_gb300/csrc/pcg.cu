@@ -14,6 +14,7 @@
 #include "ngfreg.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "lastblock.cuh"
 
 namespace ngf {
 
@@ -25,26 +26,14 @@ constexpr int kQmax = 8;            // quads per thread at most
 constexpr int kHist = RG_PCG_MAX + 1;
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
-    return v;
-}
-
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
     return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
-}
-
-// FP32 warp sum (fixed shuffle tree); FP64 is ~1/64 of the FP32 rate on this
-// part, so only the per-warp partials are widened
-__device__ __forceinline__ float warp_sum_f(float v) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
-    return v;
 }
 
 // Block sum of a per-thread value (FP32 within a warp, FP64 across warps);
 // the result is valid in thread 0.
 __device__ __forceinline__ double block_total(float v, double *red) {
-    v = warp_sum_f(v);
+    v = lb_warp_sum_f(v);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
     __syncthreads();
     double t = 0.0;
@@ -52,30 +41,6 @@ __device__ __forceinline__ double block_total(float v, double *red) {
         for (int i = 0; i < kVW; ++i) t += red[i];
     __syncthreads();
     return t;
-}
-
-// Sum of part[0..n) in a fixed order (lane-strided, then a fixed shuffle
-// tree) by one warp; valid in every lane.
-__device__ __forceinline__ double warp_sum_parts(const double *part, int n) {
-    double s = 0.0;
-    for (int i = threadIdx.x & 31; i < n; i += 32) s += __ldcg(part + i);
-    return warp_sum(s);
-}
-
-// True in the block that arrives last (after every block has published its
-// partials); that block resets the ticket for the next launch.
-__device__ __forceinline__ bool last_block(unsigned *ticket) {
-    __shared__ int is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(ticket, 1u);
-        is_last = t == gridDim.x - 1;
-        if (is_last) *ticket = 0u;
-    }
-    __syncthreads();
-    if (is_last) __threadfence();
-    return is_last != 0;
 }
 
 struct Part {
@@ -122,9 +87,9 @@ __global__ void __launch_bounds__(kVT) pcg_start_kernel(Part P, const float *g, 
     const double tg = block_total(gg, red);
     const double tr = block_total(rz, red);
     if (threadIdx.x == 0) { part[blockIdx.x] = tg; part[nb + blockIdx.x] = tr; }
-    if (!last_block(ticket)) return;
+    if (!lb_last_block(ticket, gridDim.x)) return;
     if (threadIdx.x < 64) {
-        const double v = warp_sum_parts(part + (threadIdx.x >> 5) * nb, nb);
+        const double v = lb_sum_parts(part + (threadIdx.x >> 5) * nb, nb);
         if (threadIdx.x == 0) {
             sc->pq = sc->alpha = sc->beta = sc->rend = sc->rz_new = 0.0;
             sc->stop = 0;
@@ -156,14 +121,10 @@ __global__ void __launch_bounds__(kVT) pcg_alpha_kernel(Part P, const float *d, 
     }
     const double t = block_total(acc, red);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
-    if (!last_block(ticket)) return;
+    if (!lb_last_block(ticket, gridDim.x)) return;
     if (threadIdx.x < 32) {
-        const double v = warp_sum_parts(part, gridDim.x);
-        if (threadIdx.x == 0) {
-            sc->pq = v;
-            if (sc->stop || !(sc->rz != 0.0) || !(v > 0.0)) { sc->stop = 1; sc->alpha = 0.0; }
-            else sc->alpha = sc->rz / v;
-        }
+        const double v = lb_sum_parts(part, gridDim.x);
+        if (threadIdx.x == 0) pcg_set_alpha(sc, v);
     }
 }
 
@@ -214,7 +175,7 @@ __global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars 
             if (i < P.qpt && e < P.n4) acc += dot4(zn[i], ldg4(rj, e));
         }
         if (tail) acc = fmaf(zt, rj[et], acc);
-        acc = warp_sum_f(acc);
+        acc = lb_warp_sum_f(acc);
         if (lane == 0) wp[j][warp] = (double)acc;
     }
     __syncthreads();
@@ -223,9 +184,9 @@ __global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars 
         for (int w = 0; w < kVW; ++w) t += wp[j][w];
         part[(long)j * nb + blockIdx.x] = t;
     }
-    if (!last_block(ticket)) return;
+    if (!lb_last_block(ticket, gridDim.x)) return;
     for (int j = warp; j <= k; j += kVW) {
-        const double v = warp_sum_parts(part + (long)j * nb, nb);
+        const double v = lb_sum_parts(part + (long)j * nb, nb);
         if (lane == 0) coef[j] = (sc->stop || rzh[j] == 0.0) ? 0.0 : v / rzh[j];
     }
 }
@@ -280,9 +241,9 @@ __global__ void __launch_bounds__(kVT, 3) pcg_reorth_kernel(Part P, const float 
     }
     const double t = block_total(acc, red);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
-    if (!last_block(ticket)) return;
+    if (!lb_last_block(ticket, gridDim.x)) return;
     if (threadIdx.x < 32) {
-        const double v = warp_sum_parts(part, gridDim.x);
+        const double v = lb_sum_parts(part, gridDim.x);
         if (threadIdx.x == 0) {
             sc->rz_new = v;
             if (sc->stop) {
