@@ -167,17 +167,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // the row pitch is not a multiple of 16 bytes.
 static bool encode_field_map(CUtensorMap *map, const int *n, int TY, float *base) {
     if (n[0] % 4 != 0 || n[0] < kTmaBoxX || n[1] < TY + 4) return false;
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    static const EncodeTiledFn fn = [] {   // looked up once, also under concurrent callers
         void *f = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !f) {
             cudaGetLastError();
-            return false;
+            return (EncodeTiledFn) nullptr;
         }
-        fn = (EncodeTiledFn)f;
-    }
+        return (EncodeTiledFn)f;
+    }();
+    if (!fn) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2], 3};
     const cuuint64_t strides[3] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4,
                                    (cuuint64_t)n[0] * n[1] * n[2] * 4};

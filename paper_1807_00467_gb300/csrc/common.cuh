@@ -8,6 +8,41 @@
 
 namespace ngf {
 
+// Host-side launch helpers, safe to call from several host threads at once
+// (function-local statics are initialised exactly once).  The device is the
+// one current at the first call; the library drives one GPU per process.
+inline int device_sm_count() {
+    static const int sms = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || v <= 0)
+            v = 1;
+        return v;
+    }();
+    return sms;
+}
+
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum less the kernel's static shared memory.  That value is fixed per
+// kernel, so launches of one kernel with different sizes from concurrent host
+// threads cannot lower the limit under one another; a launch asking for more
+// than the limit still fails.
+template <typename K>
+inline cudaError_t allow_max_dynamic_smem(K kernel) {
+    static const int optin = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            v = 48 * 1024;
+        return v;
+    }();
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 
 // Image element loads: float32, or IEEE half storing (HU + 1024).  The NGF
 // distance only sees differences, so the offset cancels (Eq. (1)).

@@ -489,16 +489,10 @@ static cudaError_t launch_grad(int mode, const TileArgs<TImg> &a, cudaStream_t s
     const bool adj = mode != MODE_OBJ;
     const size_t smem = sizeof(float) * (size_t)gr_smem(a.g, adj).total;
     const int ntiles = a.g.nb[0] * a.g.nb[1] * a.g.nb[2];
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                      cudaSuccess || sms <= 0)
-            sms = 1;
-    }
+    const int sms = device_sm_count();
     const int grid = ntiles < sms ? ntiles : sms;
     auto run = [&](auto kernel) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(kernel);
         if (e != cudaSuccess) return e;
         kernel<<<grid, kNT, smem, st>>>(a);
         return cudaGetLastError();

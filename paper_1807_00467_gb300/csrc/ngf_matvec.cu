@@ -323,16 +323,10 @@ cudaError_t launch_gn_matvec(const TileArgs<float> &a, bool diag, cudaStream_t s
     // plane sequence is a whole number of ring cycles, else one tile per CTA
     const int tail = a.g.n[2] - (a.g.nb[2] - 1) * a.g.TZ;
     const int chain = (a.g.TZ + 4) % kStages == 0 && (tail + 4) % kStages == 0;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                      cudaSuccess || sms <= 0)
-            sms = 1;
-    }
+    const int sms = device_sm_count();
     const int grid = chain ? (ntiles < sms ? ntiles : sms) : ntiles;
     auto run = [&](auto kernel) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(kernel);
         if (e != cudaSuccess) return e;
         kernel<<<grid, kNT, smem, st>>>(a, chain);
         return cudaGetLastError();

@@ -569,7 +569,7 @@ static cudaError_t launch_mode(int mode, const TileArgs<TImg> &a, cudaStream_t s
 #define NGF_LAUNCH(TYV, MV)                                                                              \
     do {                                                                                                 \
         auto k = ngf_tile_kernel<TYV, MV, TImg>;                                                         \
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        cudaError_t e = allow_max_dynamic_smem(k);                                                       \
         if (e != cudaSuccess) return e;                                                                  \
         k<<<grid, 32 * (TYV + 4), smem, st>>>(a);                                                        \
         return cudaGetLastError();                                                                       \

@@ -24,7 +24,6 @@ constexpr int kVT = 256;            // threads per block
 constexpr int kVW = kVT / 32;
 constexpr int kQmax = 8;            // quads per thread at most
 constexpr int kHist = RG_PCG_MAX + 1;
-constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
     return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
