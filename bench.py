@@ -434,6 +434,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         out["solve_s"] = time.perf_counter() - t0
         out["solve_config"] = "3 levels x 10 GN x 30 PCG, Armijo; 128x128x32 -> 512x512x128"
+        out["batch"] = batch_rates(R, T, h, params, dev)
         # the small workloads are launch- and latency-bound: eager vs CUDA-graph replay
         out["small"] = {name: small_config_rates(name, 200, dev) for name in ("tiny", "mid")}
         # precision form: images stored as FP16 (HU + 1024), FP32 per-voxel arithmetic
@@ -478,6 +479,34 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def batch_rates(R, T, h, params, dev, n_pairs=24, workers=(1, 2, 4, 8)):
+    """Many uneven pairs (centred crops of one pair, 96x96x64 .. the whole
+    volume, log-uniform voxel counts), each through the 3-level pyramid with
+    10 GN x 30 PCG per level: pairs per minute on one stream against several
+    concurrent streams, and whether every pair's result is the same bits."""
+    import torch
+    from paper_1807_00467_gb300 import batch
+    shapes = batch.crop_shapes((R.shape[2], R.shape[1], R.shape[0]), n_pairs=n_pairs, seed=1)
+    pairs = batch.crop_pairs(R, T, h, shapes)
+    sched = dict(levels=3, gn_iters=10, pcg_iters=30)
+    small = sorted(range(n_pairs), key=lambda i: pairs[i][0].numel())
+    batch.register_batch([pairs[small[0]], pairs[small[-1]]], params, workers=2, **sched)   # load the kernels
+    res = {"pairs": n_pairs, "voxels": int(sum(p[0].numel() for p in pairs)),
+           "smallest": list(shapes[small[0]]), "largest": list(shapes[small[-1]]),
+           "schedule": "3 levels x 10 GN x 30 PCG per pair, Armijo", "workers": {}}
+    first = None
+    for w in workers:
+        us, reps, sec = batch.register_batch(pairs, params, workers=w, **sched)
+        mv = int(sum(r[..., 6].sum() for r in reps))
+        same = first is None or all(torch.equal(a, b) for a, b in zip(first, us))
+        first = first if first is not None else us
+        res["workers"][str(w)] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
+                                  "gn_matvec_per_s": mv / sec, "same_bits_as_one_stream": bool(same)}
+    del pairs, first
+    torch.cuda.synchronize(dev)
+    return res
 
 
 def main():

@@ -1,0 +1,99 @@
+"""Many registration problems of uneven sizes on one GPU.
+
+``register_batch`` advances a list of image pairs through the multilevel
+Gauss-Newton schedule (``api.register_pyramid`` per pair: restriction, GN-PCG
+per level, grid prolongation) with several pairs in flight at once: each
+worker owns a CUDA stream and a host thread, pairs are handed out largest
+first to the least-loaded worker, so the kernels of small pairs (which leave
+most of the GPU idle on their own) overlap with those of other pairs.  The
+library calls release the interpreter lock, and every pair's work is ordered
+on its worker's stream, so results do not depend on the interleaving.
+
+``crop_shapes`` draws the uneven problem sizes of the batching workload:
+voxel counts log-uniform between 96 x 96 x 64 and the whole volume, z extent
+growing with the cube root of the count, every extent a multiple of 16 (three
+pyramid levels over a grid of one node per 4 voxels).  ``crop_pairs`` cuts the
+centred sub-volumes out of one reference/template pair on the device: each is
+a registration problem of its own under the same motion, at the same spacing.
+"""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import api
+
+__all__ = ["crop_shapes", "crop_pairs", "register_batch"]
+
+def crop_shapes(n_full, n_pairs=24, seed=0, lo=(96, 96, 64), q=16):
+    """[(nx, ny, nz)] of n_pairs sub-volumes of an n_full = (nx, ny, nz) volume."""
+    rng = np.random.default_rng(seed)
+    v0, v1 = float(np.prod(lo)), float(np.prod(n_full))
+    rq = lambda x, a, b: int(min(max(int(round(x / q)) * q, a), b))
+    out = []
+    for _ in range(n_pairs):
+        v = np.exp(rng.uniform(np.log(v0), np.log(v1)))
+        nz = rq(lo[2] * (v / v0) ** (1.0 / 3.0), lo[2], n_full[2] // q * q)
+        nx = rq(np.sqrt(v / nz), lo[0], n_full[0] // q * q)
+        ny = rq(np.sqrt(v / nz), lo[1], n_full[1] // q * q)
+        out.append((nx, ny, nz))
+    return out
+
+
+def crop_pairs(R, T, h, shapes, grid_step=4):
+    """Centred crops [(R_c, T_c, h, m)] of the [nz][ny][nx] device images R, T;
+    m = n / grid_step + 1 nodes per axis."""
+    out = []
+    for n in shapes:
+        o = [(R.shape[2 - a] - n[a]) // 2 for a in range(3)]
+        sl = (slice(o[2], o[2] + n[2]), slice(o[1], o[1] + n[1]), slice(o[0], o[0] + n[0]))
+        m = tuple(n[a] // grid_step + 1 for a in range(3))
+        out.append((R[sl].contiguous(), T[sl].contiguous(), tuple(h), m))
+    return out
+
+
+def register_batch(pairs, params, levels, gn_iters, pcg_iters, workers=4, ls_max=10, armijo_c=1e-4):
+    """Register every pair (R, T, h, m) (CUDA tensors, float32 or float16 of
+    HU + 1024) from u = 0.  Returns (displacements, reports, seconds); the
+    displacement of pair i is a float32 tensor (3, m3, m2, m1)."""
+    dev = pairs[0][0].device
+    order = sorted(range(len(pairs)), key=lambda i: -pairs[i][0].numel())
+    load = [0] * workers
+    share = [[] for _ in range(workers)]
+    for i in order:                       # largest first to the least-loaded worker
+        w = min(range(workers), key=lambda k: load[k])
+        share[w].append(i)
+        load[w] += pairs[i][0].numel()
+    us = [None] * len(pairs)
+    reps = [None] * len(pairs)
+    errors = []
+
+    def run(w):
+        try:
+            torch.cuda.set_device(dev)
+            s = torch.cuda.Stream(device=dev)
+            for i in share[w]:
+                R, T, h, m = pairs[i]
+                with torch.cuda.stream(s):   # u and the workspace belong to this stream
+                    u = torch.zeros((3, m[2], m[1], m[0]), dtype=torch.float32, device=dev)
+                    code, rep = api.register_pyramid(R, T, h, m, u, params, levels, gn_iters, pcg_iters, ls_max,
+                                                     armijo_c, stream=s)
+                us[i], reps[i] = u, rep
+        except Exception as e:   # reported after all workers have stopped
+            errors.append(e)
+
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=run, args=(w,)) for w in range(workers) if share[w]]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize(dev)
+    seconds = time.perf_counter() - t0
+    if errors:
+        raise errors[0]
+    return us, reps, seconds
