@@ -283,6 +283,17 @@ def small_config_rates(name, reps, dev):
     s.synchronize()
     out["graph_obj_grad_evals_per_s"] = reps / (ev[0].elapsed_time(ev[1]) / 1e3)
     out["graph_gn_matvec_per_s"] = reps / (ev[1].elapsed_time(ev[2]) / 1e3)
+    # whole Gauss-Newton iterations (gradient + linearisation, 30 PCG, line
+    # search) by drive: host reads, device decisions, device + graph replay
+    for drive in ("host", "device", "graph"):
+        uu = u.clone()
+        torch.cuda.synchronize(dev)
+        ctx.gn_solve(uu, gn_iters=1, pcg_iters=30, drive=drive)
+        uu.copy_(u)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        code, rep = ctx.gn_solve(uu, gn_iters=10, pcg_iters=30, drive=drive)
+        out[f"gn_iter_per_s_{drive}"] = 10 / (time.perf_counter() - t0)
     return out
 
 
@@ -402,6 +413,15 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         out["obj_grad_evals_per_s"] = reps / (ev[0].elapsed_time(ev[1]) / 1e3)
         out["matvec_only_per_s"] = reps / (ev[1].elapsed_time(ev[2]) / 1e3)
+        # the same GN iterations with the line search decided on the device and
+        # each iteration replayed from a CUDA graph (capture included)
+        ug = u.clone()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        code, rep = ctx.gn_solve(ug, gn_iters=5, pcg_iters=args.pcg_iters, drive="graph")
+        out["graph_drive"] = {"gn_matvec_per_s": float(rep[:, 6].sum()) / (time.perf_counter() - t0),
+                              "gn_iters": 5, "note": "wall clock of one gn_solve call, capture included"}
+        del ug
         # end to end through the C ABI with host buffers: per step copy R, T, u
         # from pinned host memory, one GN iteration, read u back
         Rh, Th = torch.from_numpy(ph.R).pin_memory(), torch.from_numpy(ph.T).pin_memory()
@@ -481,7 +501,8 @@ def run_ours(args):
     return 0
 
 
-def batch_rates(R, T, h, params, dev, n_pairs=24, workers=(1, 2, 4, 8)):
+def batch_rates(R, T, h, params, dev, n_pairs=24, runs=(("host", 1), ("host", 4), ("graph", 1), ("graph", 4),
+                                                        ("graph", 8))):
     """Many uneven pairs (centred crops of one pair, 96x96x64 .. the whole
     volume, log-uniform voxel counts), each through the 3-level pyramid with
     10 GN x 30 PCG per level: pairs per minute on one stream against several
@@ -492,18 +513,18 @@ def batch_rates(R, T, h, params, dev, n_pairs=24, workers=(1, 2, 4, 8)):
     pairs = batch.crop_pairs(R, T, h, shapes)
     sched = dict(levels=3, gn_iters=10, pcg_iters=30)
     small = sorted(range(n_pairs), key=lambda i: pairs[i][0].numel())
-    batch.register_batch([pairs[small[0]], pairs[small[-1]]], params, workers=2, **sched)   # load the kernels
+    batch.register_batch([pairs[small[0]], pairs[small[-1]]], params, workers=2, drive="graph", **sched)   # load
     res = {"pairs": n_pairs, "voxels": int(sum(p[0].numel() for p in pairs)),
            "smallest": list(shapes[small[0]]), "largest": list(shapes[small[-1]]),
-           "schedule": "3 levels x 10 GN x 30 PCG per pair, Armijo", "workers": {}}
+           "schedule": "3 levels x 10 GN x 30 PCG per pair, Armijo", "runs": {}}
     first = None
-    for w in workers:
-        us, reps, sec = batch.register_batch(pairs, params, workers=w, **sched)
+    for drive, w in runs:
+        us, reps, sec = batch.register_batch(pairs, params, workers=w, drive=drive, **sched)
         mv = int(sum(r[..., 6].sum() for r in reps))
         same = first is None or all(torch.equal(a, b) for a, b in zip(first, us))
         first = first if first is not None else us
-        res["workers"][str(w)] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
-                                  "gn_matvec_per_s": mv / sec, "same_bits_as_one_stream": bool(same)}
+        res["runs"][f"{drive}_x{w}"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
+                                        "gn_matvec_per_s": mv / sec, "same_bits_as_first": bool(same)}
     del pairs, first
     torch.cuda.synchronize(dev)
     return res

@@ -93,7 +93,20 @@ typedef struct {
     int32_t pcg_iters;    /* PCG steps per Gauss-Newton step */
     int32_t ls_max;       /* line search tries t = 1, 1/2, ..., 2^-ls_max */
     double armijo_c;      /* Armijo constant */
+    int32_t flags;        /* 0: host-driven line search; RG_SCHED_DEVICE / RG_SCHED_GRAPH below */
 } rg_schedule;
+
+/* rg_schedule.flags.  RG_SCHED_DEVICE: the slope g.p, the Armijo test and the
+ * update run on the device, so an iteration needs no host synchronisation
+ * (every line-search try is launched; the tries after the accepted one skip
+ * their work).  RG_SCHED_GRAPH: as RG_SCHED_DEVICE, with one iteration's
+ * launches captured once into a CUDA graph and replayed gn_iters times.
+ * Both run on a private stream of the context ordered after and before the
+ * caller's stream, give the same bits as the host-driven loop, synchronise
+ * once at the end, and apply when 1 <= gn_iters <= 256 and profiling is off
+ * (otherwise the host-driven loop runs). */
+#define RG_SCHED_DEVICE 1
+#define RG_SCHED_GRAPH 2
 
 typedef struct rg_ctx rg_ctx;
 
@@ -166,8 +179,8 @@ int gn_pcg_solve(rg_ctx *ctx, const float *g_dev, float *p_dev, int32_t iters, d
 /* Fixed Gauss-Newton schedule on one level: gn_iters x (gradient +
  * linearisation, PCG, Armijo backtracking).  u_dev is updated in place.
  * report_host: double[gn_iters][8] = {it, J, g.p, t (0 = rejected), J new,
- * evaluations, pcg steps, status} or NULL.  Synchronises the stream once per
- * line-search try. */
+ * evaluations, pcg steps, status} or NULL.  Host-driven (flags 0):
+ * synchronises the stream once per line-search try; see RG_SCHED_DEVICE. */
 int gn_solve(rg_ctx *ctx, float *u_dev, const rg_schedule *sched, double *report_host);
 
 /* Multilevel registration (Sec. II-D3): levels-1 times 2x2x2 box restriction

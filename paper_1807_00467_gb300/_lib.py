@@ -34,7 +34,7 @@ class Params(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("levels", C.c_int32), ("gn_iters", C.c_int32), ("pcg_iters", C.c_int32), ("ls_max", C.c_int32),
-                ("armijo_c", C.c_double)]
+                ("armijo_c", C.c_double), ("flags", C.c_int32)]
 
 
 EXPORTS = [

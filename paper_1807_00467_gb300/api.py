@@ -43,8 +43,15 @@ def make_params(eta=10.0, alpha=1.0, gamma=0.0, delta=0.0, delta_adaptive=False,
     return Params(eta, alpha, gamma, delta, int(bool(delta_adaptive)), tau)
 
 
-def make_schedule(levels=1, gn_iters=5, pcg_iters=30, ls_max=10, armijo_c=1e-4):
-    return Schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c)
+SCHED_DEVICE, SCHED_GRAPH = 1, 2    # rg_schedule.flags
+
+
+def make_schedule(levels=1, gn_iters=5, pcg_iters=30, ls_max=10, armijo_c=1e-4, drive="host"):
+    """drive: 'host' (line search read on the host), 'device' (decided on the
+    GPU, no per-iteration synchronisation) or 'graph' (device, with each
+    iteration replayed from a captured CUDA graph)."""
+    flags = {"host": 0, "device": SCHED_DEVICE, "graph": SCHED_GRAPH}[drive]
+    return Schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c, flags)
 
 
 def _img_geom(shape, h):
@@ -192,9 +199,9 @@ class Context:
                "rg_profile_read")
         return ms.value, cnt.value
 
-    def gn_solve(self, u, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4):
+    def gn_solve(self, u, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, drive="host"):
         """Runs the fixed Gauss-Newton schedule in place on u; returns (status, report)."""
-        sched = make_schedule(1, gn_iters, pcg_iters, ls_max, armijo_c)
+        sched = make_schedule(1, gn_iters, pcg_iters, ls_max, armijo_c, drive)
         rep = np.zeros((gn_iters, 8))
         code = _check(_lib.load().gn_solve(self._ctx, _ptr(self._field(u)), C.byref(sched),
                                            rep.ctypes.data_as(C.POINTER(C.c_double))), self._ctx, "gn_solve")
@@ -202,7 +209,7 @@ class Context:
 
 
 def register_pyramid(R, T, h, m_finest, u, params, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4,
-                     kx=None, ky=None, stream=None):
+                     kx=None, ky=None, stream=None, drive="host"):
     """Multilevel registration; u (finest grid) is updated in place; returns (status, report)."""
     L = _lib.load()
     ig, gg = _img_geom(R.shape, h), _grid_geom(m_finest)
@@ -213,7 +220,7 @@ def register_pyramid(R, T, h, m_finest, u, params, levels, gn_iters, pcg_iters, 
            name="rg_pyramid_workspace_size")
     ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=R.device)
     wp = (ws.data_ptr() + 255) & ~255
-    sched = make_schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c)
+    sched = make_schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c, drive)
     rep = np.zeros((levels, gn_iters, 8))
     code = L.register_pyramid(C.byref(ig), _ptr(R), _ptr(T), dtype, C.byref(gg), C.byref(params), C.byref(sched), nk,
                               _ptr(kx), _ptr(ky), _ptr(u), rep.ctypes.data_as(C.POINTER(C.c_double)),

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
@@ -47,6 +48,12 @@ struct rg_ctx {
     PcgScalars *sc;
     bool has_lin, minv_valid;
     char err[512];
+    GnState *gn;              // device side of a Gauss-Newton iteration
+    double *gnrep;            // its report rows [kGnRows][8]
+    const int *skip;          // set while a line-search try is launched: the try's kernels skip when *skip
+    cudaStream_t gst;         // private stream of device-driven schedules (created on first use)
+    cudaEvent_t gev[2];
+    long long launches;       // library kernels launched (or replayed) for this context
     // optional per-kernel CUDA-event timing (rg_profile)
     bool prof;
     std::vector<cudaEvent_t> *ev_pool;
@@ -63,6 +70,7 @@ struct ProfScope {
     cudaEvent_t a = nullptr, b = nullptr;
     ProfScope(rg_ctx *c_, int id_) : c(c_), id(id_) {
         g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (c) ++c->launches;
         if (!c || !c->prof) return;
         a = take();
         b = take();
@@ -238,6 +246,8 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->ts = cv.take<float>(3 * M);
     c->sc = cv.take<PcgScalars>(1);
     c->tma_err = cv.take<int>(2);
+    c->gn = cv.take<GnState>(1);
+    c->gnrep = cv.take<double>(8 * kGnRows);
 }
 
 static void derive(rg_ctx *c) {
@@ -335,6 +345,11 @@ extern "C" int rg_ctx_destroy(rg_ctx *c) {
     if (c->ev_pool) {
         for (auto e : *c->ev_pool) cudaEventDestroy(e);
         delete c->ev_pool;
+    }
+    if (c->gst) {
+        cudaStreamDestroy(c->gst);
+        cudaEventDestroy(c->gev[0]);
+        cudaEventDestroy(c->gev[1]);
     }
     free(c);
     return RG_OK;
@@ -449,6 +464,7 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
         a.map_dT = c->map_dT;
         a.map_a = c->map_a;
         a.err = c->tma_err;
+        a.skip = c->skip;
     };
     const int pid = mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1));
     if ((mode == MODE_MATVEC || mode == MODE_DIAG) && gn_matvec_supported(c->tg)) {
@@ -496,6 +512,7 @@ static int run_vcc(rg_ctx *c, const float *u, const float *v, int diag = 0) {
     a.fold = c->fold;
     a.dmin = c->dmin;
     a.dmax = c->dmax;
+    a.skip = c->skip;
     LAUNCH((diag ? 10 : (a.v ? 4 : 3)), launch_vcc(a, c->st));
     return RG_OK;
 }
@@ -521,6 +538,7 @@ static int run_nodes(rg_ctx *c, const float *v, bool energy, float *out, double 
     a.sC = (float)sC;
     a.rpart = energy ? c->rpart : nullptr;
     a.out = out;
+    a.skip = c->skip;
     if (v) LAUNCH(5, launch_curv(a, c->st));
     if (out) LAUNCH(6, launch_nodes(a, c->st));
     return RG_OK;
@@ -541,6 +559,7 @@ static int run_kp(rg_ctx *c, const float *u, const float *v, double scale, float
     k.scale = (float)scale;
     k.out = out;
     k.part = energy ? c->kpart : nullptr;
+    k.skip = c->skip;
     LAUNCH(7, launch_kp(k, c->st));
     return RG_OK;
 }
@@ -566,6 +585,7 @@ static int run_terms(rg_ctx *c, double *terms, bool useD, bool useR, bool useV, 
     t.dmax = c->dmax;
     t.dminmax = c->dminmax;
     t.terms = terms;
+    t.skip = c->skip;
     LAUNCH(8, launch_terms(t, c->st));
     return RG_OK;
 }
@@ -768,9 +788,142 @@ static int set_delta_adaptive(rg_ctx *c, const float *u) {
     return RG_OK;
 }
 
+// ------------------------------------------------ device-driven schedule
+// The same iteration as gn_solve_impl's host loop with the decisions taken on
+// the GPU (gn_loop.cu): every line-search try is launched, and the tries after
+// the accepted one skip all their work.
+struct SkipScope {
+    rg_ctx *c;
+    SkipScope(rg_ctx *c_, const int *flag) : c(c_) { c->skip = flag; }
+    ~SkipScope() { c->skip = nullptr; }
+};
+
+struct StreamSwap {   // the context's launches go to another stream for a scope
+    rg_ctx *c;
+    cudaStream_t saved;
+    StreamSwap(rg_ctx *c_, cudaStream_t s) : c(c_), saved(c_->st) { c->st = s; }
+    ~StreamSwap() { c->st = saved; }
+};
+
+static int gn_iteration_device(rg_ctx *c, float *u, const rg_schedule *s) {
+    int st;
+    const long n = 3 * c->M;
+    if ((st = evaluate(c, u, c->terms_tmp, c->tg_, true))) return st;
+    LAUNCH(9, launch_gn_begin(c->gn, c->terms_tmp, c->st));
+    if ((st = pcg(c, c->tg_, c->ts, s->pcg_iters, c->terms_tmp + 5))) return st;
+    LAUNCH(9, launch_dot(n, c->tg_, c->ts, c->vecpart, c->st));
+    LAUNCH(9, launch_gn_slope(c->gn, c->vecpart, vec_blocks(n), c->st));
+    {
+        SkipScope sk(c, &c->gn->done);
+        double t = 1.0;
+        for (int k = 0; k <= s->ls_max; ++k) {
+            LAUNCH(9, launch_axpy_copy(n, (float)t, u, c->ts, c->tu, c->st, c->skip));
+            if ((st = evaluate(c, c->tu, c->terms_tmp, nullptr, false))) return st;
+            LAUNCH(9, launch_gn_armijo(c->gn, c->terms_tmp, t, s->armijo_c, c->st));
+            t *= 0.5;
+        }
+    }
+    LAUNCH(9, launch_gn_accept(c->gn, n, c->tu, u, c->st));
+    LAUNCH(9, launch_gn_report(c->gn, c->terms_tmp + 5, c->gnrep, kGnRows, c->st));
+    return RG_OK;
+}
+
+// gn_iters iterations on c->st: launched one by one, or captured once into a
+// CUDA graph and replayed (the iteration's launches and pointers do not
+// change between iterations)
+static int gn_run_device(rg_ctx *c, float *u, const rg_schedule *s, bool graph) {
+    if (!c->err_zeroed) {
+        CK(cudaMemsetAsync(c->tma_err, 0, 2 * sizeof(int), c->st));
+        c->err_zeroed = true;
+    }
+    CK(cudaMemsetAsync(c->gn, 0, sizeof(GnState), c->st));
+    if (!graph) {
+        for (int it = 0; it < s->gn_iters; ++it) {
+            const int st = gn_iteration_device(c, u, s);
+            if (st) return st;
+        }
+        return RG_OK;
+    }
+    cudaGraph_t g = nullptr;
+    const long long l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed));
+    const int st = gn_iteration_device(c, u, s);
+    const cudaError_t ce = cudaStreamEndCapture(c->st, &g);
+    const long long per = c->launches - l0;   // counted while capturing; nothing ran yet
+    c->launches -= per;
+    g_launches.fetch_sub(per, std::memory_order_relaxed);
+    if (st != RG_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != RG_OK ? st : set_err(c, RG_ECUDA, "gn_solve: capture failed: %s", cudaGetErrorString(ce));
+    }
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return set_err(c, RG_ECUDA, "gn_solve: graph instantiation: %s", cudaGetErrorString(ie));
+    int rc = RG_OK;
+    for (int it = 0; it < s->gn_iters; ++it) {
+        const cudaError_t le = cudaGraphLaunch(ge, c->st);
+        if (le != cudaSuccess) {
+            rc = set_err(c, RG_ECUDA, "gn_solve: graph launch: %s", cudaGetErrorString(le));
+            break;
+        }
+        c->launches += per;
+        g_launches.fetch_add(per, std::memory_order_relaxed);
+    }
+    cudaGraphExecDestroy(ge);
+    return rc;
+}
+
+// Device-driven schedule on the context's private stream, ordered after and
+// before the caller's stream by events; one host synchronisation at the end.
+static int gn_solve_device(rg_ctx *c, float *u, const rg_schedule *s, double *report, bool graph) {
+    if (!c->gst) {
+        cudaStream_t gs = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+        if (cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            cudaStreamDestroy(gs);
+            return set_err(c, RG_ECUDA, "gn_solve: event creation failed");
+        }
+        c->gst = gs;
+        c->gev[0] = e0;
+        c->gev[1] = e1;
+    }
+    const cudaStream_t user = c->st;
+    CK(cudaEventRecord(c->gev[0], user));
+    CK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
+    int st;
+    {
+        StreamSwap sw(c, c->gst);
+        st = gn_run_device(c, u, s, graph);
+    }
+    CK(cudaEventRecord(c->gev[1], c->gst));
+    CK(cudaStreamWaitEvent(user, c->gev[1], 0));
+    if (st) return st;
+    GnState hs;
+    std::vector<double> rows(8 * (size_t)s->gn_iters);
+    int err = 0;
+    CK(cudaMemcpyAsync(&hs, c->gn, sizeof hs, cudaMemcpyDeviceToHost, c->gst));
+    CK(cudaMemcpyAsync(rows.data(), c->gnrep, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost, c->gst));
+    CK(cudaMemcpyAsync(&err, c->tma_err, sizeof(int), cudaMemcpyDeviceToHost, c->gst));
+    CK(cudaStreamSynchronize(c->gst));
+    if (err) return set_err(c, RG_ETIMEOUT, "a kernel gave up waiting for a TMA transfer");
+    const int nrows = hs.halted ? hs.halt_it + 1 : s->gn_iters;
+    if (report) memcpy(report, rows.data(), sizeof(double) * 8 * (size_t)nrows);
+    if (hs.halted)
+        return hs.status == RG_EFOLD ? set_err(c, RG_EFOLD, "gn_solve: fold at the current iterate")
+                                     : set_err(c, RG_ENONFINITE, "gn_solve: non-finite objective");
+    return RG_OK;
+}
+
 static int gn_solve_impl(rg_ctx *c, float *u, const rg_schedule *s, double *report, bool adapt) {
     int st;
     if (adapt && (st = set_delta_adaptive(c, u))) return st;
+    if ((s->flags & (RG_SCHED_DEVICE | RG_SCHED_GRAPH)) && s->gn_iters > 0 && s->gn_iters <= kGnRows && !c->prof)
+        return gn_solve_device(c, u, s, report, (s->flags & RG_SCHED_GRAPH) != 0);
     const long n = 3 * c->M;
     double h5[5], slope;
     for (int it = 0; it < s->gn_iters; ++it) {
@@ -803,7 +956,7 @@ static int gn_solve_impl(rg_ctx *c, float *u, const rg_schedule *s, double *repo
             if ((st = evaluate(c, c->tu, c->terms_tmp, nullptr, false))) return st;
             if ((st = read_terms(c, c->terms_tmp, h5))) return st;
             ++evals;
-            if (isfinite(h5[4]) && h5[4] <= J0 + s->armijo_c * t * slope) {
+            if (isfinite(h5[4]) && h5[4] <= std::fma(s->armijo_c * t, slope, J0)) {
                 acc_t = t;
                 Jn = h5[4];
                 break;

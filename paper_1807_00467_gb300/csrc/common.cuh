@@ -94,6 +94,7 @@ struct TileArgs {
     // {kTmaBoxX, TY + 4, 1, 3} starting at (x0 - 4, y0 - 2, plane, 0).
     CUtensorMap map_dT, map_a;
     int *err;               // set to 1 if a bounded wait on a TMA barrier gave up
+    const int *skip = nullptr;   // nonzero: the launch does nothing (a line-search try after acceptance)
 };
 
 constexpr int kTmaBoxX = 36;      // floats per TMA box row: tile columns x0-4 .. x0+31

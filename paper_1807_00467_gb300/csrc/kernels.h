@@ -37,6 +37,7 @@ struct VccArgs {
     double *epart;         // per-CTA partial sums of psi(d)
     int *fold;             // per-CTA count of d <= 0
     float *dmin, *dmax;    // per-CTA min / max of d
+    const int *skip = nullptr;   // nonzero: the launch does nothing
 };
 constexpr int kVccTile[3] = {8, 4, 4};
 cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st);
@@ -55,6 +56,7 @@ struct NodeArgs {
     float sC;              // scale of L^T w (alpha ghat)
     double *rpart;         // per-block partial sums of |L v|^2, may be NULL
     float *out;            // [3][M] (launch_nodes)
+    const int *skip = nullptr;   // nonzero: the launch does nothing
 };
 int node_blocks(const int *m);
 cudaError_t launch_curv(const NodeArgs &a, cudaStream_t st);
@@ -71,6 +73,7 @@ struct KpArgs {
     float scale;           // multiplies the node contributions (delta)
     float *out;            // accumulated with atomics
     double *part;          // per-CTA partial sums of |res|^2
+    const int *skip = nullptr;   // nonzero: the launch does nothing
 };
 int kp_blocks(int nk);
 cudaError_t launch_kp(const KpArgs &a, cudaStream_t st);
@@ -84,6 +87,7 @@ struct TermsArgs {
     double alpha, gamma, delta;
     const float *dmin, *dmax; double *dminmax;
     double *terms;         // [5]
+    const int *skip = nullptr;   // nonzero: the launch does nothing
 };
 cudaError_t launch_terms(const TermsArgs &a, cudaStream_t st);
 
@@ -124,7 +128,25 @@ cudaError_t launch_pcg_alpha(const PcgArgs &a, const float *q, cudaStream_t st);
 cudaError_t launch_pcg_step(const PcgArgs &a, const float *q, float *s, int k, cudaStream_t st);
 cudaError_t launch_pcg_reorth(const PcgArgs &a, int k, cudaStream_t st);
 cudaError_t launch_pcg_dir(const PcgArgs &a, int k, cudaStream_t st);
-cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, float *y, cudaStream_t st);
+cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, float *y, cudaStream_t st,
+                             const int *skip = nullptr);
+
+// Device side of one Gauss-Newton iteration (line search without host reads).
+struct GnState {
+    double J0, Jn, slope, acc_t;
+    int done;      // the line search has finished (or the schedule halted): later tries skip
+    int evals;     // objective evaluations of the line search
+    int halted;    // a non-finite objective stopped the schedule
+    int halt_it;   // ... at this iteration
+    int status;    // RG_OK, RG_EFOLD or RG_ENONFINITE
+    int it;        // iterations run (report row index)
+};
+constexpr int kGnRows = 256;   // report rows the workspace keeps for device-driven schedules
+cudaError_t launch_gn_begin(GnState *s, const double *terms, cudaStream_t st);
+cudaError_t launch_gn_slope(GnState *s, const double *part, int nparts, cudaStream_t st);
+cudaError_t launch_gn_armijo(GnState *s, const double *terms, double t, double c, cudaStream_t st);
+cudaError_t launch_gn_accept(const GnState *s, long n, const float *tu, float *u, cudaStream_t st);
+cudaError_t launch_gn_report(GnState *s, const double *pcg_stats, double *rep, int rows, cudaStream_t st);
 
 // Pyramid.
 cudaError_t launch_restrict(const int *n, bool half, const void *in, void *out, cudaStream_t st);

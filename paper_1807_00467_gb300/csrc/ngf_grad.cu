@@ -59,6 +59,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // ngf_obj_kernel below.
 template <int MODE, typename TImg, int RZ>
 __global__ void __launch_bounds__(kNT, 1) ngf_grad_kernel(const __grid_constant__ TileArgs<TImg> a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     constexpr bool ADJ = MODE != MODE_OBJ, STORE = MODE == MODE_GRADLIN;
     constexpr int HZ = ADJ ? 2 : 1;   // z halo of stage W
     constexpr unsigned FULL = 0xffffffffu;
@@ -314,6 +315,7 @@ __global__ void __launch_bounds__(kNT, 1) ngf_grad_kernel(const __grid_constant_
 // plane, so that their latency overlaps the barrier.
 template <typename TImg, int RZ>
 __global__ void __launch_bounds__(kNT, 1) ngf_obj_kernel(const __grid_constant__ TileArgs<TImg> a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     constexpr int HZ = 1;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) float smem[];

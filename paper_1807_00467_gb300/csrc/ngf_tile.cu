@@ -121,6 +121,7 @@ __device__ __forceinline__ void write_box(const TileGeom &g, const float *rowA, 
 
 template <int TY, int MODE, typename TImg>
 __global__ void __launch_bounds__(32 * (TY + 4), TY == 8 ? 2 : 1) ngf_tile_kernel(const __grid_constant__ TileArgs<TImg> a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     using M = Mode<MODE>;
     constexpr int NW = TY + 4, NT = 32 * NW;
     constexpr unsigned FULL = 0xffffffffu;

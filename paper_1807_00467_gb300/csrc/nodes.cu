@@ -54,6 +54,7 @@ __device__ __forceinline__ void gather_boxes(const float *boxes, const BoxGeom &
 
 // w = L v per node (3 components) and per-block partials of |L v|^2.
 __global__ void __launch_bounds__(NT) curv_kernel(const NodeArgs a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     const int mx = a.m[0], my = a.m[1], mz = a.m[2];
     const long mxy = (long)mx * my, M = mxy * mz;
     const int kx = blockIdx.x * NX + (int)threadIdx.x % NX, ky = blockIdx.y * NY + ((int)threadIdx.x / NX) % NY;
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(NT) curv_kernel(const NodeArgs a) {
 
 // out = sA (NGF boxes) + sB (VCC boxes) + sC L^T w
 __global__ void __launch_bounds__(NT, 5) node_kernel(const NodeArgs a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     __shared__ int tabA[NX + NY + NZ], tabB[NX + NY + NZ];
     const int tid = threadIdx.x;
     const int mx = a.m[0], my = a.m[1], mz = a.m[2];

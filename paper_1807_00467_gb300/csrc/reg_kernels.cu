@@ -299,6 +299,7 @@ cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st) {
 int kp_blocks(int nk) { return nk <= 0 ? 1 : (nk + 255) / 256; }
 
 __global__ void kp_kernel(const KpArgs a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int mx = a.m[0], my = a.m[1], mz = a.m[2];
     const long mxy = (long)mx * my, M = mxy * mz;
@@ -356,6 +357,7 @@ __device__ double sum_parts(const double *p, int n) {
 }
 
 __global__ void terms_kernel(const TermsArgs a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     double D = a.dpart ? sum_parts(a.dpart, a.nd) * a.dscale : 0.0;
     __syncthreads();
     double R = a.rpart ? sum_parts(a.rpart, a.nr) * a.rscale : 0.0;
@@ -551,12 +553,14 @@ cudaError_t launch_dot_slot(long n, const float *Rh, long stride, const PcgScala
     return cudaGetLastError();
 }
 
-__global__ void axpy_copy_kernel(long n, float t, const float *x, const float *p, float *y) {
+__global__ void axpy_copy_kernel(long n, float t, const float *x, const float *p, float *y, const int *skip) {
+    if (skip && *skip) return;
     GRID_STRIDE(i, n) y[i] = fmaf(t, p[i], x[i]);
 }
 
-cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, float *y, cudaStream_t st) {
-    axpy_copy_kernel<<<vec_blocks(n), 256, 0, st>>>(n, t, x, p, y);
+cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, float *y, cudaStream_t st,
+                             const int *skip) {
+    axpy_copy_kernel<<<vec_blocks(n), 256, 0, st>>>(n, t, x, p, y, skip);
     return cudaGetLastError();
 }
 

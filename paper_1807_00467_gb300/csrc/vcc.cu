@@ -56,6 +56,7 @@ struct Kahan32 {
 // VM = 1: GN product along v.
 template <int VM>
 __global__ void __launch_bounds__(NC, VM == 1 ? 4 : 5) vcc_cell_kernel(const VccArgs a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     constexpr bool GN = VM == 1;
     __shared__ float su[3][NB];
     __shared__ float sv[GN ? 3 : 1][GN ? NB : 1];
