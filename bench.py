@@ -454,7 +454,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         out["solve_s"] = time.perf_counter() - t0
         out["solve_config"] = "3 levels x 10 GN x 30 PCG, Armijo; 128x128x32 -> 512x512x128"
-        out["batch"] = batch_rates(R, T, h, params, dev)
+        out["batch"] = batch_rates(params, dev)
         # the small workloads are launch- and latency-bound: eager vs CUDA-graph replay
         out["small"] = {name: small_config_rates(name, 200, dev) for name in ("tiny", "mid")}
         # precision form: images stored as FP16 (HU + 1024), FP32 per-voxel arithmetic
@@ -501,20 +501,32 @@ def run_ours(args):
     return 0
 
 
-def batch_rates(R, T, h, params, dev, n_pairs=24, runs=(("host", 1), ("host", 4), ("graph", 1), ("graph", 4),
-                                                        ("graph", 8))):
-    """Many uneven pairs (centred crops of one pair, 96x96x64 .. the whole
-    volume, log-uniform voxel counts), each through the 3-level pyramid with
-    10 GN x 30 PCG per level: pairs per minute on one stream against several
-    concurrent streams, and whether every pair's result is the same bits."""
+def batch_rates(params, dev, n_pairs=24, runs=(("host", 1), ("host", 4), ("graph", 1), ("graph", 4),
+                                              ("graph", 8))):
+    """24 independent phantom pairs (seeds 0-23, large motion with amplitudes
+    5-20 mm) of uneven sizes (96x96x64 .. 512x512x128, log-uniform voxel
+    counts, 358.4 x 358.4 x 320 mm field of view, grids n/4 + 1), images
+    stored as FP16 (HU + 1024), each through the 3-level pyramid with 10 GN x
+    30 PCG per level: pairs per minute by drive and number of streams, and
+    whether every pair's result has the same bits in every run."""
     import torch
-    from paper_1807_00467_gb300 import batch
-    shapes = batch.crop_shapes((R.shape[2], R.shape[1], R.shape[0]), n_pairs=n_pairs, seed=1)
-    pairs = batch.crop_pairs(R, T, h, shapes)
+    from paper_1807_00467_gb300 import batch, phantom
+    shapes = batch.batch_shapes(n_pairs=n_pairs, seed=0)
+    t0 = time.perf_counter()
+    host = phantom.batch_pairs(shapes, seeds=range(n_pairs))
+    gen_s = time.perf_counter() - t0
+    pairs = []
+    for (R, T, h), n in zip(host, shapes):
+        Rd = (torch.from_numpy(R).to(dev) + 1024.0).half()
+        Td = (torch.from_numpy(T).to(dev) + 1024.0).half()
+        pairs.append((Rd, Td, h, tuple(x // 4 + 1 for x in n)))
+    del host
+    torch.cuda.synchronize(dev)
     sched = dict(levels=3, gn_iters=10, pcg_iters=30)
     small = sorted(range(n_pairs), key=lambda i: pairs[i][0].numel())
     batch.register_batch([pairs[small[0]], pairs[small[-1]]], params, workers=2, drive="graph", **sched)   # load
-    res = {"pairs": n_pairs, "voxels": int(sum(p[0].numel() for p in pairs)),
+    res = {"pairs": n_pairs, "voxels": int(sum(p[0].numel() for p in pairs)), "images": "fp16 (HU + 1024)",
+           "phantom_seconds": gen_s,
            "smallest": list(shapes[small[0]]), "largest": list(shapes[small[-1]]),
            "schedule": "3 levels x 10 GN x 30 PCG per pair, Armijo", "runs": {}}
     first = None

@@ -9,12 +9,13 @@ most of the GPU idle on their own) overlap with those of other pairs.  The
 library calls release the interpreter lock, and every pair's work is ordered
 on its worker's stream, so results do not depend on the interleaving.
 
-``crop_shapes`` draws the uneven problem sizes of the batching workload:
-voxel counts log-uniform between 96 x 96 x 64 and the whole volume, z extent
+``batch_shapes`` draws the uneven problem sizes of the batching workload:
+voxel counts log-uniform between 96 x 96 x 64 and 512 x 512 x 128, z extent
 growing with the cube root of the count, every extent a multiple of 16 (three
-pyramid levels over a grid of one node per 4 voxels).  ``crop_pairs`` cuts the
-centred sub-volumes out of one reference/template pair on the device: each is
-a registration problem of its own under the same motion, at the same spacing.
+pyramid levels over a grid of one node per 4 voxels); ``phantom.batch_pairs``
+makes an independent image pair for each.  ``crop_pairs`` instead cuts
+centred sub-volumes out of one pair on the device (each a registration
+problem of its own under the same motion, at the same spacing).
 """
 from __future__ import annotations
 
@@ -26,19 +27,19 @@ import torch
 
 from . import api
 
-__all__ = ["crop_shapes", "crop_pairs", "register_batch"]
+__all__ = ["batch_shapes", "crop_pairs", "register_batch"]
 
-def crop_shapes(n_full, n_pairs=24, seed=0, lo=(96, 96, 64), q=16):
-    """[(nx, ny, nz)] of n_pairs sub-volumes of an n_full = (nx, ny, nz) volume."""
+def batch_shapes(n_pairs=24, seed=0, lo=(96, 96, 64), hi=(512, 512, 128), q=16):
+    """[(nx, ny, nz)] of n_pairs problems between the shapes lo and hi."""
     rng = np.random.default_rng(seed)
-    v0, v1 = float(np.prod(lo)), float(np.prod(n_full))
+    v0, v1 = float(np.prod(lo)), float(np.prod(hi))
     rq = lambda x, a, b: int(min(max(int(round(x / q)) * q, a), b))
     out = []
     for _ in range(n_pairs):
         v = np.exp(rng.uniform(np.log(v0), np.log(v1)))
-        nz = rq(lo[2] * (v / v0) ** (1.0 / 3.0), lo[2], n_full[2] // q * q)
-        nx = rq(np.sqrt(v / nz), lo[0], n_full[0] // q * q)
-        ny = rq(np.sqrt(v / nz), lo[1], n_full[1] // q * q)
+        nz = rq(lo[2] * (v / v0) ** (1.0 / 3.0), lo[2], hi[2] // q * q)
+        nx = rq(np.sqrt(v / nz), lo[0], hi[0] // q * q)
+        ny = rq(np.sqrt(v / nz), lo[1], hi[1] // q * q)
         out.append((nx, ny, nz))
     return out
 

@@ -331,6 +331,40 @@ def _make_phantom(n, h, seed, motion, amp_range, n_vessels, n_keypoints, kp_sigm
                    amps=amps, centres=centres, kp_x=kp_x, kp_y=kp_y, meta=meta)
 
 
+def _pair_job(job):
+    n, h, seed = job
+    ph = make_phantom(n, h, seed, motion="large")
+    return ph.R, ph.T
+
+
+def batch_pairs(shapes, seeds, fov=(358.4, 358.4, 320.0), procs=None):
+    """[(R, T, h)] for each shape (nx, ny, nz) and seed: independent phantoms
+    with large motion (amplitudes U(5, 20) mm) over one field of view, h =
+    fov / n.  Made in a pool of spawned processes (safe after the parent has
+    initialised CUDA), largest first."""
+    import multiprocessing as mp
+    hs = [tuple(fov[a] / n[a] for a in range(3)) for n in shapes]
+    jobs = [(tuple(n), h, int(sd)) for n, h, sd in zip(shapes, hs, seeds)]
+    order = sorted(range(len(jobs)), key=lambda i: -int(np.prod(jobs[i][0])))
+    procs = procs or max(1, min(len(jobs), os.cpu_count() or 1))
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})   # one thread per child: the pool fills the cores
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_pair_job, [jobs[i] for i in order], chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    out = [None] * len(jobs)
+    for k, i in enumerate(order):
+        out[i] = (res[k][0], res[k][1], hs[i])
+    return out
+
+
 def motion_on_grid(ph: Phantom, m, scale=1.0) -> np.ndarray:
     """u* sampled at the nodes of an m-node grid spanning the FOV, float32 [3][mz][my][mx]."""
     fov = np.array(ph.n) * np.array(ph.h)

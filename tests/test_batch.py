@@ -14,8 +14,8 @@ from helpers import oracle_problem
 TOL_U = 0.01    # mm, final displacement against the oracle
 
 
-def test_crop_shapes_are_pyramid_ready():
-    sh = batch.crop_shapes((512, 512, 128), n_pairs=200, seed=3)
+def test_batch_shapes_are_pyramid_ready():
+    sh = batch.batch_shapes(n_pairs=200, seed=3)
     v = np.array([np.prod(s) for s in sh], dtype=float)
     for s in sh:
         assert all(e % 16 == 0 for e in s)
@@ -23,7 +23,7 @@ def test_crop_shapes_are_pyramid_ready():
     # log-uniform counts: roughly half the pairs below the geometric mean
     gm = np.sqrt(96 * 96 * 64 * 512 * 512 * 128.0)
     assert 0.35 < np.mean(v < gm) < 0.65
-    assert sh == batch.crop_shapes((512, 512, 128), n_pairs=200, seed=3)
+    assert sh == batch.batch_shapes(n_pairs=200, seed=3)
 
 
 @pytest.mark.gpu
