@@ -537,6 +537,15 @@ def batch_rates(params, dev, n_pairs=24, runs=(("host", 1), ("host", 4), ("graph
         first = first if first is not None else us
         res["runs"][f"{drive}_x{w}"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
                                         "gn_matvec_per_s": mv / sec, "same_bits_as_first": bool(same)}
+    # tile shapes picked per level geometry by the autotuner (its timings are
+    # cached per process by an untimed pass first), graph drive, 8 streams
+    batch.register_batch(pairs, params, workers=8, drive="graph", autotune=True, **sched)
+    us, reps, sec = batch.register_batch(pairs, params, workers=8, drive="graph", autotune=True, **sched)
+    mv = int(sum(r[..., 6].sum() for r in reps))
+    res["runs"]["graph_x8_autotuned"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
+                                         "gn_matvec_per_s": mv / sec,
+                                         "max_abs_du_vs_first_mm": max(float((a - b).abs().max())
+                                                                      for a, b in zip(first, us))}
     del pairs, first
     torch.cuda.synchronize(dev)
     return res

@@ -107,6 +107,9 @@ typedef struct {
  * (otherwise the host-driven loop runs). */
 #define RG_SCHED_DEVICE 1
 #define RG_SCHED_GRAPH 2
+/* rg_schedule.flags: run rg_autotune on each level's context (at the start
+ * iterate) before its Gauss-Newton steps.  Combines with the flags above. */
+#define RG_SCHED_AUTOTUNE 4
 
 typedef struct rg_ctx rg_ctx;
 
@@ -132,6 +135,20 @@ int rg_set_stream(rg_ctx *ctx, void *cuda_stream);
  * for tuning.  The workspace covers both; results do not depend on it beyond
  * FP32 summation order.  Invalidates the stored preconditioner. */
 int rg_set_tile(rg_ctx *ctx, int32_t tile_y);
+
+/* Tile autotuner (the paper has no counterpart: it picks launch shapes).
+ * Candidates: 16-row tiles on the persistent objective/gradient and GN-product
+ * kernels (the default), 16-row tiles on the general column kernel, 8-row
+ * tiles on the general column kernel.  Each is timed with CUDA events on the
+ * context's stream at u_dev (one linearisation pass and three GN products,
+ * after one untimed round; the stream is synchronised) and scored as one
+ * Gauss-Newton iteration, gradient pass + 30 products; the fastest is kept in
+ * the context (tile_y / general, either may be NULL, report it) and cached
+ * per process by image and grid shape, image type and active terms, so later
+ * contexts of the same problem skip the timing.  Results of the candidates
+ * agree within the stated tolerances, not bit for bit.  The linearisation is
+ * discarded: call gn_linearize again before gn_matvec / gn_pcg_solve. */
+int rg_autotune(rg_ctx *ctx, const float *u_dev, int32_t *tile_y, int32_t *general);
 
 /* Borrow the reference R (fixed image F) and template T (moving image M),
  * [n3][n2][n1], float32 for RG_F32, IEEE half of (HU + 1024) for RG_F16.

@@ -42,7 +42,7 @@ EXPORTS = [
     "rg_set_images", "rg_set_keypoints", "ngf_objective", "ngf_gradient", "gn_linearize", "gn_matvec",
     "regularizer_apply", "gn_pcg_solve", "gn_solve", "rg_pyramid_workspace_size", "register_pyramid",
     "rg_restrict_image", "rg_prolong_grid", "rg_last_error", "rg_version", "rg_profile", "rg_profile_read",
-    "rg_launch_count", "ngf_distance_noalloc", "rg_set_tile",
+    "rg_launch_count", "ngf_distance_noalloc", "rg_set_tile", "rg_autotune",
 ]
 
 _lib = None
@@ -72,6 +72,7 @@ def load():
         "rg_get_params": ([vp, PP], C.c_int),
         "rg_set_stream": ([vp, vp], C.c_int),
         "rg_set_tile": ([vp, i32], C.c_int),
+        "rg_autotune": ([vp, vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "rg_set_images": ([vp, vp, vp], C.c_int),
         "rg_set_keypoints": ([vp, i32, fp, fp], C.c_int),
         "ngf_objective": ([vp, fp, dp], C.c_int),

@@ -43,14 +43,15 @@ def make_params(eta=10.0, alpha=1.0, gamma=0.0, delta=0.0, delta_adaptive=False,
     return Params(eta, alpha, gamma, delta, int(bool(delta_adaptive)), tau)
 
 
-SCHED_DEVICE, SCHED_GRAPH = 1, 2    # rg_schedule.flags
+SCHED_DEVICE, SCHED_GRAPH, SCHED_AUTOTUNE = 1, 2, 4    # rg_schedule.flags
 
 
-def make_schedule(levels=1, gn_iters=5, pcg_iters=30, ls_max=10, armijo_c=1e-4, drive="host"):
+def make_schedule(levels=1, gn_iters=5, pcg_iters=30, ls_max=10, armijo_c=1e-4, drive="host", autotune=False):
     """drive: 'host' (line search read on the host), 'device' (decided on the
     GPU, no per-iteration synchronisation) or 'graph' (device, with each
-    iteration replayed from a captured CUDA graph)."""
-    flags = {"host": 0, "device": SCHED_DEVICE, "graph": SCHED_GRAPH}[drive]
+    iteration replayed from a captured CUDA graph); autotune: pick each
+    level's tile shape with rg_autotune first."""
+    flags = {"host": 0, "device": SCHED_DEVICE, "graph": SCHED_GRAPH}[drive] | (SCHED_AUTOTUNE if autotune else 0)
     return Schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c, flags)
 
 
@@ -142,6 +143,14 @@ class Context:
         """Tile height (8 or 16 voxel rows) of the NGF kernels (tuning)."""
         _check(_lib.load().rg_set_tile(self._ctx, int(tile_y)), self._ctx, "rg_set_tile")
 
+    def autotune(self, u):
+        """Times the tile candidates at u and keeps the fastest; returns
+        (tile_y, general_kernel).  Discards the linearisation."""
+        ty, gen = C.c_int32(), C.c_int32()
+        _check(_lib.load().rg_autotune(self._ctx, _ptr(self._field(u)), C.byref(ty), C.byref(gen)), self._ctx,
+               "rg_autotune")
+        return ty.value, bool(gen.value)
+
     def set_keypoints(self, kx, ky):
         kx = kx.contiguous().float()
         ky = ky.contiguous().float()
@@ -199,9 +208,9 @@ class Context:
                "rg_profile_read")
         return ms.value, cnt.value
 
-    def gn_solve(self, u, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, drive="host"):
+    def gn_solve(self, u, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, drive="host", autotune=False):
         """Runs the fixed Gauss-Newton schedule in place on u; returns (status, report)."""
-        sched = make_schedule(1, gn_iters, pcg_iters, ls_max, armijo_c, drive)
+        sched = make_schedule(1, gn_iters, pcg_iters, ls_max, armijo_c, drive, autotune)
         rep = np.zeros((gn_iters, 8))
         code = _check(_lib.load().gn_solve(self._ctx, _ptr(self._field(u)), C.byref(sched),
                                            rep.ctypes.data_as(C.POINTER(C.c_double))), self._ctx, "gn_solve")
@@ -209,7 +218,7 @@ class Context:
 
 
 def register_pyramid(R, T, h, m_finest, u, params, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4,
-                     kx=None, ky=None, stream=None, drive="host"):
+                     kx=None, ky=None, stream=None, drive="host", autotune=False):
     """Multilevel registration; u (finest grid) is updated in place; returns (status, report)."""
     L = _lib.load()
     ig, gg = _img_geom(R.shape, h), _grid_geom(m_finest)
@@ -220,7 +229,7 @@ def register_pyramid(R, T, h, m_finest, u, params, levels, gn_iters, pcg_iters, 
            name="rg_pyramid_workspace_size")
     ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=R.device)
     wp = (ws.data_ptr() + 255) & ~255
-    sched = make_schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c, drive)
+    sched = make_schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c, drive, autotune)
     rep = np.zeros((levels, gn_iters, 8))
     code = L.register_pyramid(C.byref(ig), _ptr(R), _ptr(T), dtype, C.byref(gg), C.byref(params), C.byref(sched), nk,
                               _ptr(kx), _ptr(ky), _ptr(u), rep.ctypes.data_as(C.POINTER(C.c_double)),

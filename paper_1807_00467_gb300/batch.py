@@ -56,7 +56,8 @@ def crop_pairs(R, T, h, shapes, grid_step=4):
     return out
 
 
-def register_batch(pairs, params, levels, gn_iters, pcg_iters, workers=4, ls_max=10, armijo_c=1e-4, drive="host"):
+def register_batch(pairs, params, levels, gn_iters, pcg_iters, workers=4, ls_max=10, armijo_c=1e-4, drive="host",
+                   autotune=False):
     """Register every pair (R, T, h, m) (CUDA tensors, float32 or float16 of
     HU + 1024) from u = 0.  Returns (displacements, reports, seconds); the
     displacement of pair i is a float32 tensor (3, m3, m2, m1)."""
@@ -81,7 +82,7 @@ def register_batch(pairs, params, levels, gn_iters, pcg_iters, workers=4, ls_max
                 with torch.cuda.stream(s):   # u and the workspace belong to this stream
                     u = torch.zeros((3, m[2], m[1], m[0]), dtype=torch.float32, device=dev)
                     code, rep = api.register_pyramid(R, T, h, m, u, params, levels, gn_iters, pcg_iters, ls_max,
-                                                     armijo_c, stream=s, drive=drive)
+                                                     armijo_c, stream=s, drive=drive, autotune=autotune)
                 us[i], reps[i] = u, rep
         except Exception as e:   # reported after all workers have stopped
             errors.append(e)

@@ -10,6 +10,9 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ngfreg.h"
@@ -54,6 +57,7 @@ struct rg_ctx {
     cudaStream_t gst;         // private stream of device-driven schedules (created on first use)
     cudaEvent_t gev[2];
     long long launches;       // library kernels launched (or replayed) for this context
+    bool general_only;        // tile kernels: the general column kernel only (autotuner choice)
     // optional per-kernel CUDA-event timing (rg_profile)
     bool prof;
     std::vector<cudaEvent_t> *ev_pool;
@@ -467,7 +471,7 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
         a.skip = c->skip;
     };
     const int pid = mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1));
-    if ((mode == MODE_MATVEC || mode == MODE_DIAG) && gn_matvec_supported(c->tg)) {
+    if ((mode == MODE_MATVEC || mode == MODE_DIAG) && !c->general_only && gn_matvec_supported(c->tg)) {
         // the GN product and its diagonal read only the stored linearisation, not the images
         TileArgs<float> a;
         fill(a);
@@ -476,7 +480,8 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
         return RG_OK;
     }
     // objective, gradient and linearisation: the persistent pass where the tile shape allows
-    const bool grad_kernel = mode != MODE_MATVEC && mode != MODE_DIAG && ngf_grad_supported(c->tg);
+    const bool grad_kernel =
+        mode != MODE_MATVEC && mode != MODE_DIAG && !c->general_only && ngf_grad_supported(c->tg);
     if (c->dtype == RG_F32) {
         TileArgs<float> a;
         fill(a);
@@ -922,6 +927,7 @@ static int gn_solve_device(rg_ctx *c, float *u, const rg_schedule *s, double *re
 static int gn_solve_impl(rg_ctx *c, float *u, const rg_schedule *s, double *report, bool adapt) {
     int st;
     if (adapt && (st = set_delta_adaptive(c, u))) return st;
+    if ((s->flags & RG_SCHED_AUTOTUNE) && (st = rg_autotune(c, u, nullptr, nullptr))) return st;
     if ((s->flags & (RG_SCHED_DEVICE | RG_SCHED_GRAPH)) && s->gn_iters > 0 && s->gn_iters <= kGnRows && !c->prof)
         return gn_solve_device(c, u, s, report, (s->flags & RG_SCHED_GRAPH) != 0);
     const long n = 3 * c->M;
@@ -976,6 +982,95 @@ extern "C" int gn_solve(rg_ctx *c, float *u, const rg_schedule *s, double *repor
     if (!c || !u || !s || s->gn_iters < 0 || s->pcg_iters < 0 || s->ls_max < 0)
         return set_err(c, RG_EINVAL, "gn_solve: bad argument");
     return gn_solve_impl(c, u, s, report, c->P.delta_adaptive != 0);
+}
+
+// ---------------------------------------------------------------- autotuner
+// Tile shape and kernel family per problem geometry: 16-row tiles on the
+// persistent kernels, 16-row tiles on the general column kernel, 8-row tiles
+// on the general kernel.  Each is timed with CUDA events on the context's
+// stream (one linearisation pass and three GN products after one untimed
+// round) and scored as a Gauss-Newton iteration, gradient pass + 30 products.
+// The choice is cached per process by geometry, image type and active terms.
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+}  // namespace
+
+static TuneKey tune_key(const rg_ctx *c) {
+    return TuneKey{c->img.n[0], c->img.n[1], c->img.n[2], c->grid.m[0], c->grid.m[1], c->grid.m[2], (int)c->dtype,
+                   c->P.gamma != 0.0, c->nk > 0};
+}
+
+static int apply_tile(rg_ctx *c, int ty, int general) {
+    const int st = rg_set_tile(c, ty);
+    if (st != RG_OK) return st;
+    c->general_only = general != 0;
+    c->has_lin = false;
+    c->minv_valid = false;
+    return RG_OK;
+}
+
+extern "C" int rg_autotune(rg_ctx *c, const float *u, int32_t *tile_y, int32_t *general) {
+    if (!c || !u) return set_err(c, RG_EINVAL, "rg_autotune: NULL argument");
+    if (!c->R || !c->T) return set_err(c, RG_EINVAL, "rg_autotune: images not set");
+    const TuneKey key = tune_key(c);
+    std::pair<int, int> best{16, 0};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        const std::pair<int, int> cand[3] = {{16, 0}, {16, 1}, {8, 1}};
+        cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+        for (auto &x : e)
+            if (cudaEventCreate(&x) != cudaSuccess) {
+                for (auto y : e)
+                    if (y) cudaEventDestroy(y);
+                return set_err(c, RG_ECUDA, "rg_autotune: event creation failed");
+            }
+        double best_score = 1e300;
+        int st = RG_OK;
+        for (const auto &cd : cand) {
+            if ((st = apply_tile(c, cd.first, cd.second))) break;
+            float tg = 0.f, tm = 0.f;
+            for (int round = 0; round < 2 && st == RG_OK; ++round) {
+                if (cudaEventRecord(e[0], c->st) != cudaSuccess) st = set_err(c, RG_ECUDA, "rg_autotune: event");
+                if (!st) st = evaluate(c, u, c->terms_tmp, c->tg_, true);
+                if (!st && cudaEventRecord(e[1], c->st) != cudaSuccess) st = set_err(c, RG_ECUDA, "rg_autotune");
+                for (int k = 0; k < 3 && !st; ++k) st = matvec(c, c->tg_, c->q);
+                if (!st && cudaEventRecord(e[2], c->st) != cudaSuccess) st = set_err(c, RG_ECUDA, "rg_autotune");
+                if (!st && cudaEventSynchronize(e[2]) != cudaSuccess) st = set_err(c, RG_ECUDA, "rg_autotune");
+                if (!st) {
+                    cudaEventElapsedTime(&tg, e[0], e[1]);
+                    cudaEventElapsedTime(&tm, e[1], e[2]);
+                }
+            }
+            if (st) break;
+            const double score = tg + 30.0 * tm / 3.0;
+            if (score < best_score) {
+                best_score = score;
+                best = cd;
+            }
+        }
+        for (auto x : e) cudaEventDestroy(x);
+        if (st) {
+            apply_tile(c, 16, 0);
+            return st;
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best;
+    }
+    int st = apply_tile(c, best.first, best.second);
+    if (st) return st;
+    if (tile_y) *tile_y = best.first;
+    if (general) *general = best.second;
+    return RG_OK;
 }
 
 // ---------------------------------------------------------------- pyramid
