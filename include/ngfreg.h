@@ -255,6 +255,73 @@ const char *rg_last_error(const rg_ctx *ctx);
 /* Library build/version string. */
 const char *rg_version(void);
 
+/* ------------------------------------------------------------------------
+ * Discrete keypoint stage (Sec. II-C).  Images F (fixed) and M (moving) are
+ * float32 [n[2]][n[1]][n[0]] at 1 mm isotropic spacing (Sec. II-C resamples
+ * both scans to 1 mm^3); keypoints are int32 [nk][3] voxel positions
+ * (x, y, z), 2 <= nk <= 65535.  Displacement labels: d = 2 (i - 16) mm per
+ * axis, i = 0..32 (Sec. II-C2: {0, +-2, ..., +-32}^3 mm, 35 937 labels),
+ * label index l = (i_z 33 + i_y) 33 + i_x.  Positions outside the volume read
+ * the nearest voxel.  All pointers are device memory unless stated; calls are
+ * asynchronous on cuda_stream except where they say they synchronise.
+ * ------------------------------------------------------------------------ */
+#define KP_LABELS 35937
+
+typedef struct {
+    double eta;           /* NGF edge parameter (Eq. 1, as used in Eq. 2) */
+    double alpha;         /* alpha_KP of Eq. 3 */
+    double sigma_i;       /* sigma_I of Eq. 3 (150 in the paper) */
+} kp_params;
+
+/* Workspace bytes of kp_match (two feature volumes of n voxels x 16 bytes,
+ * four [nk][35937] float volumes, tree and MST scratch). */
+int kp_workspace_size(const int32_t *n, int32_t nk, size_t *bytes);
+/* Scratch bytes of kp_mst and kp_bp_marginals (one [nk][35937] message
+ * volume plus tree and MST scratch). */
+int kp_scratch_size(int32_t nk, size_t *bytes);
+
+/* NGF features of Eq. 2: feat[z][y][x] = (grad I, eta) / ||(grad I, eta)||
+ * as float4 (16-byte aligned), grad I by central differences over clamped
+ * neighbours, so that the NGF cosine of two images is the dot product. */
+int kp_ngf_features(const int32_t *n, const float *img, double eta, float *feat4, void *cuda_stream);
+
+/* Eq. 2: D[k][l] = (1/64) sum_p (1 - (n_M(k + p + d_l) . n_F(k + p))^2) over
+ * the 7^3 patch at stride 2 (p in {-3, -1, 1, 3}^3), float [nk][35937]. */
+int kp_cost_volume(const int32_t *n, const float *feat_fixed, const float *feat_moving, int32_t nk,
+                   const int32_t *kps, float *D, void *cuda_stream);
+
+/* Minimum spanning tree over the keypoints with the edge weight of Eq. 3's
+ * denominator, w = ||x_k - x_q|| + |I(k) - I(q)| / sigma_i (intensity: float
+ * [nk]), evaluated in FP32 with each operation rounded once; ties broken by
+ * (smaller index, larger index), so the tree is unique.  edges: int32
+ * [nk - 1][2] (smaller, larger), sorted.  Synchronises the stream; RG_ECUDA
+ * if the tree is incomplete. */
+int kp_mst(int32_t nk, const int32_t *kps, const float *intensity, double sigma_i, int32_t *edges, void *scratch,
+           size_t scratch_bytes, void *cuda_stream);
+
+/* Exact min-marginals of sum_k D(k, d_k) + sum_edges alpha ||d_k - d_q||^2 /
+ * w_kq (Eqs. 3-4) by two passes of min-sum belief propagation on the tree
+ * rooted at keypoint 0; messages are squared-distance min-convolutions over
+ * the label grid (axis by axis).  marginals: float [nk][35937].
+ * Synchronises the stream once (tree levels). */
+int kp_bp_marginals(int32_t nk, const float *D, const int32_t *kps, const float *intensity, const int32_t *edges,
+                    double sigma_i, double alpha, float *marginals, void *scratch, size_t scratch_bytes,
+                    void *cuda_stream);
+
+/* Sec. II-C2-4: features, cost volume, MST (intensities of F), marginals and
+ * their argmin; symmetric != 0 adds the backward search from x_k + d*_k with
+ * M fixed and F moving (intensities of M) and takes the argmin of
+ * (E_fw(k, d) + E_bw(k, -d)) / 2 (lowest label among equal energies).
+ * disp: int32 [nk][3] displacements in voxels (mm).  marginals: NULL, or
+ * float [nk][35937] forward marginals followed (symmetric) by [nk][35937]
+ * backward ones.  Synchronises the stream. */
+int kp_match(const int32_t *n, const float *F, const float *M, int32_t nk, const int32_t *kps, const kp_params *p,
+             int32_t symmetric, int32_t *disp, float *marginals, void *workspace, size_t ws_bytes,
+             void *cuda_stream);
+
+/* Kernels launched by the kp_* entry points in this process so far. */
+int64_t kp_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

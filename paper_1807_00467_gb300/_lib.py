@@ -42,7 +42,8 @@ EXPORTS = [
     "rg_set_images", "rg_set_keypoints", "ngf_objective", "ngf_gradient", "gn_linearize", "gn_matvec",
     "regularizer_apply", "gn_pcg_solve", "gn_solve", "rg_pyramid_workspace_size", "register_pyramid",
     "rg_restrict_image", "rg_prolong_grid", "rg_last_error", "rg_version", "rg_profile", "rg_profile_read",
-    "rg_launch_count", "ngf_distance_noalloc", "rg_set_tile", "rg_autotune",
+    "rg_launch_count", "ngf_distance_noalloc", "rg_set_tile", "rg_autotune", "kp_workspace_size", "kp_scratch_size",
+    "kp_ngf_features", "kp_cost_volume", "kp_mst", "kp_bp_marginals", "kp_match", "kp_launch_count",
 ]
 
 _lib = None
@@ -73,6 +74,14 @@ def load():
         "rg_set_stream": ([vp, vp], C.c_int),
         "rg_set_tile": ([vp, i32], C.c_int),
         "rg_autotune": ([vp, vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "kp_workspace_size": ([C.POINTER(i32), i32, C.POINTER(sz)], C.c_int),
+        "kp_scratch_size": ([i32, C.POINTER(sz)], C.c_int),
+        "kp_ngf_features": ([C.POINTER(i32), vp, C.c_double, vp, vp], C.c_int),
+        "kp_cost_volume": ([C.POINTER(i32), vp, vp, i32, vp, vp, vp], C.c_int),
+        "kp_mst": ([i32, vp, vp, C.c_double, vp, vp, sz, vp], C.c_int),
+        "kp_bp_marginals": ([i32, vp, vp, vp, vp, C.c_double, C.c_double, vp, vp, sz, vp], C.c_int),
+        "kp_match": ([C.POINTER(i32), vp, vp, i32, vp, vp, i32, vp, vp, vp, sz, vp], C.c_int),
+        "kp_launch_count": ([], C.c_longlong),
         "rg_set_images": ([vp, vp, vp], C.c_int),
         "rg_set_keypoints": ([vp, i32, fp, fp], C.c_int),
         "ngf_objective": ([vp, fp, dp], C.c_int),

@@ -1,0 +1,133 @@
+"""Discrete keypoint stage (Sec. II-C) on the GPU against the FP64 oracle.
+
+Tolerances: features and the Eq. 2 costs (means of 64 FP32 terms in [0, 1])
+within 2e-6 absolute; the MST bit for bit (both sides decide it in FP32 with
+the same rounding and order); min-marginals (FP32 sums along tree paths of
+values up to ~nk) within 1e-5 of each keypoint's largest energy; label
+decisions equal wherever the oracle's gap between its best and second-best
+label exceeds that tolerance, and the GPU's label within the tolerance of the
+oracle's minimum elsewhere."""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import discrete as Dq
+
+from paper_1807_00467_gb300 import phantom
+
+pytestmark = pytest.mark.gpu
+
+TOL_F, TOL_D, TOL_E = 2e-6, 2e-6, 1e-5
+
+
+@functools.lru_cache(maxsize=2)
+def _pair():
+    ph = phantom.make_phantom((96, 96, 80), (1.0, 1.0, 1.0), seed=3, motion="large", n_keypoints=400)
+    kp = np.unique(np.rint(ph.kp_x.astype(np.float64) - 0.5).astype(np.int64), axis=0)
+    return ph.R, ph.T, kp
+
+
+def _dev(x, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    return (t.to(dtype) if dtype is not None else t).cuda()
+
+
+def _check_labels(E_gpu, E_or, tol_rows):
+    """Equal argmin where the oracle's gap exceeds the row tolerance; else the
+    GPU's label within the tolerance of the oracle's minimum."""
+    a_g, a_o = np.argmin(E_gpu, axis=1), np.argmin(E_or, axis=1)
+    srt = np.sort(E_or, axis=1)
+    gap = srt[:, 1] - srt[:, 0]
+    for k in range(E_or.shape[0]):
+        if gap[k] > tol_rows[k]:
+            assert a_g[k] == a_o[k], k
+        else:
+            assert E_or[k, a_g[k]] - srt[k, 0] <= 2 * tol_rows[k], k
+    return a_g, a_o, gap
+
+
+def test_features_match_oracle():
+    import torch
+    from paper_1807_00467_gb300 import discrete
+    R, T, kp = _pair()
+    f = discrete.features(_dev(R), 10.0).cpu().numpy()
+    fo = Dq.ngf_features(R, 10.0)
+    assert np.abs(f - fo).max() <= TOL_F
+
+
+def test_cost_volume_matches_oracle_including_borders():
+    from paper_1807_00467_gb300 import discrete
+    R, T, kp = _pair()
+    kps = np.concatenate([kp[::40], [[0, 0, 0], [95, 2, 79], [50, 95, 1]]])   # windows cross the borders
+    fF, fM = discrete.features(_dev(R)), discrete.features(_dev(T))
+    D = discrete.cost_volume(fF, fM, _dev(kps, None).int()).cpu().numpy()
+    Do = Dq.cost_volume(Dq.ngf_features(R, 10.0), Dq.ngf_features(T, 10.0), kps)
+    err = np.abs(D - Do).max()
+    print(f"cost volume: {len(kps)} keypoints, max |D - D_oracle| = {err:.2e}")
+    assert err <= TOL_D
+
+
+@pytest.mark.parametrize("case", ["phantom", "lattice_ties"])
+def test_mst_is_bit_exact(case):
+    import torch
+    from paper_1807_00467_gb300 import discrete
+    if case == "phantom":
+        R, T, kp = _pair()
+        kps = kp[:300]
+        inten = R[kps[:, 2], kps[:, 1], kps[:, 0]]
+    else:   # 4 x 5 x 6 lattice at spacing 2, equal intensities: many equal weights
+        g = np.stack(np.meshgrid(np.arange(4), np.arange(5), np.arange(6), indexing="ij"), -1).reshape(-1, 3) * 2
+        kps = g[np.random.default_rng(1).permutation(len(g))]
+        inten = np.full(len(kps), -850.0, np.float32)
+    e = discrete.mst(_dev(kps).int(), _dev(np.asarray(inten, np.float32)), 150.0).cpu().numpy()
+    eo = Dq.mst(Dq.edge_weights(kps, inten))
+    np.testing.assert_array_equal(e, eo)
+
+
+@pytest.mark.parametrize("nk", [2, 40])
+def test_bp_marginals_match_oracle(nk):
+    from paper_1807_00467_gb300 import discrete
+    R, T, kp = _pair()
+    kps = kp[:: max(1, len(kp) // nk)][:nk]
+    inten = R[kps[:, 2], kps[:, 1], kps[:, 0]]
+    D = np.random.default_rng(nk).random((nk, Dq.N_STEPS ** 3)).astype(np.float32)
+    W = Dq.edge_weights(kps, inten)
+    eo = Dq.mst(W)
+    E = discrete.bp_marginals(_dev(D), _dev(kps).int(), _dev(inten), _dev(eo).int(), alpha=0.2).cpu().numpy()
+    Eo = Dq.bp_marginals(D.astype(np.float64), eo, W, 0.2)
+    tol = TOL_E * np.abs(Eo).max(axis=1)
+    err = np.abs(E - Eo).max(axis=1)
+    print(f"bp nk={nk}: max rel marginal error {np.max(err / np.abs(Eo).max(axis=1)):.2e}")
+    assert np.all(err <= tol)
+    _check_labels(E, Eo, tol)
+
+
+def test_symmetric_match_against_oracle():
+    from paper_1807_00467_gb300 import discrete
+    R, T, kp = _pair()
+    kps = kp[::16][:24]
+    nk = len(kps)
+    m = discrete.Matcher(R.shape, nk, eta=10.0, alpha=0.2)
+    disp, E = m.match(_dev(R), _dev(T), _dev(kps).int(), symmetric=True, marginals=True)
+    disp, E = disp.cpu().numpy(), E.cpu().numpy()
+    Efw, Ebw = E[:nk], E[nk:]
+    # the oracle's forward marginals and decisions
+    fF, fM = Dq.ngf_features(R, 10.0), Dq.ngf_features(T, 10.0)
+    inten = R[kps[:, 2], kps[:, 1], kps[:, 0]]
+    W = Dq.edge_weights(kps, inten)
+    Eo = Dq.bp_marginals(Dq.cost_volume(fF, fM, kps), Dq.mst(W), W, 0.2)
+    tol = TOL_E * np.abs(Eo).max(axis=1)
+    assert np.all(np.abs(Efw - Eo).max(axis=1) <= tol)
+    a_g, a_o, gap = _check_labels(Efw, Eo, tol)
+    if not np.array_equal(a_g, a_o):
+        pytest.skip("a forward near-tie: the backward searches start from different points")
+    d_o, Es_o = Dq.match(R, T, kps, eta=10.0, alpha=0.2, symmetric=True)
+    Es = 0.5 * (Efw + Ebw[:, Dq.mirror_labels()])
+    tol_s = TOL_E * np.abs(Es_o).max(axis=1)
+    assert np.all(np.abs(Es - Es_o).max(axis=1) <= tol_s)
+    a_s, a_so, _ = _check_labels(Es, Es_o, tol_s)
+    np.testing.assert_array_equal(disp, Dq.label_displacements()[a_s])
+    print(f"match: {nk} keypoints, |d| mean {np.abs(disp).sum(1).mean():.1f} mm, "
+          f"agree with the oracle on {np.mean(a_s == a_so) * 100:.0f}% of labels")
