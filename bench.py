@@ -211,6 +211,84 @@ def cpu_baseline(ph, m, seconds):
             "sample": f"{n} oracle GN products at 512x512x128 ({dt:.1f} s, after one untimed linearisation)"}
 
 
+DISC_SHAPE = (224, 192, 192)   # (nx, ny, nz) voxels at 1 mm: the lungs resampled to 1 mm^3 (Sec. II-C)
+FP32_LANES = 152 * 128         # FP32 lanes of the GPU (152 SMs x 128)
+
+
+def discrete_phantom():
+    """1 mm isotropic pair with large motion and ~3000 vessel-centreline keypoints."""
+    import numpy as np
+
+    from paper_1807_00467_gb300 import phantom
+    ph = phantom.make_phantom(DISC_SHAPE, (1.0, 1.0, 1.0), seed=0, motion="large", n_keypoints=3000)
+    kp = np.unique(np.rint(ph.kp_x.astype(np.float64) - 0.5).astype(np.int64), axis=0)
+    return ph, kp
+
+
+def discrete_rates(ph, kp, dev, sm_mhz, reps=3):
+    """Sec. II-C on the GPU: the symmetric match of all keypoints (features,
+    Eq. 2 cost volumes, MSTs, two-pass BP per direction, refinement), and each
+    stage of the forward direction timed alone with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_1807_00467_gb300 import discrete
+    s = torch.cuda.Stream(device=dev)
+    F, M = torch.from_numpy(ph.R).to(dev), torch.from_numpy(ph.T).to(dev)
+    K = torch.from_numpy(kp.astype(np.int32)).to(dev)
+    nk = len(kp)
+    mt = discrete.Matcher(ph.R.shape, nk, device=dev)
+    torch.cuda.synchronize(dev)
+    mt.match(F, M, K, symmetric=True, stream=s)   # kernels loaded
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    l0 = discrete.launch_count()
+    ev[0].record(s)
+    for _ in range(reps):
+        disp = mt.match(F, M, K, symmetric=True, stream=s)
+    ev[1].record(s)
+    s.synchronize()
+    launches = (discrete.launch_count() - l0) // reps
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    with torch.cuda.stream(s):
+        ev[0].record(s)
+        fF = discrete.features(F, stream=s)
+        fM = discrete.features(M, stream=s)
+        ev[1].record(s)
+        D = discrete.cost_volume(fF, fM, K, stream=s)
+        ev[2].record(s)
+        inten = F[K[:, 2].long(), K[:, 1].long(), K[:, 0].long()]
+        ev[3].record(s)
+        E = discrete.mst(K, inten, stream=s)
+        ev[4].record(s)
+        discrete.bp_marginals(D, K, inten, E, stream=s)
+        ev[5].record(s)
+    s.synchronize()
+    t = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+    flops = nk * discrete.LABELS * 64 * 10.0          # 4-term dot + squared accumulate per patch point
+    peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    ach = flops / (t[1] / 1e3) / 1e12
+    dd = disp.cpu().numpy()
+    return {"workload": f"{DISC_SHAPE[0]}x{DISC_SHAPE[1]}x{DISC_SHAPE[2]} at 1 mm, {nk} keypoints, 35937 labels, "
+                        "64-voxel patches, symmetric", "keypoints": nk, "ms_per_match": ms,
+            "keypoints_per_s": nk / (ms / 1e3), "gpu_launches_per_match": launches,
+            "stages_ms_forward": {"features_x2": t[0], "cost_volume": t[1], "mst": t[3], "bp_two_pass": t[4]},
+            "roofline": {"bound": "alu", "kernel": "cost_volume", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x sampled SM clock",
+                         "flop_per_launch": flops},
+            "mean_abs_disp_mm": float(np.abs(dd).sum(axis=1).mean())}
+
+
+def cpu_discrete(ph, kp, n_sample=4):
+    """The oracle's symmetric match (Sec. II-C) for a sample of keypoints."""
+    import oracle
+    from oracle import discrete as Dq
+    t0 = time.perf_counter()
+    Dq.match(ph.R, ph.T, kp[:: max(1, len(kp) // n_sample)][:n_sample], eta=10.0, alpha=0.2)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": "keypoints/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"symmetric match of {n_sample} keypoints ({dt:.1f} s, numpy FP64)"}
+
+
 def replica_seed(rank):
     """Each rank registers its own phantom pair (replicas: no data-path collective)."""
     return rank
@@ -455,6 +533,8 @@ def run_ours(args):
         out["solve_s"] = time.perf_counter() - t0
         out["solve_config"] = "3 levels x 10 GN x 30 PCG, Armijo; 128x128x32 -> 512x512x128"
         out["batch"] = batch_rates(params, dev)
+        ph_d, kp_d = discrete_phantom()
+        out["discrete"] = discrete_rates(ph_d, kp_d, dev, clk.get("sm_mhz") or 2070.0)
         # the small workloads are launch- and latency-bound: eager vs CUDA-graph replay
         out["small"] = {name: small_config_rates(name, 200, dev) for name in ("tiny", "mid")}
         # precision form: images stored as FP16 (HU + 1024), FP32 per-voxel arithmetic
@@ -494,6 +574,7 @@ def run_ours(args):
         del ctx16
         if rank == 0 and world == 1:
             out["cpu_baseline"] = cpu_baseline(ph, m, args.cpu_seconds)
+            out["cpu_baseline"]["discrete"] = cpu_discrete(ph_d, kp_d)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -537,9 +618,9 @@ def batch_rates(params, dev, n_pairs=24, runs=(("host", 1), ("host", 4), ("graph
         first = first if first is not None else us
         res["runs"][f"{drive}_x{w}"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
                                         "gn_matvec_per_s": mv / sec, "same_bits_as_first": bool(same)}
-    # tile shapes picked per level geometry by the autotuner (its timings are
-    # cached per process by an untimed pass first), graph drive, 8 streams
-    batch.register_batch(pairs, params, workers=8, drive="graph", autotune=True, **sched)
+    # tile shapes picked per level geometry by the autotuner (timed on one
+    # stream in an untimed pass and cached per process), graph drive, 8 streams
+    batch.register_batch(pairs, params, workers=1, drive="graph", autotune=True, **sched)
     us, reps, sec = batch.register_batch(pairs, params, workers=8, drive="graph", autotune=True, **sched)
     mv = int(sum(r[..., 6].sum() for r in reps))
     res["runs"]["graph_x8_autotuned"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,

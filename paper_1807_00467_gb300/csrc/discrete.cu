@@ -215,24 +215,18 @@ __global__ void mst_sort_kernel(int m, const int *edges, const int *nedges, int 
 
 // ------------------------------------------------------------ tree
 // One CTA: adjacency lists (sorted), breadth-first levels from the root,
-// parents and sorted child lists.  Scratch: deg/off/cur [n + 1] each, adj [2 (n - 1)].
-__global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *edges, int *deg, int *off, int *adj,
-                                                    int *order, int *level_off, int *nlevels, int *parent,
-                                                    int *child_off, int *child) {
+// parents and sorted child lists.  Edges with an index outside [0, n) or
+// equal ends are ignored and each vertex is claimed once, so a list that is
+// not a spanning tree cannot write out of bounds (vertices it does not reach
+// are left out of the levels).  Scratch: deg/off [n + 1] each, adj [2 n].
+__device__ __forceinline__ bool edge_ok(int n, int a, int b) { return a >= 0 && a < n && b >= 0 && b < n && a != b; }
+
+// exclusive scan of cnt[0..n) into out[0..n], one CTA (chunks per thread)
+__device__ void cta_scan(int n, const int *cnt, int *out, int *s_part) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    __shared__ int s_count, s_lvl;
-    __shared__ int s_part[1024];
-    for (int v = tid; v <= n; v += nt) deg[v] = 0;
-    __syncthreads();
-    for (int e = tid; e < n - 1; e += nt) {
-        atomicAdd(deg + edges[2 * e], 1);
-        atomicAdd(deg + edges[2 * e + 1], 1);
-    }
-    __syncthreads();
-    // exclusive scan of deg into off (chunks per thread, then the chunk sums)
     const int chunk = (n + nt - 1) / nt, a0 = min(n, tid * chunk), a1 = min(n, a0 + chunk);
     int s = 0;
-    for (int v = a0; v < a1; ++v) s += deg[v];
+    for (int v = a0; v < a1; ++v) s += cnt[v];
     s_part[tid] = s;
     __syncthreads();
     if (tid == 0) {
@@ -242,24 +236,45 @@ __global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *
             s_part[i] = t;
             t += x;
         }
+        s_part[nt] = t;
     }
     __syncthreads();
     s = s_part[tid];
     for (int v = a0; v < a1; ++v) {
-        off[v] = s;
-        s += deg[v];
+        const int c = cnt[v];
+        out[v] = s;
+        s += c;
     }
-    if (tid == nt - 1) off[n] = 2 * (n - 1);
+    if (tid == 0) out[n] = s_part[nt];
     __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *edges, int *deg, int *off, int *adj,
+                                                    int *order, int *level_off, int *nlevels, int *parent,
+                                                    int *child_off, int *child) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ int s_count, s_lvl;
+    __shared__ int s_part[1025];
+    for (int v = tid; v <= n; v += nt) deg[v] = 0;
+    __syncthreads();
+    for (int e = tid; e < n - 1; e += nt) {
+        const int a = edges[2 * e], b = edges[2 * e + 1];
+        if (!edge_ok(n, a, b)) continue;
+        atomicAdd(deg + a, 1);
+        atomicAdd(deg + b, 1);
+    }
+    __syncthreads();
+    cta_scan(n, deg, off, s_part);
     for (int v = tid; v < n; v += nt) deg[v] = off[v];   // fill cursors
     __syncthreads();
     for (int e = tid; e < n - 1; e += nt) {
         const int a = edges[2 * e], b = edges[2 * e + 1];
+        if (!edge_ok(n, a, b)) continue;
         adj[atomicAdd(deg + a, 1)] = b;
         adj[atomicAdd(deg + b, 1)] = a;
     }
     __syncthreads();
-    for (int v = tid; v < n; v += nt)   // insertion sort of each (short) list
+    for (int v = tid; v < n; v += nt) {   // insertion sort of each (short) list
         for (int i = off[v] + 1; i < off[v + 1]; ++i) {
             const int x = adj[i];
             int j = i - 1;
@@ -269,7 +284,8 @@ __global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *
             }
             adj[j + 1] = x;
         }
-    for (int v = tid; v < n; v += nt) parent[v] = -2;   // unvisited
+        parent[v] = -2;   // unvisited
+    }
     __syncthreads();
     if (tid == 0) {
         order[0] = root;
@@ -280,18 +296,14 @@ __global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *
         s_lvl = 0;
     }
     __syncthreads();
-    // level by level: at most n levels
-    for (int lv = 0; lv < n; ++lv) {
+    for (int lv = 0; lv < n; ++lv) {   // at most n levels
         const int b0 = level_off[lv], b1 = level_off[lv + 1];
         if (b0 == b1) break;
         for (int i = b0 + tid; i < b1; i += nt) {
             const int v = order[i];
             for (int j = off[v]; j < off[v + 1]; ++j) {
                 const int u = adj[j];
-                if (u != parent[v]) {
-                    parent[u] = v;
-                    order[atomicAdd(&s_count, 1)] = u;
-                }
+                if (atomicCAS(parent + u, -2, v) == -2) order[atomicAdd(&s_count, 1)] = u;
             }
         }
         __syncthreads();
@@ -302,15 +314,19 @@ __global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *
         __syncthreads();
     }
     if (tid == 0) *nlevels = s_lvl;   // levels 0 .. s_lvl - 1 are non-empty
-    // child lists: the sorted adjacency without the parent
-    for (int v = tid; v < n; v += nt) child_off[v] = off[v] - v + (v > root ? 1 : 0);
+    // child lists: the neighbours claimed by v, in sorted order
+    for (int v = tid; v < n; v += nt) {
+        int c = 0;
+        for (int j = off[v]; j < off[v + 1]; ++j) c += parent[adj[j]] == v;
+        deg[v] = c;
+    }
     __syncthreads();
+    cta_scan(n, deg, child_off, s_part);
     for (int v = tid; v < n; v += nt) {
         int c = child_off[v];
         for (int j = off[v]; j < off[v + 1]; ++j)
-            if (adj[j] != parent[v]) child[c++] = adj[j];
+            if (parent[adj[j]] == v) child[c++] = adj[j];
     }
-    if (tid == 0) child_off[n] = n - 1;
 }
 
 // ------------------------------------------------------------ belief propagation

@@ -341,7 +341,8 @@ def batch_pairs(shapes, seeds, fov=(358.4, 358.4, 320.0), procs=None):
     """[(R, T, h)] for each shape (nx, ny, nz) and seed: independent phantoms
     with large motion (amplitudes U(5, 20) mm) over one field of view, h =
     fov / n.  Made in a pool of spawned processes (safe after the parent has
-    initialised CUDA), largest first."""
+    initialised CUDA), largest first; a calling script must guard its entry
+    point with ``if __name__ == "__main__":`` (spawned children import it)."""
     import multiprocessing as mp
     hs = [tuple(fov[a] / n[a] for a in range(3)) for n in shapes]
     jobs = [(tuple(n), h, int(sd)) for n, h, sd in zip(shapes, hs, seeds)]
