@@ -360,80 +360,102 @@ struct BpArgs {
 // spread over a cluster of 8 CTAs: CTA r owns z planes [4 r, 4 r + 4) (the
 // last one also plane 32), runs the x and y passes on them, and after a
 // cluster barrier the z pass on its share of the 1089 (y, x) columns, reading
-// the planes of the other CTAs through distributed shared memory.
+// the planes of the other CTAs through distributed shared memory.  The UP
+// pass leaves h_k = D_k + sum of the children's messages in marg[k]; the DOWN
+// pass adds the parent's message to it, which completes k's marginal.
 template <bool DOWN>
 __global__ void __launch_bounds__(kBpT) bp_message_kernel(const BpArgs a) {
+    constexpr int kPer = (5 * kPlane + kBpT - 1) / kBpT;   // slab values per thread
     __shared__ float s[5 * kPlane];
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank();
     const int k = a.order[a.base + blockIdx.x / kCl];
     const int q = a.parent[k];
-    const int z0 = 4 * r, nzp = r == kCl - 1 ? 5 : 4;
+    const int z0 = 4 * r, nzp = r == kCl - 1 ? 5 : 4, nown = nzp * kPlane;
     const int tid = threadIdx.x;
     const float lam = __fdiv_rn(a.alpha, edge_w(a.kps, a.inten, a.sig, k, q));
     float C[kS];
 #pragma unroll
     for (int d = 0; d < kS; ++d) C[d] = d == 0 ? 0.f : lam * (float)(4 * d * d);
-    // h over the own planes: UP: D_k + sum of the children's messages;
-    // DOWN: marginal of the parent without k's message
+    // h over the own planes (all loads of one array issued together): UP:
+    // D_k + the children's messages; DOWN: the parent's marginal without k's message
     const long pb = (long)z0 * kPlane;
-    for (int i = tid; i < nzp * kPlane; i += kBpT) {
-        float h;
-        if (DOWN) {
-            h = a.marg[(long)q * kL + pb + i] - a.up[(long)k * kL + pb + i];
-        } else {
-            h = a.D[(long)k * kL + pb + i];
-            for (int c = a.child_off[k]; c < a.child_off[k + 1]; ++c) h += a.up[(long)a.child[c] * kL + pb + i];
+    {
+        float h[kPer];
+        const float *src = DOWN ? a.marg + (long)q * kL + pb : a.D + (long)k * kL + pb;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const int i = tid + t * kBpT;
+            h[t] = i < nown ? __ldg(src + i) : 0.f;
         }
-        s[i] = h;
-    }
-    __syncthreads();
-    // x pass, then y pass, one line per thread
-    if (tid < nzp * kS) {
-        const int zl = tid / kS, y = tid - zl * kS;
-        float v[kS];
-#pragma unroll
-        for (int i = 0; i < kS; ++i) v[i] = s[zl * kPlane + y * kS + i];
-        min_conv_line(v, C);
-#pragma unroll
-        for (int i = 0; i < kS; ++i) s[zl * kPlane + y * kS + i] = v[i];
-    }
-    __syncthreads();
-    if (tid < nzp * kS) {
-        const int zl = tid / kS, x = tid - zl * kS;
-        float v[kS];
-#pragma unroll
-        for (int i = 0; i < kS; ++i) v[i] = s[zl * kPlane + i * kS + x];
-        min_conv_line(v, C);
-#pragma unroll
-        for (int i = 0; i < kS; ++i) s[zl * kPlane + i * kS + x] = v[i];
-    }
-    cl.sync();   // every CTA's planes are complete
-    // z pass on columns [j0, j1)
-    const int per = (kPlane + kCl - 1) / kCl, j0 = r * per, j1 = min(kPlane, j0 + per);
-    const int j = j0 + tid;
-    if (j < j1) {
-        float v[kS];
-#pragma unroll
-        for (int z = 0; z < kS; ++z) {
-            const int owner = z / 4 < kCl - 1 ? z / 4 : kCl - 1;
-            const float *rs = cl.map_shared_rank(s, owner);
-            v[z] = rs[(z - 4 * owner) * kPlane + j];
-        }
-        min_conv_line(v, C);
         if (DOWN) {
+            const float *u = a.up + (long)k * kL + pb;
 #pragma unroll
-            for (int z = 0; z < kS; ++z) {
-                const long o = (long)k * kL + (long)z * kPlane + j;
-                float m = a.D[o];
-                for (int c = a.child_off[k]; c < a.child_off[k + 1]; ++c)
-                    m += a.up[(long)a.child[c] * kL + (long)z * kPlane + j];
-                a.marg[o] = m + v[z];
+            for (int t = 0; t < kPer; ++t) {
+                const int i = tid + t * kBpT;
+                if (i < nown) h[t] -= __ldg(u + i);
             }
         } else {
+            for (int c = a.child_off[k]; c < a.child_off[k + 1]; ++c) {
+                const float *u = a.up + (long)a.child[c] * kL + pb;
 #pragma unroll
-            for (int z = 0; z < kS; ++z) a.up[(long)k * kL + (long)z * kPlane + j] = v[z];
+                for (int t = 0; t < kPer; ++t) {
+                    const int i = tid + t * kBpT;
+                    if (i < nown) h[t] += __ldg(u + i);
+                }
+            }
+            float *mk = a.marg + (long)k * kL + pb;
+#pragma unroll
+            for (int t = 0; t < kPer; ++t) {
+                const int i = tid + t * kBpT;
+                if (i < nown) mk[i] = h[t];
+            }
         }
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const int i = tid + t * kBpT;
+            if (i < nown) s[i] = h[t];
+        }
+    }
+    __syncthreads();
+    // x pass, y pass (own planes, one line per thread), then the z pass over
+    // columns [j0, j1) of all planes; one copy of the line code for all three
+    const int per = (kPlane + kCl - 1) / kCl, j0 = r * per, j1 = min(kPlane, j0 + per);
+    const int zl = tid / kS, w = tid - zl * kS, j = j0 + tid;
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+        if (pass == 2) cl.sync();   // every CTA's planes are complete
+        const bool act = pass < 2 ? tid < nzp * kS : j < j1;
+        float v[kS];
+        if (act) {
+            if (pass < 2) {
+                const int base = zl * kPlane + (pass == 0 ? w * kS : w), step = pass == 0 ? 1 : kS;
+#pragma unroll
+                for (int i = 0; i < kS; ++i) v[i] = s[base + i * step];
+            } else {
+#pragma unroll
+                for (int z = 0; z < kS; ++z) {
+                    const int owner = z / 4 < kCl - 1 ? z / 4 : kCl - 1;
+                    const float *rs = cl.map_shared_rank(s, owner);
+                    v[z] = rs[(z - 4 * owner) * kPlane + j];
+                }
+            }
+            min_conv_line(v, C);
+            if (pass < 2) {
+                const int base = zl * kPlane + (pass == 0 ? w * kS : w), step = pass == 0 ? 1 : kS;
+#pragma unroll
+                for (int i = 0; i < kS; ++i) s[base + i * step] = v[i];
+            } else if (DOWN) {
+                float *mk = a.marg + (long)k * kL + j;
+#pragma unroll
+                for (int z = 0; z < kS; ++z) mk[(long)z * kPlane] += v[z];
+            } else {
+                float *uk = a.up + (long)k * kL + j;
+#pragma unroll
+                for (int z = 0; z < kS; ++z) uk[(long)z * kPlane] = v[z];
+            }
+        }
+        if (pass < 2) __syncthreads();
     }
     cl.sync();   // no CTA leaves while another may still read its planes
 }
