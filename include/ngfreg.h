@@ -301,7 +301,9 @@ int kp_mst(int32_t nk, const int32_t *kps, const float *intensity, double sigma_
 
 /* Exact min-marginals of sum_k D(k, d_k) + sum_edges alpha ||d_k - d_q||^2 /
  * w_kq (Eqs. 3-4) by two passes of min-sum belief propagation on the tree
- * rooted at keypoint 0; messages are squared-distance min-convolutions over
+ * rooted at its centre (the middle of a longest path, which minimises the
+ * number of levels; exact min-marginals do not depend on the root); messages
+ * are squared-distance min-convolutions over
  * the label grid (axis by axis).  marginals: float [nk][35937].
  * Synchronises the stream once (tree levels). */
 int kp_bp_marginals(int32_t nk, const float *D, const int32_t *kps, const float *intensity, const int32_t *edges,

@@ -214,8 +214,9 @@ __global__ void mst_sort_kernel(int m, const int *edges, const int *nedges, int 
 }
 
 // ------------------------------------------------------------ tree
-// One CTA: adjacency lists (sorted), breadth-first levels from the root,
-// parents and sorted child lists.  Edges with an index outside [0, n) or
+// One CTA: adjacency lists (sorted), breadth-first levels from the centre of
+// a longest path (found by two sweeps from `root`), parents and sorted child
+// lists; order[0] is the root the messages run to.  Edges with an index outside [0, n) or
 // equal ends are ignored and each vertex is claimed once, so a list that is
 // not a spanning tree cannot write out of bounds (vertices it does not reach
 // are left out of the levels).  Scratch: deg/off [n + 1] each, adj [2 n].
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *
                                                     int *order, int *level_off, int *nlevels, int *parent,
                                                     int *child_off, int *child) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    __shared__ int s_count, s_lvl;
+    __shared__ int s_count, s_lvl, s_far, s_root;
     __shared__ int s_part[1025];
     for (int v = tid; v <= n; v += nt) deg[v] = 0;
     __syncthreads();
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *
         adj[atomicAdd(deg + b, 1)] = a;
     }
     __syncthreads();
-    for (int v = tid; v < n; v += nt) {   // insertion sort of each (short) list
+    for (int v = tid; v < n; v += nt)   // insertion sort of each (short) list
         for (int i = off[v] + 1; i < off[v + 1]; ++i) {
             const int x = adj[i];
             int j = i - 1;
@@ -284,35 +285,55 @@ __global__ void __launch_bounds__(1024) tree_kernel(int n, int root, const int *
             }
             adj[j + 1] = x;
         }
-        parent[v] = -2;   // unvisited
-    }
     __syncthreads();
-    if (tid == 0) {
-        order[0] = root;
-        parent[root] = -1;
-        level_off[0] = 0;
-        level_off[1] = 1;
-        s_count = 1;
-        s_lvl = 0;
-    }
-    __syncthreads();
-    for (int lv = 0; lv < n; ++lv) {   // at most n levels
-        const int b0 = level_off[lv], b1 = level_off[lv + 1];
-        if (b0 == b1) break;
-        for (int i = b0 + tid; i < b1; i += nt) {
-            const int v = order[i];
-            for (int j = off[v]; j < off[v + 1]; ++j) {
-                const int u = adj[j];
-                if (atomicCAS(parent + u, -2, v) == -2) order[atomicAdd(&s_count, 1)] = u;
-            }
-        }
+    // breadth-first levels from r: order[], level_off[], parent[]; returns the
+    // number of levels and (in s_far) the smallest index on the deepest level
+    auto bfs = [&](int r) {
+        for (int v = tid; v < n; v += nt) parent[v] = -2;   // unvisited
         __syncthreads();
         if (tid == 0) {
-            level_off[lv + 2] = s_count;
-            s_lvl = lv + 1;
+            order[0] = r;
+            parent[r] = -1;
+            level_off[0] = 0;
+            level_off[1] = 1;
+            s_count = 1;
+            s_lvl = 0;
         }
         __syncthreads();
+        for (int lv = 0; lv < n; ++lv) {   // at most n levels
+            const int b0 = level_off[lv], b1 = level_off[lv + 1];
+            if (b0 == b1) break;
+            for (int i = b0 + tid; i < b1; i += nt) {
+                const int v = order[i];
+                for (int j = off[v]; j < off[v + 1]; ++j) {
+                    const int u = adj[j];
+                    if (atomicCAS(parent + u, -2, v) == -2) order[atomicAdd(&s_count, 1)] = u;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                level_off[lv + 2] = s_count;
+                s_lvl = lv + 1;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            int far = n;
+            for (int i = level_off[s_lvl - 1]; i < level_off[s_lvl]; ++i) far = min(far, order[i]);
+            s_far = far;
+        }
+        __syncthreads();
+    };
+    // root = centre of a longest path (two sweeps), so the levels are fewest
+    bfs(root);
+    bfs(s_far);
+    if (tid == 0) {
+        int c = s_far;
+        for (int st = 0; st < (s_lvl - 1) / 2; ++st) c = parent[c];
+        s_root = c;
     }
+    __syncthreads();
+    bfs(s_root);
     if (tid == 0) *nlevels = s_lvl;   // levels 0 .. s_lvl - 1 are non-empty
     // child lists: the neighbours claimed by v, in sorted order
     for (int v = tid; v < n; v += nt) {
@@ -460,8 +481,9 @@ __global__ void __launch_bounds__(kBpT) bp_message_kernel(const BpArgs a) {
     cl.sync();   // no CTA leaves while another may still read its planes
 }
 
-// marginal of the root: D + the children's messages
-__global__ void bp_root_kernel(const BpArgs a, int root) {
+// marginal of the root (order[0]): D + the children's messages
+__global__ void bp_root_kernel(const BpArgs a) {
+    const int root = a.order[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kL; i += gridDim.x * blockDim.x) {
         float m = a.D[(long)root * kL + i];
         for (int c = a.child_off[root]; c < a.child_off[root + 1]; ++c) m += a.up[(long)a.child[c] * kL + i];
@@ -639,7 +661,7 @@ cudaError_t launch_cluster(void (*kernel)(const BpArgs), int nverts, const BpArg
 // read back once (one synchronisation) to size the per-level launches.
 int run_bp(int n, const float *D, const int *kps, const float *inten, float sig, float alpha, KpWs &w, float *marg,
            cudaStream_t st) {
-    const int root = 0;
+    const int root = 0;   // start of the sweeps that find the tree's centre
     tree_kernel<<<1, 1024, 0, st>>>(n, root, w.edges, w.deg, w.off, w.adj, w.order, w.level_off, w.nlevels, w.parent,
                                     w.child_off, w.child);
     if (cudaGetLastError() != cudaSuccess) return RG_ECUDA;
@@ -668,7 +690,7 @@ int run_bp(int n, const float *D, const int *kps, const float *inten, float sig,
         if (launch_cluster(bp_message_kernel<false>, lo[lv + 1] - lo[lv], a, st) != cudaSuccess) return RG_ECUDA;
         ++cnt;
     }
-    bp_root_kernel<<<grid_for(kL, 256), 256, 0, st>>>(a, root);
+    bp_root_kernel<<<grid_for(kL, 256), 256, 0, st>>>(a);
     ++cnt;
     for (int lv = 1; lv < nl; ++lv) {
         a.base = lo[lv];
