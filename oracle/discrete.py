@@ -27,6 +27,13 @@ Conventions (images at 1 mm isotropic spacing, arrays [z][y][x], positions
   distance, taken axis by axis (the squared distance is a sum over axes).  A
   zero edge weight (coincident keypoints of the backward search) gives
   lambda = inf: only equal labels are compatible.
+* Sec. II-C1 (Foerstner keypoints): S = G_sigma * (grad F grad F^T) with the
+  central-difference gradient, a separable Gaussian of sigma = 1.4 voxels
+  truncated at radius 5 (weights exp(-i^2 / (2 sigma^2)) normalised to sum 1,
+  nearest-voxel extension), F_D = 1 / trace(S^-1) = det S / (sum of the
+  principal 2x2 minors) (0 where that sum is 0), F_D* the maximum over the
+  6^3 window of offsets -3..2 per axis (nearest-voxel extension); keypoints
+  are the voxels of the mask with F_D = F_D* > 0, in linear index order.
 * Sec. II-C4: the backward search starts at x_k + d*_k with the images'
   roles swapped (M fixed, F moving, weights from M's intensities); the two
   marginals are averaged with the backward displacement mirrored,
@@ -215,3 +222,52 @@ def match(F, Mv, kps, eta=10.0, alpha=0.2, sigma_i=SIGMA_I, symmetric=True):
         Eb = one_way(fM, fF, np.asarray(Mv, np.float32), kps + d1)
         E = 0.5 * (E + Eb[:, mirror_labels()])
     return disp[np.argmin(E, axis=1)], E
+
+
+FORSTNER_SIGMA = 1.4           # mm (= voxels at 1 mm)
+FORSTNER_RADIUS = 5            # Gaussian taps -5..5
+FORSTNER_BOX = 6               # side of the maximum filter's cube
+
+
+def gaussian_weights(sigma=FORSTNER_SIGMA, radius=FORSTNER_RADIUS):
+    i = np.arange(-radius, radius + 1, dtype=np.float64)
+    w = np.exp(-(i * i) / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def forstner_response(F, sigma=FORSTNER_SIGMA, radius=FORSTNER_RADIUS):
+    """F_D = 1 / trace((G_sigma * grad F grad F^T)^-1) per voxel (FP64)."""
+    from scipy.ndimage import correlate1d
+    I = np.pad(np.asarray(F, dtype=np.float64), 1, mode="edge")
+    g = [0.5 * (I[1:-1, 1:-1, 2:] - I[1:-1, 1:-1, :-2]),
+         0.5 * (I[1:-1, 2:, 1:-1] - I[1:-1, :-2, 1:-1]),
+         0.5 * (I[2:, 1:-1, 1:-1] - I[:-2, 1:-1, 1:-1])]
+    w = gaussian_weights(sigma, radius)
+    S = {}
+    for a in range(3):
+        for b in range(a, 3):
+            t = g[a] * g[b]
+            for axis in (2, 1, 0):
+                t = correlate1d(t, w, axis=axis, mode="nearest")
+            S[a, b] = t
+    det = (S[0, 0] * (S[1, 1] * S[2, 2] - S[1, 2] ** 2) - S[0, 1] * (S[0, 1] * S[2, 2] - S[1, 2] * S[0, 2])
+           + S[0, 2] * (S[0, 1] * S[1, 2] - S[1, 1] * S[0, 2]))
+    minors = (S[1, 1] * S[2, 2] - S[1, 2] ** 2) + (S[0, 0] * S[2, 2] - S[0, 2] ** 2) + (S[0, 0] * S[1, 1] - S[0, 1] ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(minors > 0, det / minors, 0.0)
+
+
+def forstner_select(R, mask=None, box=FORSTNER_BOX):
+    """(n, 3) voxel positions (x, y, z) of the window maxima of the response R inside mask."""
+    from scipy.ndimage import maximum_filter
+    Rm = maximum_filter(R, size=box, mode="nearest")     # window offsets -box/2 .. box/2 - 1
+    keep = (R == Rm) & (R > 0)
+    if mask is not None:
+        keep &= np.asarray(mask, dtype=bool)
+    z, y, x = np.nonzero(keep)                           # linear index order
+    return np.stack([x, y, z], axis=1).astype(np.int64)
+
+
+def forstner_keypoints(F, mask=None, sigma=FORSTNER_SIGMA, radius=FORSTNER_RADIUS, box=FORSTNER_BOX):
+    """Sec. II-C1: keypoints of the fixed image F inside mask."""
+    return forstner_select(forstner_response(F, sigma, radius), mask, box)

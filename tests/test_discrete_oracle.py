@@ -162,3 +162,46 @@ def test_symmetric_match_recovers_a_shift():
     d1, E1 = Dq.match(F, Mv, kps, symmetric=False)
     d2, E2 = Dq.match(F, Mv, kps, symmetric=True)
     assert np.all(d1 == s) and np.all(d2 == s)
+
+
+def test_forstner_response_against_direct_inverse():
+    """F_D = 1 / trace(S^-1), S by an explicit 3-D convolution with the outer
+    product of the Gaussian weights, inverted with numpy."""
+    img = _smooth_noise((14, 14, 14), 8, sigma=1.5)
+    Rq = Dq.forstner_response(img)
+    I = np.pad(img.astype(np.float64), 1, mode="edge")
+    g = np.stack([0.5 * (I[1:-1, 1:-1, 2:] - I[1:-1, 1:-1, :-2]), 0.5 * (I[1:-1, 2:, 1:-1] - I[1:-1, :-2, 1:-1]),
+                  0.5 * (I[2:, 1:-1, 1:-1] - I[:-2, 1:-1, 1:-1])], axis=-1)
+    w = Dq.gaussian_weights()
+    K = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    r = len(w) // 2
+    P = np.pad(g[..., :, None] * g[..., None, :], ((r, r), (r, r), (r, r), (0, 0), (0, 0)), mode="edge")
+    for z, y, x in [(7, 7, 7), (5, 9, 6), (8, 4, 10)]:
+        S = np.einsum("abc,abcij->ij", K, P[z:z + 2 * r + 1, y:y + 2 * r + 1, x:x + 2 * r + 1])
+        assert Rq[z, y, x] == pytest.approx(1.0 / np.trace(np.linalg.inv(S)), rel=1e-10)
+    assert Dq.forstner_response(2.0 * img) == pytest.approx(4.0 * Rq, rel=1e-12)   # exact scaling by 2
+
+
+def test_forstner_zero_for_rank_one_structure():
+    z, y, x = np.meshgrid(np.arange(24), np.arange(24), np.arange(24), indexing="ij")
+    img = (5.0 * x - 2.0 * y + 3.0 * z).astype(np.float32)      # one gradient direction everywhere
+    R = Dq.forstner_response(img)
+    assert np.abs(R[8:16, 8:16, 8:16]).max() < 1e-9 * 38.0
+
+
+def test_forstner_selection_against_brute_force():
+    rng = np.random.default_rng(9)
+    R = rng.random((9, 10, 11))
+    R[2:4, 2:4, 2:4] = 0.0
+    mask = rng.random(R.shape) < 0.8
+    k = Dq.forstner_select(R, mask)
+    want = []
+    nz, ny, nx = R.shape
+    for zz in range(nz):
+        for yy in range(ny):
+            for xx in range(nx):
+                win = [R[min(max(a, 0), nz - 1), min(max(b, 0), ny - 1), min(max(c, 0), nx - 1)]
+                       for a in range(zz - 3, zz + 3) for b in range(yy - 3, yy + 3) for c in range(xx - 3, xx + 3)]
+                if mask[zz, yy, xx] and R[zz, yy, xx] > 0 and R[zz, yy, xx] == max(win):
+                    want.append((xx, yy, zz))
+    assert [tuple(map(int, r)) for r in k] == want
