@@ -270,14 +270,25 @@ def discrete_rates(ph, kp, dev, sm_mhz, reps=3):
     flops = nk * discrete.LABELS * 64 * 10.0          # 4-term dot + squared accumulate per patch point
     peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     ach = flops / (t[1] / 1e3) / 1e12
-    dd = disp.cpu().numpy()
+    # keypoints of Sec. II-C1 (Foerstner, FP64) inside the lungs of the same image
     from paper_1807_00467_gb300 import phantom
+    lm = torch.from_numpy(phantom.lung_mask(ph.n, ph.h)).to(dev)
+    discrete.forstner(F, lm, stream=s)
+    ev[0].record(s)
+    kf = discrete.forstner(F, lm, stream=s)
+    ev[1].record(s)
+    s.synchronize()
+    t_forstner = ev[0].elapsed_time(ev[1])
+    dd = disp.cpu().numpy()
     u_true = phantom.rbf_motion((kp + 0.5).astype(np.float64), ph.amps, ph.centres)
     err = np.linalg.norm(dd - u_true, axis=1)
     return {"workload": f"{DISC_SHAPE[0]}x{DISC_SHAPE[1]}x{DISC_SHAPE[2]} at 1 mm, {nk} keypoints, 35937 labels, "
                         "64-voxel patches, symmetric", "keypoints": nk, "ms_per_match": ms,
             "keypoints_per_s": nk / (ms / 1e3), "gpu_launches_per_match": launches,
             "stages_ms_forward": {"features_x2": t[0], "cost_volume": t[1], "mst": t[3], "bp_two_pass": t[4]},
+            "foerstner": {"ms": t_forstner, "keypoints_in_lungs": int(kf.shape[0]),
+                          "note": "Sec. II-C1 detector, FP64 response; the match above uses the phantom's "
+                                  "vessel-centreline keypoints"},
             "roofline": {"bound": "alu", "kernel": "cost_volume", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x sampled SM clock",
                          "flop_per_launch": flops},

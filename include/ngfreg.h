@@ -321,6 +321,19 @@ int kp_match(const int32_t *n, const float *F, const float *M, int32_t nk, const
              int32_t symmetric, int32_t *disp, float *marginals, void *workspace, size_t ws_bytes,
              void *cuda_stream);
 
+/* Keypoints of Sec. II-C1 (Foerstner operator) in the fixed image F:
+ * F_D = 1 / trace((G_sigma * grad F grad F^T)^-1) in FP64 (central
+ * differences, separable Gaussian with taps -5..5, weights exp(-i^2 /
+ * (2 sigma^2)) normalised; nearest voxel outside the volume), F_D* its
+ * maximum over the 6^3 window of offsets -3..2 per axis, keypoints = voxels
+ * with mask != 0 (mask: uint8 [N], or NULL for all) and F_D = F_D* > 0, in
+ * linear index order.  kps: int32 [max_kp][3] (x, y, z); *count (host) gets
+ * the number found (only the first max_kp are written).  response: NULL or
+ * double [N] for F_D.  Synchronises the stream. */
+int kp_forstner_workspace_size(const int32_t *n, size_t *bytes);
+int kp_forstner(const int32_t *n, const float *F, const uint8_t *mask, double sigma, int32_t max_kp, int32_t *kps,
+                int32_t *count, double *response, void *workspace, size_t ws_bytes, void *cuda_stream);
+
 /* Kernels launched by the kp_* entry points in this process so far. */
 int64_t kp_launch_count(void);
 

@@ -44,6 +44,7 @@ EXPORTS = [
     "rg_restrict_image", "rg_prolong_grid", "rg_last_error", "rg_version", "rg_profile", "rg_profile_read",
     "rg_launch_count", "ngf_distance_noalloc", "rg_set_tile", "rg_autotune", "kp_workspace_size", "kp_scratch_size",
     "kp_ngf_features", "kp_cost_volume", "kp_mst", "kp_bp_marginals", "kp_match", "kp_launch_count",
+    "kp_forstner_workspace_size", "kp_forstner",
 ]
 
 _lib = None
@@ -81,7 +82,9 @@ def load():
         "kp_mst": ([i32, vp, vp, C.c_double, vp, vp, sz, vp], C.c_int),
         "kp_bp_marginals": ([i32, vp, vp, vp, vp, C.c_double, C.c_double, vp, vp, sz, vp], C.c_int),
         "kp_match": ([C.POINTER(i32), vp, vp, i32, vp, vp, i32, vp, vp, vp, sz, vp], C.c_int),
-        "kp_launch_count": ([], C.c_longlong),
+        "kp_launch_count": ([], C.c_int64),
+        "kp_forstner_workspace_size": ([C.POINTER(i32), C.POINTER(sz)], C.c_int),
+        "kp_forstner": ([C.POINTER(i32), vp, vp, C.c_double, i32, vp, C.POINTER(i32), vp, vp, sz, vp], C.c_int),
         "rg_set_images": ([vp, vp, vp], C.c_int),
         "rg_set_keypoints": ([vp, i32, fp, fp], C.c_int),
         "ngf_objective": ([vp, fp, dp], C.c_int),

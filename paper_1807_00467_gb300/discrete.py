@@ -81,6 +81,26 @@ def bp_marginals(D, kps, intensity, edges, alpha=0.2, sigma_i=150.0, stream=None
     return E
 
 
+def forstner(F, mask=None, sigma=1.4, max_kp=100000, response=False, stream=None):
+    """Sec. II-C1: (n, 3) int32 keypoints (x, y, z) of the fixed image F
+    inside mask (uint8/bool, same shape) in linear index order; with
+    response=True also the FP64 distinctiveness F_D."""
+    F = F.contiguous().float()
+    L = _lib.load()
+    b = C.c_size_t()
+    _ok(L.kp_forstner_workspace_size(_dims(F), C.byref(b)), "kp_forstner_workspace_size")
+    ws = torch.empty(b.value + 256, dtype=torch.uint8, device=F.device)
+    wp = (ws.data_ptr() + 255) & ~255
+    kps = torch.empty((max_kp, 3), dtype=torch.int32, device=F.device)
+    m = None if mask is None else mask.contiguous().to(torch.uint8)
+    R = torch.empty(F.shape, dtype=torch.float64, device=F.device) if response else None
+    cnt = C.c_int32()
+    _ok(L.kp_forstner(_dims(F), _ptr(F), _ptr(m), float(sigma), int(max_kp), _ptr(kps), C.byref(cnt), _ptr(R),
+                      C.c_void_p(wp), b.value, _stream_ptr(stream)), "kp_forstner")
+    k = kps[: min(cnt.value, max_kp)]
+    return (k, R) if response else k
+
+
 class Matcher:
     """kp_match with a workspace kept for one image shape and keypoint count."""
 

@@ -331,6 +331,15 @@ def _make_phantom(n, h, seed, motion, amp_range, n_vessels, n_keypoints, kp_sigm
                    amps=amps, centres=centres, kp_x=kp_x, kp_y=kp_y, meta=meta)
 
 
+def lung_mask(n, h):
+    """uint8 [nz][ny][nx]: 1 inside the two lung ellipsoids of the recipe."""
+    fov = np.asarray(n, dtype=np.float64) * np.asarray(h, dtype=np.float64)
+    centres, semi = _lung_geometry(fov)
+    zc, yc, xc = np.meshgrid(_axis_centres(n[2], h[2]), _axis_centres(n[1], h[1]), _axis_centres(n[0], h[0]),
+                             indexing="ij")
+    return (_ellipsoid(xc, yc, zc, centres[0], semi) | _ellipsoid(xc, yc, zc, centres[1], semi)).astype(np.uint8)
+
+
 def _pair_job(job):
     n, h, seed = job
     ph = make_phantom(n, h, seed, motion="large")

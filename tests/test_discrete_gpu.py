@@ -131,3 +131,26 @@ def test_symmetric_match_against_oracle():
     np.testing.assert_array_equal(disp, Dq.label_displacements()[a_s])
     print(f"match: {nk} keypoints, |d| mean {np.abs(disp).sum(1).mean():.1f} mm, "
           f"agree with the oracle on {np.mean(a_s == a_so) * 100:.0f}% of labels")
+
+
+def test_forstner_keypoints_match_oracle():
+    """Sec. II-C1 in FP64 on both sides: response within 1e-12 relative;
+    keypoint sets equal except where the oracle's F_D and its window maximum
+    are within 1e-10 (a tie that the order of the sums may decide)."""
+    from scipy.ndimage import maximum_filter
+    from paper_1807_00467_gb300 import discrete
+    R, T, kp = _pair()
+    mask = phantom.lung_mask((96, 96, 80), (1.0, 1.0, 1.0))
+    k, resp = discrete.forstner(_dev(R), _dev(mask), response=True)
+    k, resp = k.cpu().numpy(), resp.cpu().numpy()
+    Ro = Dq.forstner_response(R)
+    assert np.abs(resp - Ro).max() <= 1e-12 * np.abs(Ro).max()
+    ko = Dq.forstner_select(Ro, mask)
+    Rm = maximum_filter(Ro, size=6, mode="nearest")
+    a, b = {tuple(r) for r in k.tolist()}, {tuple(r) for r in ko.tolist()}
+    for x, y, z in a ^ b:
+        assert abs(Ro[z, y, x] - Rm[z, y, x]) <= 1e-10 * Rm[z, y, x]
+    lin = k[:, 2] * 96 * 96 + k[:, 1] * 96 + k[:, 0]
+    assert np.all(np.diff(lin) > 0)                     # linear index order
+    print(f"foerstner: {len(k)} keypoints (oracle {len(ko)}), {len(a ^ b)} near-tie differences")
+    assert len(k) > 50
