@@ -183,8 +183,8 @@ def bp_marginals(D, edges, W, alpha, n_steps=N_STEPS, step=LABEL_STEP, root=0):
     by two passes of min-sum messages (Eq. 4) on the tree."""
     n = D.shape[0]
     order, parent, children = tree_order(n, edges, root)
-    with np.errstate(divide="ignore"):
-        lam = {k: float(alpha) / float(W[k, parent[k]]) for k in range(n) if parent[k] >= 0}
+    with np.errstate(divide="ignore"):   # a zero weight gives lambda = inf
+        lam = {k: float(np.float64(alpha) / np.float64(W[k, parent[k]])) for k in range(n) if parent[k] >= 0}
     up = {}
     for k in reversed(order):
         if parent[k] < 0:

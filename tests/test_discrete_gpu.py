@@ -154,3 +154,45 @@ def test_forstner_keypoints_match_oracle():
     assert np.all(np.diff(lin) > 0)                     # linear index order
     print(f"foerstner: {len(k)} keypoints (oracle {len(ko)}), {len(a ^ b)} near-tie differences")
     assert len(k) > 50
+
+
+def test_match_entry_points_agree_and_edge_cases():
+    """kp_match without refinement = argmin of kp_bp_marginals over
+    kp_cost_volume and kp_mst (same kernels, same bits); duplicate keypoints
+    (zero edge weight, lambda = inf) and keypoints whose windows are clamped on
+    every side, against the oracle."""
+    import torch
+    from paper_1807_00467_gb300 import discrete
+    R, T, kp = _pair()
+    kps = np.concatenate([kp[::50][:6], kp[::50][:2], [[0, 0, 0], [95, 95, 79]]])   # two duplicates, two corners
+    nk = len(kps)
+    K = _dev(kps).int()
+    m = discrete.Matcher(R.shape, nk, eta=10.0, alpha=0.2)
+    disp, E = m.match(_dev(R), _dev(T), K, symmetric=False, marginals=True)
+    fF, fM = discrete.features(_dev(R)), discrete.features(_dev(T))
+    inten = _dev(R)[K[:, 2].long(), K[:, 1].long(), K[:, 0].long()]
+    D = discrete.cost_volume(fF, fM, K)
+    e = discrete.mst(K, inten)
+    E2 = discrete.bp_marginals(D, K, inten, e, alpha=0.2)
+    assert torch.equal(E, E2)
+    E = E.cpu().numpy()
+    lab = Dq.label_displacements()
+    np.testing.assert_array_equal(disp.cpu().numpy(), lab[np.argmin(E, axis=1)])
+    W = Dq.edge_weights(kps, R[kps[:, 2], kps[:, 1], kps[:, 0]])
+    eo = Dq.mst(W)
+    np.testing.assert_array_equal(e.cpu().numpy(), eo)
+    Eo = Dq.bp_marginals(Dq.cost_volume(Dq.ngf_features(R, 10.0), Dq.ngf_features(T, 10.0), kps), eo, W, 0.2)
+    tol = TOL_E * np.abs(Eo).max(axis=1)
+    assert np.all(np.abs(E - Eo).max(axis=1) <= tol)
+    a_g, _, _ = _check_labels(E, Eo, tol)
+    assert a_g[6] == a_g[0] and a_g[7] == a_g[1]          # duplicates share their label (lambda = inf)
+
+
+def test_forstner_without_mask():
+    from paper_1807_00467_gb300 import discrete
+    R, T, kp = _pair()
+    k = discrete.forstner(_dev(R)).cpu().numpy()
+    ko = Dq.forstner_keypoints(R)
+    assert len(k) > len(kp) // 4
+    a, b = {tuple(r) for r in k.tolist()}, {tuple(r) for r in ko.tolist()}
+    assert len(a ^ b) <= max(2, len(b) // 1000)

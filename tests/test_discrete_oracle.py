@@ -205,3 +205,31 @@ def test_forstner_selection_against_brute_force():
                 if mask[zz, yy, xx] and R[zz, yy, xx] > 0 and R[zz, yy, xx] == max(win):
                     want.append((xx, yy, zz))
     assert [tuple(map(int, r)) for r in k] == want
+
+
+def test_bp_exact_with_a_duplicate_keypoint():
+    """A keypoint listed twice: zero edge weight, lambda = inf, so only equal
+    labels of the two copies are compatible; brute-force min-marginals over
+    all 27^4 labelings with that constraint."""
+    rng = np.random.default_rng(11)
+    n, L = 4, 27
+    kps = np.array([[0, 0, 0], [3, 0, 0], [0, 0, 0], [0, 4, 2]])
+    inten = np.array([-700.0, -650.0, -700.0, -820.0], np.float32)
+    W = Dq.edge_weights(kps, inten)
+    e = Dq.mst(W)
+    assert W[0, 2] == 0.0 and [0, 2] in e.tolist()
+    D = rng.random((n, L))
+    Mbp = Dq.bp_marginals(D, e, W, 0.3, n_steps=3)
+    d = Dq.label_displacements(3)
+    sq = ((d[:, None, :] - d[None, :, :]) ** 2).sum(axis=2)
+    A = np.array(list(itertools.product(range(L), repeat=n)))
+    E = D[np.arange(n)[None, :], A].sum(axis=1)
+    for a, b in e:
+        if W[a, b] == 0.0:
+            E = np.where(A[:, a] == A[:, b], E, np.inf)
+        else:
+            E = E + 0.3 / float(W[a, b]) * sq[A[:, a], A[:, b]]
+    for k in range(n):
+        mk = np.full(L, np.inf)
+        np.minimum.at(mk, A[:, k], E)
+        assert np.allclose(Mbp[k], mk, rtol=1e-12, atol=1e-12)

@@ -104,3 +104,19 @@ def test_pyramid_graph_drive_matches_host():
     assert res["graph"][0] == res["host"][0] == 0
     np.testing.assert_array_equal(res["graph"][1], res["host"][1])
     np.testing.assert_array_equal(res["graph"][2], res["host"][2])
+
+
+def test_graph_drive_beyond_the_device_report_falls_back_to_host():
+    """More iterations than the device keeps report rows for (256): the
+    host-driven loop runs instead, with the same bits."""
+    import torch
+    ph = get_phantom("tiny", seed=0)
+    out = {}
+    for drive in ("host", "graph"):
+        ctx = gpu_context(ph, TINY_M, gamma=0.001)
+        u = torch.zeros((3,) + TINY_M[::-1], device="cuda")
+        code, rep = ctx.gn_solve(u, gn_iters=260, pcg_iters=2, ls_max=2, drive=drive)
+        out[drive] = (code, rep, u.cpu().numpy())
+    assert out["host"][0] == out["graph"][0]
+    np.testing.assert_array_equal(out["host"][1], out["graph"][1])
+    np.testing.assert_array_equal(out["host"][2], out["graph"][2])
