@@ -666,6 +666,14 @@ def batch_rates(params, dev, n_pairs=24, runs=(("host", 1), ("host", 4), ("graph
         first = first if first is not None else us
         res["runs"][f"{drive}_x{w}"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
                                         "gn_matvec_per_s": mv / sec, "same_bits_as_first": bool(same)}
+    # one CUDA graph per level advancing every pair's Gauss-Newton iteration
+    # (register_pyramid_batch), no host threads; same bits as the graph drive
+    batch.register_batch_graph(pairs, params, **sched)
+    us, reps, sec = batch.register_batch_graph(pairs, params, **sched)
+    mv = int(sum(r[..., 6].sum() for r in reps))
+    res["runs"]["batched_graph"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
+                                    "gn_matvec_per_s": mv / sec,
+                                    "same_bits_as_first": bool(all(torch.equal(a, b) for a, b in zip(first, us)))}
     # tile shapes picked per level geometry by the autotuner (timed on one
     # stream in an untimed pass and cached per process), graph drive, 8 streams
     batch.register_batch(pairs, params, workers=1, drive="graph", autotune=True, **sched)

@@ -213,6 +213,23 @@ int register_pyramid(const rg_image_geom *img, const void *R_dev, const void *T_
                      int32_t nk, const float *kx_dev, const float *ky_dev, float *u_inout_dev,
                      double *report_host, void *workspace_dev, size_t ws_bytes, void *cuda_stream);
 
+/* Many pairs through register_pyramid's schedule in lockstep (batching; the
+ * paper has no counterpart).  Per pair p: img[p], R[p], T[p] (dtype shared),
+ * fin[p], u_inout[p] and a workspace ws[p] of rg_pyramid_workspace_size(...,
+ * nk_max = 0, ...) bytes (ws_bytes[p]); params and sched are shared, no
+ * keypoints; 1 <= gn_iters <= 256 and sched->flags is ignored.  At each level
+ * one CUDA graph holds every pair's Gauss-Newton iteration (line search
+ * decided on the device) as a parallel branch and is replayed gn_iters times:
+ * one graph launch advances all pairs.  Per pair the results have the bits of
+ * register_pyramid with RG_SCHED_GRAPH.  report_host: double
+ * [npairs][levels][gn_iters][8] or NULL.  Returns the first pair's error, if
+ * any, after the level where it arose.  Synchronises the stream once per
+ * level. */
+int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, const void *const *R, const void *const *T,
+                           rg_dtype dtype, const rg_grid_geom *finest, const rg_params *params,
+                           const rg_schedule *sched, float *const *u_inout, double *report_host,
+                           void *const *workspace_dev, const size_t *ws_bytes, void *cuda_stream);
+
 /* 2x2x2 box restriction of an image (float32 or half as dtype), n even. */
 int rg_restrict_image(const int32_t *n, rg_dtype dtype, const void *in_dev, void *out_dev, void *cuda_stream);
 /* Dyadic trilinear prolongation of a grid field from mc nodes to mf = 2 mc - 1. */

@@ -44,7 +44,7 @@ EXPORTS = [
     "rg_restrict_image", "rg_prolong_grid", "rg_last_error", "rg_version", "rg_profile", "rg_profile_read",
     "rg_launch_count", "ngf_distance_noalloc", "rg_set_tile", "rg_autotune", "kp_workspace_size", "kp_scratch_size",
     "kp_ngf_features", "kp_cost_volume", "kp_mst", "kp_bp_marginals", "kp_match", "kp_launch_count",
-    "kp_forstner_workspace_size", "kp_forstner",
+    "kp_forstner_workspace_size", "kp_forstner", "register_pyramid_batch",
 ]
 
 _lib = None
@@ -84,6 +84,7 @@ def load():
         "kp_match": ([C.POINTER(i32), vp, vp, i32, vp, vp, i32, vp, vp, vp, sz, vp], C.c_int),
         "kp_launch_count": ([], C.c_int64),
         "kp_forstner_workspace_size": ([C.POINTER(i32), C.POINTER(sz)], C.c_int),
+        "register_pyramid_batch": ([i32, IG, vp, vp, C.c_int, GG, PP, SP, vp, fp, vp, C.POINTER(sz), vp], C.c_int),
         "kp_forstner": ([C.POINTER(i32), vp, vp, C.c_double, i32, vp, C.POINTER(i32), vp, vp, sz, vp], C.c_int),
         "rg_set_images": ([vp, vp, vp], C.c_int),
         "rg_set_keypoints": ([vp, i32, fp, fp], C.c_int),

@@ -27,7 +27,7 @@ import torch
 
 from . import api
 
-__all__ = ["batch_shapes", "crop_pairs", "register_batch"]
+__all__ = ["batch_shapes", "crop_pairs", "register_batch", "register_batch_graph"]
 
 def batch_shapes(n_pairs=24, seed=0, lo=(96, 96, 64), hi=(512, 512, 128), q=16):
     """[(nx, ny, nz)] of n_pairs problems between the shapes lo and hi."""
@@ -54,6 +54,53 @@ def crop_pairs(R, T, h, shapes, grid_step=4):
         m = tuple(n[a] // grid_step + 1 for a in range(3))
         out.append((R[sl].contiguous(), T[sl].contiguous(), tuple(h), m))
     return out
+
+
+def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, stream=None):
+    """All pairs (R, T, h, m) in lockstep through the multilevel schedule with
+    one CUDA graph per level advancing every pair's Gauss-Newton iteration
+    (register_pyramid_batch); no host threads.  Returns (displacements,
+    reports, seconds) like register_batch."""
+    import ctypes as C
+
+    from . import _lib
+    L = _lib.load()
+    n = len(pairs)
+    dev = pairs[0][0].device
+    dtype = api._dtype_code(pairs[0][0])
+    igs = (_lib.ImageGeom * n)(*[api._img_geom(R.shape, h) for R, T, h, m in pairs])
+    ggs = (_lib.GridGeom * n)(*[api._grid_geom(m) for R, T, h, m in pairs])
+    us = [torch.zeros((3, m[2], m[1], m[0]), dtype=torch.float32, device=dev) for R, T, h, m in pairs]
+    wss, wps, wbs = [], [], []
+    for i in range(n):
+        b = C.c_size_t()
+        api._check(L.rg_pyramid_workspace_size(C.byref(igs[i]), C.byref(ggs[i]), dtype, levels, 0, pcg_iters,
+                                               C.byref(b)), name="rg_pyramid_workspace_size")
+        w = torch.empty(b.value + 256, dtype=torch.uint8, device=dev)
+        wss.append(w)
+        wps.append((w.data_ptr() + 255) & ~255)
+        wbs.append(b.value)
+    keep = []
+
+    def ptrs(ts):   # a C array of device pointers, passed as void *
+        arr = (C.c_void_p * n)(*[t.data_ptr() for t in ts])
+        keep.append(arr)
+        return C.cast(arr, C.c_void_p)
+    rep = np.zeros((n, levels, gn_iters, 8))
+    sched = api.make_schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c)
+    wsa = (C.c_void_p * n)(*wps)
+    wsp = C.cast(wsa, C.c_void_p)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    code = L.register_pyramid_batch(n, igs, ptrs([p[0] for p in pairs]), ptrs([p[1] for p in pairs]), dtype, ggs,
+                                    C.byref(params), C.byref(sched), ptrs(us),
+                                    rep.ctypes.data_as(C.POINTER(C.c_double)), wsp, (C.c_size_t * n)(*wbs),
+                                    api._stream_ptr(stream))
+    torch.cuda.synchronize(dev)
+    seconds = time.perf_counter() - t0
+    if code < 0:
+        raise api.NgfError(code, "register_pyramid_batch")
+    return us, list(rep), seconds
 
 
 def register_batch(pairs, params, levels, gn_iters, pcg_iters, workers=4, ls_max=10, armijo_c=1e-4, drive="host",

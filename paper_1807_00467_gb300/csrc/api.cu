@@ -882,21 +882,26 @@ static int gn_run_device(rg_ctx *c, float *u, const rg_schedule *s, bool graph) 
 
 // Device-driven schedule on the context's private stream, ordered after and
 // before the caller's stream by events; one host synchronisation at the end.
-static int gn_solve_device(rg_ctx *c, float *u, const rg_schedule *s, double *report, bool graph) {
-    if (!c->gst) {
-        cudaStream_t gs = nullptr;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
-        if (cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
-            if (e0) cudaEventDestroy(e0);
-            cudaStreamDestroy(gs);
-            return set_err(c, RG_ECUDA, "gn_solve: event creation failed");
-        }
-        c->gst = gs;
-        c->gev[0] = e0;
-        c->gev[1] = e1;
+static int ensure_private_stream(rg_ctx *c) {
+    if (c->gst) return RG_OK;
+    cudaStream_t gs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+    if (cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaStreamDestroy(gs);
+        return set_err(c, RG_ECUDA, "gn_solve: event creation failed");
     }
+    c->gst = gs;
+    c->gev[0] = e0;
+    c->gev[1] = e1;
+    return RG_OK;
+}
+
+static int gn_solve_device(rg_ctx *c, float *u, const rg_schedule *s, double *report, bool graph) {
+    int est;
+    if ((est = ensure_private_stream(c))) return est;
     const cudaStream_t user = c->st;
     CK(cudaEventRecord(c->gev[0], user));
     CK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
@@ -1177,6 +1182,224 @@ extern "C" int register_pyramid(const rg_image_geom *img, const void *R, const v
     CK(cudaMemcpyAsync(u_inout, ul[0], sizeof(float) * 3 * (long)fin->m[0] * fin->m[1] * fin->m[2],
                        cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
+    return status;
+}
+
+// Many pairs through the multilevel schedule in lockstep: at each level one
+// CUDA graph holds every pair's device-driven Gauss-Newton iteration as a
+// parallel branch (the context's private stream, forked from and joined to the
+// caller's stream), and is replayed gn_iters times, so one graph launch
+// advances all pairs.  Per pair the same kernels run in the same order as in
+// register_pyramid with RG_SCHED_GRAPH.
+extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, const void *const *R,
+                                      const void *const *T, rg_dtype dtype, const rg_grid_geom *fin,
+                                      const rg_params *params, const rg_schedule *s, float *const *u_inout,
+                                      double *report, void *const *ws, const size_t *ws_bytes, void *stream) {
+    if (npairs < 1 || !img || !R || !T || !fin || !params || !s || !u_inout || !ws || !ws_bytes) return RG_EINVAL;
+    if (s->gn_iters < 1 || s->gn_iters > kGnRows || s->levels < 1 || s->levels > 8 || s->ls_max < 0)
+        return RG_EINVAL;
+    const int levels = s->levels, Lc = levels - 1;
+    rg_ctx *c = nullptr;   // for CK / LAUNCH in this scope
+    const size_t es = dtype == RG_F16 ? 2 : 4;
+    struct Pair {
+        char *base;
+        size_t off;
+        const void *Rl[8], *Tl[8];
+        float *ul[8];
+        rg_image_geom il[8];
+        rg_grid_geom gl[8];
+        rg_params P;
+        rg_ctx *cl;
+        void *take(size_t b) {
+            off = (off + 255) & ~(size_t)255;
+            char *p = base + off;
+            off += b;
+            return p;
+        }
+    };
+    std::vector<Pair> ps(npairs);
+    for (int p = 0; p < npairs; ++p) {
+        size_t need;
+        if (!R[p] || !T[p] || !u_inout[p] || !ws[p] || ((uintptr_t)ws[p] & 255) ||
+            rg_pyramid_workspace_size(&img[p], &fin[p], dtype, levels, 0, s->pcg_iters, &need) != RG_OK ||
+            ws_bytes[p] < need)
+            return RG_EINVAL;
+    }
+    // all work on a private stream (a capture cannot run on the legacy default
+    // stream), ordered after and, at the end, before the caller's stream
+    const cudaStream_t user = (cudaStream_t)stream;
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, edge = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&edge, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(edge, user) != cudaSuccess || cudaStreamWaitEvent(st, edge, 0) != cudaSuccess) {
+        if (fork) cudaEventDestroy(fork);
+        if (edge) cudaEventDestroy(edge);
+        cudaStreamDestroy(st);
+        return RG_ECUDA;
+    }
+    std::vector<cudaEvent_t> join(npairs, nullptr);
+    for (auto &e : join)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
+    auto release = [&]() {
+        for (auto &q : ps)
+            if (q.cl) {
+                rg_ctx_destroy(q.cl);
+                q.cl = nullptr;
+            }
+        for (auto e : join)
+            if (e) cudaEventDestroy(e);
+        cudaEventRecord(edge, st);   // the caller's stream continues after the batch
+        cudaStreamWaitEvent(user, edge, 0);
+        cudaStreamSynchronize(st);
+        cudaEventDestroy(fork);
+        cudaEventDestroy(edge);
+        cudaStreamDestroy(st);
+    };
+    for (auto e : join)
+        if (!e) {
+            release();
+            return RG_ECUDA;
+        }
+    int status = RG_OK;
+    for (int p = 0; p < npairs && status == RG_OK; ++p) {
+        Pair &q = ps[p];
+        q.base = (char *)ws[p];
+        q.off = 0;
+        q.P = *params;
+        q.cl = nullptr;
+        q.Rl[0] = R[p];
+        q.Tl[0] = T[p];
+        for (int l = 0; l < levels; ++l) {
+            level_geom(&img[p], &fin[p], l, q.il[l], q.gl[l]);
+            const long N = (long)q.il[l].n[0] * q.il[l].n[1] * q.il[l].n[2];
+            const long M = (long)q.gl[l].m[0] * q.gl[l].m[1] * q.gl[l].m[2];
+            if (l > 0) {
+                void *r = q.take(N * es), *t = q.take(N * es);
+                if (launch_restrict(q.il[l - 1].n, dtype == RG_F16, q.Rl[l - 1], r, st) != cudaSuccess ||
+                    launch_restrict(q.il[l - 1].n, dtype == RG_F16, q.Tl[l - 1], t, st) != cudaSuccess)
+                    status = RG_ECUDA;
+                g_launches.fetch_add(2, std::memory_order_relaxed);
+                q.Rl[l] = r;
+                q.Tl[l] = t;
+            }
+            q.ul[l] = (float *)q.take(3 * M * sizeof(float));
+        }
+        const long Mf = (long)fin[p].m[0] * fin[p].m[1] * fin[p].m[2];
+        if (Lc == 0) {
+            if (cudaMemcpyAsync(q.ul[0], u_inout[p], sizeof(float) * 3 * Mf, cudaMemcpyDeviceToDevice, st) !=
+                cudaSuccess)
+                status = RG_ECUDA;
+        } else {
+            if (launch_inject_grid(fin[p].m, 1 << Lc, u_inout[p], q.gl[Lc].m, q.ul[Lc], st) != cudaSuccess)
+                status = RG_ECUDA;
+            g_launches.fetch_add(1, std::memory_order_relaxed);
+        }
+    }
+    std::vector<double> rows(8 * (size_t)s->gn_iters);
+    for (int l = Lc; l >= 0 && status == RG_OK; --l) {
+        // this level's contexts (delta adapted on the host at the coarsest level)
+        for (int p = 0; p < npairs && status == RG_OK; ++p) {
+            Pair &q = ps[p];
+            size_t w;
+            rg_workspace_size(&q.il[l], &q.gl[l], dtype, 0, s->pcg_iters, &w);
+            void *wl = q.take(w);
+            status = rg_ctx_create(&q.cl, &q.il[l], &q.gl[l], dtype, &q.P, 0, s->pcg_iters, wl, w, (void *)st);
+            if (status) break;
+            rg_set_images(q.cl, q.Rl[l], q.Tl[l]);
+            if (q.P.delta_adaptive && l == Lc) status = set_delta_adaptive(q.cl, q.ul[l]);
+            if (!status) status = ensure_private_stream(q.cl);
+            if (!status && cudaMemsetAsync(q.cl->tma_err, 0, 2 * sizeof(int), st) != cudaSuccess) status = RG_ECUDA;
+            if (!status && cudaMemsetAsync(q.cl->gn, 0, sizeof(GnState), st) != cudaSuccess) status = RG_ECUDA;
+            q.cl->err_zeroed = true;
+        }
+        if (status) break;
+        // one graph: every pair's iteration as a branch forked from st
+        long long counted = 0;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            status = RG_ECUDA;
+            break;
+        }
+        int cst = cudaEventRecord(fork, st) == cudaSuccess ? RG_OK : RG_ECUDA;
+        for (int p = 0; p < npairs && cst == RG_OK; ++p) {
+            rg_ctx *cl = ps[p].cl;
+            if (cudaStreamWaitEvent(cl->gst, fork, 0) != cudaSuccess) {
+                cst = RG_ECUDA;
+                break;
+            }
+            const long long l0 = cl->launches;
+            {
+                StreamSwap sw(cl, cl->gst);
+                cst = gn_iteration_device(cl, ps[p].ul[l], s);
+            }
+            counted += cl->launches - l0;
+            cl->launches = l0;
+            if (!cst && (cudaEventRecord(join[p], cl->gst) != cudaSuccess ||
+                         cudaStreamWaitEvent(st, join[p], 0) != cudaSuccess))
+                cst = RG_ECUDA;
+        }
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        g_launches.fetch_sub(counted, std::memory_order_relaxed);   // captured, not run
+        if (cst || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            status = cst ? cst : RG_ECUDA;
+            break;
+        }
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            status = RG_ECUDA;
+            break;
+        }
+        for (int it = 0; it < s->gn_iters && status == RG_OK; ++it) {
+            if (cudaGraphLaunch(ge, st) != cudaSuccess) status = RG_ECUDA;
+            else g_launches.fetch_add(counted, std::memory_order_relaxed);
+        }
+        cudaGraphExecDestroy(ge);
+        if (status) break;
+        // outcomes: one synchronisation for all pairs
+        std::vector<GnState> hs(npairs);
+        std::vector<double> rep((size_t)npairs * rows.size());
+        std::vector<int> err(npairs, 0);
+        for (int p = 0; p < npairs && status == RG_OK; ++p) {
+            rg_ctx *cl = ps[p].cl;
+            if (cudaMemcpyAsync(&hs[p], cl->gn, sizeof(GnState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaMemcpyAsync(rep.data() + (size_t)p * rows.size(), cl->gnrep, sizeof(double) * rows.size(),
+                                cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaMemcpyAsync(&err[p], cl->tma_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                status = RG_ECUDA;
+        }
+        if (!status && cudaStreamSynchronize(st) != cudaSuccess) status = RG_ECUDA;
+        for (int p = 0; p < npairs && status == RG_OK; ++p) {
+            if (err[p]) status = RG_ETIMEOUT;
+            const int nrows = hs[p].halted ? hs[p].halt_it + 1 : s->gn_iters;
+            if (report)
+                memcpy(report + ((size_t)p * levels + (Lc - l)) * s->gn_iters * 8, rep.data() + (size_t)p * rows.size(),
+                       sizeof(double) * 8 * (size_t)nrows);
+            if (hs[p].halted && !status) status = hs[p].status;
+        }
+        for (int p = 0; p < npairs; ++p) {
+            Pair &q = ps[p];
+            q.P.delta = q.cl->P.delta;
+            rg_ctx_destroy(q.cl);
+            q.cl = nullptr;
+            if (!status && l > 0 && launch_prolong_grid(q.gl[l].m, q.ul[l], q.ul[l - 1], st) != cudaSuccess)
+                status = RG_ECUDA;
+            if (!status && l > 0) g_launches.fetch_add(1, std::memory_order_relaxed);
+        }
+    }
+    for (int p = 0; p < npairs && status == RG_OK; ++p) {
+        const long Mf = (long)fin[p].m[0] * fin[p].m[1] * fin[p].m[2];
+        if (cudaMemcpyAsync(u_inout[p], ps[p].ul[0], sizeof(float) * 3 * Mf, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            status = RG_ECUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && !status) status = RG_ECUDA;
+    release();
     return status;
 }
 

@@ -55,3 +55,26 @@ def test_batch_matches_pairs_one_by_one_and_oracle():
     d = np.abs(us[3].cpu().numpy() - uo).max()
     print(f"batch: {len(pairs)} pairs in {sec:.3f} s; smallest vs oracle max |du| = {d:.2e} mm")
     assert d <= TOL_U
+
+
+@pytest.mark.gpu
+def test_batched_graph_equals_per_pair_graph_drive():
+    """register_pyramid_batch (one graph per level advancing all pairs) gives
+    each pair the bits of register_pyramid with the graph drive, FP32 and FP16."""
+    import torch
+    from paper_1807_00467_gb300 import api
+    ph = phantom.make_phantom((64, 64, 32), (1.5, 1.5, 3.0), seed=9, motion="small", n_vessels=12)
+    for half in (False, True):
+        R, T = torch.from_numpy(ph.R).cuda(), torch.from_numpy(ph.T).cuda()
+        if half:
+            R, T = (R + 1024.0).half(), (T + 1024.0).half()
+        pairs = batch.crop_pairs(R, T, ph.h, [(64, 64, 32), (48, 56, 32), (56, 48, 24), (40, 40, 16)])
+        params = api.make_params(eta=10.0, alpha=1.0, gamma=0.001)
+        sched = dict(levels=2, gn_iters=3, pcg_iters=10)
+        us, reps, sec = batch.register_batch_graph(pairs, params, **sched)
+        for (Rc, Tc, h, m), ub, rb in zip(pairs, us, reps):
+            u = torch.zeros((3,) + m[::-1], device="cuda")
+            code, rep = api.register_pyramid(Rc, Tc, h, m, u, params, drive="graph", **sched)
+            assert code == 0
+            np.testing.assert_array_equal(rb, rep)
+            assert torch.equal(ub, u)
