@@ -665,13 +665,14 @@ int run_bp(int n, const float *D, const int *kps, const float *inten, float sig,
     tree_kernel<<<1, 1024, 0, st>>>(n, root, w.edges, w.deg, w.off, w.adj, w.order, w.level_off, w.nlevels, w.parent,
                                     w.child_off, w.child);
     if (cudaGetLastError() != cudaSuccess) return RG_ECUDA;
+    // the level count and offsets, read on the caller's stream in one synchronisation
     int nl = 0;
+    std::vector<int> lo(n + 2);
     if (cudaMemcpyAsync(&nl, w.nlevels, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(lo.data(), w.level_off, sizeof(int) * (n + 2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return RG_ECUDA;
-    std::vector<int> lo(nl + 1);
-    if (cudaMemcpy(lo.data(), w.level_off, sizeof(int) * (nl + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return RG_ECUDA;
+    if (nl < 1 || nl > n) return RG_ECUDA;
     BpArgs a;
     a.D = D;
     a.up = w.up;
