@@ -57,6 +57,7 @@ def lib():
         L.orc_check.argtypes = [P]
         L.orc_prolong.argtypes = [P, dp, dp]
         L.orc_warp.argtypes = [P, dp, dp, dp]
+        L.orc_cells.argtypes = [P, dp, ip]
         L.orc_ngf_distance.argtypes = [P, dp, dp, dp]
         L.orc_ngf_distance.restype = C.c_double
         L.orc_objective.argtypes = [P, dp, dp]
@@ -141,6 +142,13 @@ class Problem:
         out = np.empty((3, self.n[2], self.n[1], self.n[0]))
         lib().orc_prolong(self._ref(), _dp(u), _dp(out))
         return out
+
+    def cells(self, u):
+        """Sample cell per voxel and axis (int32 [3][nz][ny][nx]) as decided in FP32."""
+        u = _f64(u)
+        k = np.empty((3, self.n[2], self.n[1], self.n[0]), dtype=np.int32)
+        lib().orc_cells(self._ref(), _dp(u), k.ctypes.data_as(C.POINTER(C.c_int)))
+        return k
 
     def warp(self, u):
         u = _f64(u)

@@ -149,6 +149,20 @@ static void decide_cells(const orc_problem *p, const double *u, int i1, int i2, 
     }
 }
 
+void orc_cells(const orc_problem *p, const double *u, int *k) {
+    long N = nvox(p);
+#pragma omp parallel for collapse(2)
+    for (int i3 = 0; i3 < p->n[2]; ++i3)
+        for (int i2 = 0; i2 < p->n[1]; ++i2)
+            for (int i1 = 0; i1 < p->n[0]; ++i1) {
+                int kk[3];
+                float fr[3];
+                decide_cells(p, u, i1, i2, i3, kk, fr);
+                long v = IDX(p->n, i1, i2, i3);
+                for (int a = 0; a < 3; ++a) k[a * N + v] = kk[a];
+            }
+}
+
 /* Per-axis sample placement: cell index, FP64 fraction, inside flag. */
 static void place_axis(int n, int k, float fr32, double s, int *cell, double *frac, int *inside) {
     if (k < 0) {                         /* below the domain: clamp to 0 */
@@ -210,11 +224,14 @@ static int interior(const int *n, int i1, int i2, int i3) {
 double orc_ngf_distance(const orc_problem *p, const double *Tw, double *r, double *a) {
     long N = nvox(p);
     const int *n = p->n;
-    double eta2 = p->eta * p->eta, hb = hbar(p), D = 0.0;
-#pragma omp parallel for collapse(2) reduction(+ : D)
+    double eta2 = p->eta * p->eta, hb = hbar(p);
+    /* the sum over voxels in a fixed order: each x row in order, then the rows */
+    double *row = calloc((size_t)n[1] * n[2], sizeof(double));
+#pragma omp parallel for collapse(2)
     for (int i3 = 0; i3 < n[2]; ++i3)
         for (int i2 = 0; i2 < n[1]; ++i2)
             for (int i1 = 0; i1 < n[0]; ++i1) {
+                double *D = &row[(long)i3 * n[1] + i2];
                 long v = IDX(n, i1, i2, i3);
                 if (!interior(n, i1, i2, i3)) {
                     if (r) r[v] = 0.0;
@@ -231,13 +248,16 @@ double orc_ngf_distance(const orc_problem *p, const double *Tw, double *r, doubl
                 double ff = eta2 + f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
                 double gg = eta2 + g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
                 /* Eq. (1) as printed: 1 - <f,g>^2 / (|f|^2 |g|^2) */
-                D += hb * (1.0 - (fg * fg) / (ff * gg));
+                *D += hb * (1.0 - (fg * fg) / (ff * gg));
                 double nf = sqrt(ff), ng = sqrt(gg);
                 double rv = fg / (nf * ng);
                 if (r) r[v] = rv;
                 if (a)   /* dr/dg = f/(|f| |g|) - r g/|g|^2 */
                     for (int k = 0; k < 3; ++k) a[k * N + v] = f[k] / (nf * ng) - rv * g[k] / gg;
             }
+    double D = 0.0;
+    for (long i = 0; i < (long)n[1] * n[2]; ++i) D += row[i];
+    free(row);
     return D;
 }
 
@@ -461,12 +481,15 @@ int orc_vcc(const orc_problem *p, const double *u, const double *v, double *ener
     long NC = (long)nc[0] * nc[1] * nc[2];
     double G = ghat(p);
     double *cellout = out ? calloc((size_t)NC * 24, sizeof(double)) : NULL;
-    double e = 0.0, dmin = INFINITY, dmax = -INFINITY;
+    double dmin = INFINITY, dmax = -INFINITY;
     int fold = 0;
-#pragma omp parallel for collapse(2) reduction(+ : e, fold) reduction(min : dmin) reduction(max : dmax)
+    /* the energy summed in a fixed order: each x row of cells in order, then the rows */
+    double *erow = calloc((size_t)nc[1] * nc[2], sizeof(double));
+#pragma omp parallel for collapse(2) reduction(+ : fold) reduction(min : dmin) reduction(max : dmax)
     for (int c3 = 0; c3 < nc[2]; ++c3)
         for (int c2 = 0; c2 < nc[1]; ++c2)
             for (int c1 = 0; c1 < nc[0]; ++c1) {
+                double *e = &erow[(long)c3 * nc[1] + c2];
                 double E[3][4][3], V[3][4][3];
                 cell_edges(p, u, c1, c2, c3, E);
                 if (v) {   /* edge differences of v (no unit term) */
@@ -487,7 +510,7 @@ int orc_vcc(const orc_problem *p, const double *u, const double *v, double *ener
                             if (d < dmin) dmin = d;
                             if (d > dmax) dmax = d;
                             if (d <= 0.0) { fold += 1; continue; }
-                            e += G * psi(d);
+                            *e += G * psi(d);
                             double wgt;
                             if (!v) wgt = G * dpsi(d);
                             else wgt = G * d2psi(d) * (dot3(x23, V[0][a]) + dot3(x31, V[1][b]) + dot3(x12, V[2][c]));
@@ -511,6 +534,9 @@ int orc_vcc(const orc_problem *p, const double *u, const double *v, double *ener
                         }
                 }
             }
+    double e = 0.0;
+    for (long i = 0; i < (long)nc[1] * nc[2]; ++i) e += erow[i];
+    free(erow);
     if (dminmax) { dminmax[0] = dmin; dminmax[1] = dmax; }
     if (energy) *energy = fold ? INFINITY : e;
     if (out) {

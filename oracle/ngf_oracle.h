@@ -49,6 +49,11 @@ int orc_check(const orc_problem *p);
 /* Trilinear prolongation of a grid field onto voxel centres: disp [3][N]. */
 void orc_prolong(const orc_problem *p, const double *u, double *disp);
 
+/* The sample cell of every voxel along each axis, k[a][v] = i_a + floor(s_a)
+ * before clamping, as decided in FP32 (the integer decision both the GPU
+ * kernels and orc_warp take; exported for its pin against the FP64 floor). */
+void orc_cells(const orc_problem *p, const double *u, int *k);
+
 /* Warped template Tw = T(y) and its derivative dT = dT/dy ([3][N]), Eq. (1). */
 void orc_warp(const orc_problem *p, const double *u, double *Tw, double *dT);
 

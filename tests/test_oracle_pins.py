@@ -505,3 +505,99 @@ def test_pyramid_reduces_objective():
     u, rep, st = P.register_pyramid(u0, levels=2, gn_iters=3, pcg_iters=8)
     assert st == 0
     assert P.objective(u)[0][4] < J0
+
+
+# --------------------------------------------- multilevel driver (Sec. II-D3)
+def _pyramid_problem(seed, n_keypoints=0):
+    from paper_1807_00467_gb300 import phantom
+    ph = phantom.make_phantom((64, 32, 32), (1.5, 2.0, 4.0), seed=seed, motion="small", n_vessels=10,
+                              n_keypoints=n_keypoints)
+    return ph, (17, 9, 9)
+
+
+def test_pyramid_with_one_level_is_the_gn_schedule():
+    ph, m = _pyramid_problem(30)
+    u0 = np.random.default_rng(31).normal(0, 0.5, (3,) + m[::-1])
+    P1 = oracle.Problem(ph.R, ph.T, ph.h, m, eta=10.0, alpha=1.0, gamma=0.001)
+    u1, rep1, st1 = P1.register_pyramid(u0, levels=1, gn_iters=3, pcg_iters=8)
+    P2 = oracle.Problem(ph.R, ph.T, ph.h, m, eta=10.0, alpha=1.0, gamma=0.001)
+    u2, rep2, st2 = P2.gn_solve(u0, gn_iters=3, pcg_iters=8)
+    assert st1 == st2 == 0
+    np.testing.assert_array_equal(u1, u2)
+    np.testing.assert_array_equal(rep1[0], rep2)
+
+
+@pytest.mark.parametrize("levels,kp", [(2, False), (3, True)])
+def test_pyramid_is_coarse_solves_and_grid_prolongations(levels, kp):
+    """The multilevel driver, decomposed by hand: level l has the images
+    restricted l times (2x2x2 box), spacing 2^l h and nodes (m - 1) / 2^l + 1
+    per axis; the coarsest start is u0 injected (coarse node k <- fine node
+    2^L k); each level runs the Gauss-Newton schedule from the dyadic
+    prolongation of the coarser result; delta = D / K is set once, at the
+    coarsest start, and carried to the finer levels.  The driver's report rows
+    and result must be those of this composition bit for bit, the first row of
+    each level must hold J of its own problem at its start, and a wrong
+    spacing, grid size, injection node, delta carry or level order breaks it."""
+    ph, m = _pyramid_problem(32, n_keypoints=60 if kp else 0)
+    kx = ph.kp_x.astype(np.float64) if kp else None
+    ky = ph.kp_y.astype(np.float64) if kp else None
+    u0 = np.random.default_rng(33).normal(0, 0.5, (3,) + m[::-1])
+    kw = dict(eta=10.0, alpha=1.0, gamma=0.001, delta=0.0, kx=kx, ky=ky)
+    Pf = oracle.Problem(ph.R, ph.T, ph.h, m, **kw)
+    u_pyr, rep_pyr, st = Pf.register_pyramid(u0, levels=levels, gn_iters=2, pcg_iters=6, delta_adaptive=kp)
+    assert st == 0
+    L = levels - 1
+    R, T = [ph.R], [ph.T]
+    for _ in range(L):
+        R.append(oracle.restrict_image(R[-1]))
+        T.append(oracle.restrict_image(T[-1]))
+    ml = [tuple((m[a] - 1) // 2 ** l + 1 for a in range(3)) for l in range(levels)]
+    hl = [tuple(ph.h[a] * 2 ** l for a in range(3)) for l in range(levels)]
+    u = u0[:, ::2 ** L, ::2 ** L, ::2 ** L].copy()
+    assert u.shape == (3,) + ml[L][::-1]
+    delta = 0.0
+    for l in range(L, -1, -1):
+        Pl = oracle.Problem(R[l], T[l], hl[l], ml[l], **dict(kw, delta=delta))
+        if kp and l == L:
+            D0, K0 = Pl.ngf_gradient(u)[0], Pl.keypoints(u)[0]
+            delta = D0 / K0
+            Pl.delta = delta
+        J_start = Pl.objective(u)[0][4]
+        u, rep, st_l = Pl.gn_solve(u, gn_iters=2, pcg_iters=6)
+        assert st_l == 0
+        assert rep[0, 1] == J_start
+        np.testing.assert_array_equal(rep, rep_pyr[L - l])
+        if l > 0:
+            u = oracle.prolong_grid(u, ml[l - 1])
+    np.testing.assert_array_equal(u, u_pyr)
+    if kp:
+        assert Pf.delta == delta and delta > 0.0
+
+
+# --------------------------------------------- the FP32 cell decision
+@pytest.mark.parametrize("name,field", [("tiny", "motion"), ("mid", "motion"), ("mid", "random"), ("full", "motion")])
+def test_fp32_cell_decision_is_the_fp64_floor_away_from_knots(name, field):
+    """The sample cell is an integer decided in FP32 (the kernels' precision;
+    both sides take it the same way).  Against the definition, floor of the
+    FP64 sample coordinate s = i + (P u)(x) / h: equal at every voxel farther
+    than 1e-4 (voxel units) from an integer, and never more than one cell
+    apart; the voxels where the two differ are counted and reported."""
+    from paper_1807_00467_gb300 import phantom
+    c = phantom.CONFIGS[name]
+    ph = phantom.make_phantom(c["n"], c["h"], seed=0, motion=c["motion"])
+    m = c["m"]
+    u = phantom.motion_on_grid(ph, m, 1.0) if field == "motion" else phantom.random_grid_field(m, 40) * 4.0
+    P = oracle.Problem(ph.R, ph.T, ph.h, m)
+    k32 = P.cells(u)
+    d = P.prolong(u)
+    n = P.n
+    idx = [np.arange(n[0])[None, None, :], np.arange(n[1])[None, :, None], np.arange(n[2])[:, None, None]]
+    differ = 0
+    for a in range(3):
+        s = idx[a] + d[a] / ph.h[a]
+        k64 = np.floor(s)
+        far = np.abs(s - np.rint(s)) > 1e-4
+        assert np.array_equal(k32[a][far], k64[far].astype(np.int32)), (name, a)
+        assert np.abs(k32[a] - k64).max() <= 1
+        differ += int((k32[a] != k64).sum())
+    print(f"{name} {field}: {differ} of {3 * P.N} cell decisions differ from the FP64 floor (all within 1e-4 of a knot)")
