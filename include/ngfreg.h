@@ -85,7 +85,16 @@ typedef struct {
     double delta;         /* keypoint weight, Eq. (11) */
     int32_t delta_adaptive; /* 1: delta = D(u0)/K(u0) at the start (Sec. II-D2) */
     double tau;           /* extra shift added to the PCG preconditioner diagonal (0 by default) */
+    double det_lo, det_hi; /* reporting bounds on the Jacobian bounds d of Eq. (8) (e.g. 0.25, 4): the
+                              solve reports whether min d >= det_lo and max d <= det_hi; psi is unchanged */
 } rg_params;
+
+/* Columns of a Gauss-Newton report row: {it, J, g.p, t (0 = rejected),
+ * J new, evaluations, pcg steps, status, min d, max d, in bounds}, where
+ * min d / max d are the extremes of the 64 Jacobian bounds d of Eq. (8) over
+ * all grid cells at the iterate after the step, and "in bounds" is 1 when
+ * det_lo <= min d and max d <= det_hi, else 0. */
+#define RG_REPORT_COLS 11
 
 typedef struct {
     int32_t levels;       /* pyramid levels (register_pyramid), >= 1 */
@@ -195,8 +204,7 @@ int gn_pcg_solve(rg_ctx *ctx, const float *g_dev, float *p_dev, int32_t iters, d
 
 /* Fixed Gauss-Newton schedule on one level: gn_iters x (gradient +
  * linearisation, PCG, Armijo backtracking).  u_dev is updated in place.
- * report_host: double[gn_iters][8] = {it, J, g.p, t (0 = rejected), J new,
- * evaluations, pcg steps, status} or NULL.  Host-driven (flags 0):
+ * report_host: double[gn_iters][RG_REPORT_COLS] (see RG_REPORT_COLS) or NULL.  Host-driven (flags 0):
  * synchronises the stream once per line-search try; see RG_SCHED_DEVICE. */
 int gn_solve(rg_ctx *ctx, float *u_dev, const rg_schedule *sched, double *report_host);
 
@@ -205,7 +213,7 @@ int gn_solve(rg_ctx *ctx, float *u_dev, const rg_schedule *sched, double *report
  * prolongation between levels.  R_dev, T_dev, u_inout_dev are at the finest
  * level; u_inout's start value is injected onto the coarsest grid.
  * workspace_dev: rg_pyramid_workspace_size bytes.  report_host:
- * double[levels][gn_iters][8] (coarsest first) or NULL. */
+ * double[levels][gn_iters][RG_REPORT_COLS] (coarsest first) or NULL. */
 int rg_pyramid_workspace_size(const rg_image_geom *img, const rg_grid_geom *finest, rg_dtype dtype,
                               int32_t levels, int32_t nk_max, int32_t pcg_max, size_t *bytes);
 int register_pyramid(const rg_image_geom *img, const void *R_dev, const void *T_dev, rg_dtype dtype,
@@ -222,9 +230,14 @@ int register_pyramid(const rg_image_geom *img, const void *R_dev, const void *T_
  * decided on the device) as a parallel branch and is replayed gn_iters times:
  * one graph launch advances all pairs.  Per pair the results have the bits of
  * register_pyramid with RG_SCHED_GRAPH.  report_host: double
- * [npairs][levels][gn_iters][8] or NULL.  Returns the first pair's error, if
- * any, after the level where it arose.  Synchronises the stream once per
- * level. */
+ * [npairs][levels][gn_iters][RG_REPORT_COLS] or NULL.  A pair whose schedule
+ * halts (a fold at the iterate, RG_EFOLD, or a non-finite objective,
+ * RG_ENONFINITE) leaves the batch after that level: its u_inout keeps its start
+ * value and its report rows stop at the halting row (status in column 7,
+ * later rows zero); the other pairs run to the end and get their results.
+ * Returns RG_OK, else the halting code of the lowest-numbered pair that halted;
+ * other errors (RG_EINVAL, RG_ECUDA, RG_ETIMEOUT) abort the whole batch with no
+ * output written.  Synchronises the stream once per level. */
 int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, const void *const *R, const void *const *T,
                            rg_dtype dtype, const rg_grid_geom *finest, const rg_params *params,
                            const rg_schedule *sched, float *const *u_inout, double *report_host,
@@ -243,8 +256,10 @@ int rg_prolong_grid(const int32_t *mc, const float *uc_dev, float *uf_dev, void 
  * double.  Its only scratch is a file-scope device array of
  * RG_NOALLOC_MAX_CTAS doubles (512 KB on every GPU that loads the library,
  * held until the process exits), one partial sum per CTA: problems needing
- * more CTAs (32 x 16 voxels in x-y times z chunks of up to 32 slices) return
- * RG_ESCRATCH.  Each call overwrites the partials before reading them.  All
+ * more CTAs return RG_ESCRATCH.  A CTA covers a tile of 28 - 28 % rho_x voxels
+ * in x (rho_x = n[0] / (m[0] - 1)), 16 in y and a z chunk of at most 32 slices
+ * (fewer, whole grid cells, for large ratios), so the CTA count is
+ * ceil(n[0] / tx) x ceil(n[1] / 16) x ceil(n[2] / tz).  Each call overwrites the partials before reading them.  All
  * calls share that array, so calls whose kernels overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * The first call on each device looks the array's device address up with
@@ -266,6 +281,26 @@ int rg_profile(rg_ctx *ctx, int32_t enable);
 int rg_profile_read(rg_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches);
 /* Number of kernels this library has launched in the process so far. */
 int64_t rg_launch_count(void);
+
+/* Synchronise the context's stream and return the status its kernels
+ * latched on the device since the last call: RG_ETIMEOUT if a kernel gave up
+ * a bounded wait for a TMA transfer (its results are not valid), else
+ * RG_ENONFINITE if an objective (ngf_objective, ngf_gradient, gn_linearize,
+ * or a line-search evaluation) came out NaN, or +inf without a fold (non-finite
+ * values in the images, keypoints or u), else RG_OK.  Clears the latches.
+ * The asynchronous entry points return before their kernels run; this is where
+ * their device-side failures surface. */
+int rg_sync(rg_ctx *ctx);
+
+/* Test hooks (no counterpart in the paper), for exercising the failure
+ * paths without a GPU fault.  RG_HOOK_NO_TMA (value 0/1): the GN-product
+ * kernels issue no TMA copy, so each of their bounded waits on a TMA barrier
+ * runs out (the results are garbage and RG_ETIMEOUT is latched; no copy is
+ * ever in flight).  RG_HOOK_POLL_LIMIT (value > 0): polls of a TMA barrier
+ * before such a wait gives up (default 2^20). */
+#define RG_HOOK_NO_TMA 1
+#define RG_HOOK_POLL_LIMIT 2
+int rg_debug_hook(rg_ctx *ctx, int32_t what, int32_t value);
 
 /* Latched error text of the last failing call on this context. */
 const char *rg_last_error(const rg_ctx *ctx);

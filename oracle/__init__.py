@@ -58,6 +58,7 @@ def lib():
         L.orc_prolong.argtypes = [P, dp, dp]
         L.orc_warp.argtypes = [P, dp, dp, dp]
         L.orc_cells.argtypes = [P, dp, ip]
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_ngf_distance.argtypes = [P, dp, dp, dp]
         L.orc_ngf_distance.restype = C.c_double
         L.orc_objective.argtypes = [P, dp, dp]
@@ -298,3 +299,8 @@ def prolong_grid(uc, mf):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_threads(n):
+    """OpenMP threads of later oracle calls in this process."""
+    lib().orc_set_threads(int(n))

@@ -50,6 +50,14 @@ int orc_num_threads(void) {
 #endif
 }
 
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 static long nvox(const orc_problem *p) { return (long)p->n[0] * p->n[1] * p->n[2]; }
 static long nnod(const orc_problem *p) { return (long)p->m[0] * p->m[1] * p->m[2]; }
 static int ratio(const orc_problem *p, int a) { return p->n[a] / (p->m[a] - 1); }

@@ -99,6 +99,7 @@ int orc_register_pyramid(orc_problem *finest, int levels, double *u, int gn_iter
                          int ls_max, double armijo_c, double tau, int delta_adaptive, double *report);
 
 int orc_num_threads(void);
+void orc_set_threads(int n);   /* OpenMP threads of the following calls (timing on fewer cores) */
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,8 @@ RG_NOALLOC_MAX_CTAS = 65536
 RG_CURV, RG_VCC, RG_KP = 1, 2, 4
 RG_PCG_MAX = 63
 RG_F32, RG_F16 = 0, 1
+RG_HOOK_NO_TMA, RG_HOOK_POLL_LIMIT = 1, 2
+RG_REPORT_COLS = 11     # {it, J, g.p, t, J new, evaluations, pcg steps, status, min d, max d, in bounds}
 
 
 class ImageGeom(C.Structure):
@@ -29,7 +31,7 @@ class GridGeom(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("eta", C.c_double), ("alpha", C.c_double), ("gamma", C.c_double), ("delta", C.c_double),
-                ("delta_adaptive", C.c_int32), ("tau", C.c_double)]
+                ("delta_adaptive", C.c_int32), ("tau", C.c_double), ("det_lo", C.c_double), ("det_hi", C.c_double)]
 
 
 class Schedule(C.Structure):
@@ -44,7 +46,7 @@ EXPORTS = [
     "rg_restrict_image", "rg_prolong_grid", "rg_last_error", "rg_version", "rg_profile", "rg_profile_read",
     "rg_launch_count", "ngf_distance_noalloc", "rg_set_tile", "rg_autotune", "kp_workspace_size", "kp_scratch_size",
     "kp_ngf_features", "kp_cost_volume", "kp_mst", "kp_bp_marginals", "kp_match", "kp_launch_count",
-    "kp_forstner_workspace_size", "kp_forstner", "register_pyramid_batch",
+    "kp_forstner_workspace_size", "kp_forstner", "register_pyramid_batch", "rg_sync", "rg_debug_hook",
 ]
 
 _lib = None
@@ -104,6 +106,8 @@ def load():
         "rg_profile_read": ([vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
         "rg_launch_count": ([], C.c_int64),
         "ngf_distance_noalloc": ([IG, GG, vp, vp, vp, C.c_double, vp, vp], C.c_int),
+        "rg_sync": ([vp], C.c_int),
+        "rg_debug_hook": ([vp, i32, i32], C.c_int),
         "rg_last_error": ([vp], C.c_char_p),
         "rg_version": ([], C.c_char_p),
     }

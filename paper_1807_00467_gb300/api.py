@@ -16,8 +16,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (RG_CURV, RG_EFOLD, RG_F16, RG_F32, RG_KP, RG_OK, RG_VCC, GridGeom, ImageGeom, NgfError, Params,
-                   Schedule)
+from ._lib import (RG_CURV, RG_EFOLD, RG_F16, RG_F32, RG_KP, RG_OK, RG_REPORT_COLS, RG_VCC, GridGeom, ImageGeom,
+                   NgfError, Params, Schedule)
 
 __all__ = ["Context", "register_pyramid", "restrict_image", "prolong_grid", "launch_count", "RG_CURV", "RG_VCC", "RG_KP",
            "RG_EFOLD", "NgfError", "make_params", "make_schedule"]
@@ -39,8 +39,9 @@ def _check(code, ctx=None, name=""):
     return code
 
 
-def make_params(eta=10.0, alpha=1.0, gamma=0.0, delta=0.0, delta_adaptive=False, tau=0.0):
-    return Params(eta, alpha, gamma, delta, int(bool(delta_adaptive)), tau)
+def make_params(eta=10.0, alpha=1.0, gamma=0.0, delta=0.0, delta_adaptive=False, tau=0.0, det_lo=0.25, det_hi=4.0):
+    """det_lo, det_hi: reporting bounds on the Jacobian bounds d (report column 10)."""
+    return Params(eta, alpha, gamma, delta, int(bool(delta_adaptive)), tau, det_lo, det_hi)
 
 
 SCHED_DEVICE, SCHED_GRAPH, SCHED_AUTOTUNE = 1, 2, 4    # rg_schedule.flags
@@ -197,6 +198,15 @@ class Context:
                self._ctx, "gn_pcg_solve")
         return p, stats
 
+    def sync(self):
+        """Synchronises the context stream; returns the latched device status
+        (RG_OK) or raises NgfError with RG_ETIMEOUT / RG_ENONFINITE."""
+        return _check(_lib.load().rg_sync(self._ctx), self._ctx, "rg_sync")
+
+    def debug_hook(self, what, value):
+        """Test hooks of include/ngfreg.h (RG_HOOK_NO_TMA, RG_HOOK_POLL_LIMIT)."""
+        _check(_lib.load().rg_debug_hook(self._ctx, int(what), int(value)), self._ctx, "rg_debug_hook")
+
     def profile(self, enable=True):
         """Record CUDA events around every kernel launch on the context stream."""
         _check(_lib.load().rg_profile(self._ctx, int(bool(enable))), self._ctx, "rg_profile")
@@ -209,9 +219,10 @@ class Context:
         return ms.value, cnt.value
 
     def gn_solve(self, u, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, drive="host", autotune=False):
-        """Runs the fixed Gauss-Newton schedule in place on u; returns (status, report)."""
+        """Runs the fixed Gauss-Newton schedule in place on u; returns (status,
+        report) with report rows of RG_REPORT_COLS columns (include/ngfreg.h)."""
         sched = make_schedule(1, gn_iters, pcg_iters, ls_max, armijo_c, drive, autotune)
-        rep = np.zeros((gn_iters, 8))
+        rep = np.zeros((gn_iters, RG_REPORT_COLS))
         code = _check(_lib.load().gn_solve(self._ctx, _ptr(self._field(u)), C.byref(sched),
                                            rep.ctypes.data_as(C.POINTER(C.c_double))), self._ctx, "gn_solve")
         return code, rep
@@ -230,7 +241,7 @@ def register_pyramid(R, T, h, m_finest, u, params, levels, gn_iters, pcg_iters, 
     ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=R.device)
     wp = (ws.data_ptr() + 255) & ~255
     sched = make_schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c, drive, autotune)
-    rep = np.zeros((levels, gn_iters, 8))
+    rep = np.zeros((levels, gn_iters, RG_REPORT_COLS))
     code = L.register_pyramid(C.byref(ig), _ptr(R), _ptr(T), dtype, C.byref(gg), C.byref(params), C.byref(sched), nk,
                               _ptr(kx), _ptr(ky), _ptr(u), rep.ctypes.data_as(C.POINTER(C.c_double)),
                               C.c_void_p(wp), nbytes.value, _stream_ptr(stream))

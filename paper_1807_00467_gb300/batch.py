@@ -56,11 +56,15 @@ def crop_pairs(R, T, h, shapes, grid_step=4):
     return out
 
 
-def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, stream=None):
+def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, stream=None, u0=None):
     """All pairs (R, T, h, m) in lockstep through the multilevel schedule with
     one CUDA graph per level advancing every pair's Gauss-Newton iteration
     (register_pyramid_batch); no host threads.  Returns (displacements,
-    reports, seconds) like register_batch."""
+    reports, seconds, code): code is RG_OK, or the halting status (RG_EFOLD,
+    RG_ENONFINITE) of the lowest-numbered pair whose schedule halted; such a
+    pair keeps its start value and its report stops at the halting row, the
+    others are complete.  Other errors raise.  u0: start fields (finest grid)
+    per pair, default zero."""
     import ctypes as C
 
     from . import _lib
@@ -70,7 +74,8 @@ def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, 
     dtype = api._dtype_code(pairs[0][0])
     igs = (_lib.ImageGeom * n)(*[api._img_geom(R.shape, h) for R, T, h, m in pairs])
     ggs = (_lib.GridGeom * n)(*[api._grid_geom(m) for R, T, h, m in pairs])
-    us = [torch.zeros((3, m[2], m[1], m[0]), dtype=torch.float32, device=dev) for R, T, h, m in pairs]
+    us = [torch.zeros((3, m[2], m[1], m[0]), dtype=torch.float32, device=dev) if u0 is None else
+          u0[i].to(device=dev, dtype=torch.float32).contiguous().clone() for i, (R, T, h, m) in enumerate(pairs)]
     wss, wps, wbs = [], [], []
     for i in range(n):
         b = C.c_size_t()
@@ -86,7 +91,7 @@ def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, 
         arr = (C.c_void_p * n)(*[t.data_ptr() for t in ts])
         keep.append(arr)
         return C.cast(arr, C.c_void_p)
-    rep = np.zeros((n, levels, gn_iters, 8))
+    rep = np.zeros((n, levels, gn_iters, _lib.RG_REPORT_COLS))
     sched = api.make_schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c)
     wsa = (C.c_void_p * n)(*wps)
     wsp = C.cast(wsa, C.c_void_p)
@@ -98,9 +103,9 @@ def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, 
                                     api._stream_ptr(stream))
     torch.cuda.synchronize(dev)
     seconds = time.perf_counter() - t0
-    if code < 0:
+    if code < 0 and code != _lib.RG_ENONFINITE:
         raise api.NgfError(code, "register_pyramid_batch")
-    return us, list(rep), seconds
+    return us, list(rep), seconds, code
 
 
 def register_batch(pairs, params, levels, gn_iters, pcg_iters, workers=4, ls_max=10, armijo_c=1e-4, drive="host",

@@ -44,15 +44,22 @@ struct rg_ctx {
     float *dmin, *dmax;
     float *minv, *d, *q, *tg_, *tu, *ts;
     float *Rh;                // PCG residual history, pcg_max + 1 slots of pcg_stride(3 M) floats
-    int *tma_err;             // [0]: set by the kernels if a bounded TMA wait gave up; [1]: PCG ticket
+    int *tma_err;             // [0]: set by the kernels if a bounded TMA wait gave up; [1]: PCG ticket;
+                              // [2]: set by the terms kernel when an objective came out NaN (or +inf without a fold)
     bool err_zeroed;
     CUtensorMap map_dT, map_a;
+    ColGeom cg;               // column-marching GN-product kernel: geometry, tensor maps, node boxes
+    CUtensorMap map_col_dT, map_col_a;
+    BoxGeom bM;
+    const BoxGeom *bcur;      // node-box geometry of the last NGF tile launch (read by the node pass)
+    int hook_no_tma, hook_poll;   // test hooks (rg_debug_hook)
     double *rzh, *coef, *pcgpart;
     PcgScalars *sc;
     bool has_lin, minv_valid;
     char err[512];
     GnState *gn;              // device side of a Gauss-Newton iteration
-    double *gnrep;            // its report rows [kGnRows][8]
+    double *gnrep;            // its report rows [kGnRows][RG_REPORT_COLS]
+    double *range_terms;      // terms output of a d-range pass (volume term only)
     const int *skip;          // set while a line-search try is launched: the try's kernels skip when *skip
     cudaStream_t gst;         // private stream of device-driven schedules (created on first use)
     cudaEvent_t gev[2];
@@ -169,16 +176,40 @@ static void tile_geom(const rg_image_geom *img, const rg_grid_geom *grid, TileGe
     if ((long)t.nzt * 3 * t.nxt * t.nyt > 12 * 1024) t.nzt = 0;
 }
 
+// Column geometry of the column-marching GN-product kernel: TXI x 16 voxel
+// columns in x-y (TXI = 60 less a remainder so that it is whole cells), every z
+// plane; node boxes [3][m3][C1 + 1][C0 + 1] per column.
+static void col_geom(const rg_image_geom *img, const rg_grid_geom *grid, ColGeom &c) {
+    for (int a = 0; a < 3; ++a) {
+        c.n[a] = img->n[a];
+        c.m[a] = grid->m[a];
+        c.rho[a] = img->n[a] / (grid->m[a] - 1);
+        c.lrho[a] = c.rho[a] == 8 ? 3 : c.rho[a] == 4 ? 2 : c.rho[a] == 2 ? 1 : 0;
+        c.irho[a] = 1.0f / (float)c.rho[a];
+        c.inv2h[a] = (float)(1.0 / (2.0 * img->h[a]));
+    }
+    c.TXI = 60 - 60 % c.rho[0];
+    c.nb[0] = (c.n[0] + c.TXI - 1) / c.TXI;
+    c.nb[1] = (c.n[1] + 15) / 16;
+    c.C0 = c.TXI / c.rho[0];
+    c.C1 = 16 / c.rho[1];
+    // node columns of voxel columns x0 - 2 .. x0 + 61 (rows y0 - 2 .. y0 + 17) and the next node
+    c.nxt = ((61 >> c.lrho[0]) + 1) - ((-2) >> c.lrho[0]) + 1;
+    c.nyt = ((17 >> c.lrho[1]) + 1) - ((-2) >> c.lrho[1]) + 1;
+    c.box = (c.C0 + 1) * (c.C1 + 1) * c.m[2];
+    c.tma = 0;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // TMA maps over a stored [3][n3][n2][n1] float field as the 4-D tensor
-// {x, y, z, component}; box {kTmaBoxX, TY + 4, 1, 3}.  Returns false (and the
+// {x, y, z, component}; box {box_x, TY + 4, 1, 3}.  Returns false (and the
 // kernels read with plain loads) when the driver entry point is unavailable or
 // the row pitch is not a multiple of 16 bytes.
-static bool encode_field_map(CUtensorMap *map, const int *n, int TY, float *base) {
-    if (n[0] % 4 != 0 || n[0] < kTmaBoxX || n[1] < TY + 4) return false;
+static bool encode_field_map(CUtensorMap *map, const int *n, int TY, float *base, int box_x = kTmaBoxX) {
+    if (n[0] % 4 != 0 || n[0] < box_x || n[1] < TY + 4) return false;
     static const EncodeTiledFn fn = [] {   // looked up once, also under concurrent callers
         void *f = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -193,7 +224,7 @@ static bool encode_field_map(CUtensorMap *map, const int *n, int TY, float *base
     const cuuint64_t dims[4] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2], 3};
     const cuuint64_t strides[3] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4,
                                    (cuuint64_t)n[0] * n[1] * n[2] * 4};
-    const cuuint32_t box[4] = {(cuuint32_t)kTmaBoxX, (cuuint32_t)(TY + 4), 1, 3};
+    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)(TY + 4), 1, 3};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -249,9 +280,10 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->tu = cv.take<float>(3 * M);
     c->ts = cv.take<float>(3 * M);
     c->sc = cv.take<PcgScalars>(1);
-    c->tma_err = cv.take<int>(2);
+    c->tma_err = cv.take<int>(4);
     c->gn = cv.take<GnState>(1);
-    c->gnrep = cv.take<double>(8 * kGnRows);
+    c->gnrep = cv.take<double>(RG_REPORT_COLS * kGnRows);
+    c->range_terms = cv.take<double>(8);
 }
 
 static void derive(rg_ctx *c) {
@@ -269,6 +301,21 @@ static void derive(rg_ctx *c) {
         if (n > c->nA_cap) c->nA_cap = n;
         if (n * 3 * t.box > c->boxA_cap) c->boxA_cap = n * 3 * t.box;
     }
+    col_geom(&c->img, &c->grid, c->cg);
+    {
+        const long n = (long)c->cg.nb[0] * c->cg.nb[1] * 3 * c->cg.box;
+        if (n > c->boxA_cap) c->boxA_cap = n;
+    }
+    c->bM.m[0] = c->grid.m[0];
+    c->bM.m[1] = c->grid.m[1];
+    c->bM.m[2] = c->grid.m[2];
+    c->bM.nb[0] = c->cg.nb[0];
+    c->bM.nb[1] = c->cg.nb[1];
+    c->bM.nb[2] = 1;
+    c->bM.C[0] = c->cg.C0;
+    c->bM.C[1] = c->cg.C1;
+    c->bM.C[2] = c->grid.m[2] - 1;
+    c->bM.box = c->cg.box;
     tile_geom(&c->img, &c->grid, c->tg, 16);
     c->nA = c->tg.nb[0] * c->tg.nb[1] * c->tg.nb[2];
     for (int a = 0; a < 3; ++a) {
@@ -331,6 +378,12 @@ extern "C" int rg_ctx_create(rg_ctx **out, const rg_image_geom *img, const rg_gr
                  encode_field_map(&c->map_a, c->tg.n, c->tg.TY, c->lin_a))
                     ? 1
                     : 0;
+    c->cg.tma = (encode_field_map(&c->map_col_dT, c->cg.n, 16, c->lin_dT, kColBoxX) &&
+                 encode_field_map(&c->map_col_a, c->cg.n, 16, c->lin_a, kColBoxX))
+                    ? 1
+                    : 0;
+    c->bcur = &c->bA;
+    c->hook_poll = 1 << 20;
     c->ev_pool = new std::vector<cudaEvent_t>();
     c->ev_used = new std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>();
     *out = c;
@@ -453,7 +506,7 @@ extern "C" int rg_set_keypoints(rg_ctx *c, int32_t nk, const float *x, const flo
 static int run_tile(rg_ctx *c, int mode, const float *field) {
     if (!c->R || !c->T) return set_err(c, RG_EINVAL, "images not set");
     if (!c->err_zeroed) {
-        CK(cudaMemsetAsync(c->tma_err, 0, 2 * sizeof(int), c->st));
+        CK(cudaMemsetAsync(c->tma_err, 0, 4 * sizeof(int), c->st));
         c->err_zeroed = true;
     }
     auto fill = [&](auto &a) {
@@ -469,8 +522,27 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
         a.map_a = c->map_a;
         a.err = c->tma_err;
         a.skip = c->skip;
+        a.poll_limit = c->hook_poll;
+        a.no_tma = c->hook_no_tma;
     };
     const int pid = mode == MODE_MATVEC ? 0 : (mode == MODE_OBJ ? 2 : (mode == MODE_DIAG ? 10 : 1));
+    c->bcur = &c->bA;
+    if ((mode == MODE_MATVEC || mode == MODE_DIAG) && !c->general_only && gn_product_supported(c->cg)) {
+        // the column-marching kernel (node boxes per column of the volume)
+        ColArgs a;
+        a.g = c->cg;
+        a.v = field;
+        a.boxes = c->boxA;
+        a.map_dT = c->map_col_dT;
+        a.map_a = c->map_col_a;
+        a.err = c->tma_err;
+        a.skip = c->skip;
+        a.poll_limit = c->hook_poll;
+        a.no_tma = c->hook_no_tma;
+        LAUNCH(pid, launch_gn_product(a, mode == MODE_DIAG, c->st));
+        c->bcur = &c->bM;
+        return RG_OK;
+    }
     if ((mode == MODE_MATVEC || mode == MODE_DIAG) && !c->general_only && gn_matvec_supported(c->tg)) {
         // the GN product and its diagonal read only the stored linearisation, not the images
         TileArgs<float> a;
@@ -533,7 +605,7 @@ static int run_nodes(rg_ctx *c, const float *v, bool energy, float *out, double 
         a.ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
     }
     a.boxA = useA ? c->boxA : nullptr;
-    a.gA = c->bA;
+    a.gA = *c->bcur;
     a.sA = (float)sA;
     a.boxB = useB ? c->boxB : nullptr;
     a.gB = c->bB;
@@ -569,7 +641,7 @@ static int run_kp(rg_ctx *c, const float *u, const float *v, double scale, float
     return RG_OK;
 }
 
-static int run_terms(rg_ctx *c, double *terms, bool useD, bool useR, bool useV, bool useK) {
+static int run_terms(rg_ctx *c, double *terms, bool useD, bool useR, bool useV, bool useK, bool latch = true) {
     TermsArgs t;
     t.dpart = useD ? c->dpart : nullptr;
     t.nd = c->nA;
@@ -590,9 +662,18 @@ static int run_terms(rg_ctx *c, double *terms, bool useD, bool useR, bool useV, 
     t.dmax = c->dmax;
     t.dminmax = c->dminmax;
     t.terms = terms;
+    t.nonfinite = latch ? c->tma_err + 2 : nullptr;
     t.skip = c->skip;
     LAUNCH(8, launch_terms(t, c->st));
     return RG_OK;
+}
+
+// The extremes of the Jacobian bounds d of Eq. (8) at u into dminmax (a
+// volume-term pass of its own, for when the objective does not evaluate it).
+static int run_range(rg_ctx *c, const float *u) {
+    int st;
+    if ((st = run_vcc(c, u, nullptr))) return st;
+    return run_terms(c, c->range_terms, false, false, true, false, false);
 }
 
 // Objective (and gradient) of Eq. (11).
@@ -731,7 +812,7 @@ static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
     int st;
     if ((st = ensure_minv(c))) return st;
     if (!c->err_zeroed) {
-        CK(cudaMemsetAsync(c->tma_err, 0, 2 * sizeof(int), c->st));
+        CK(cudaMemsetAsync(c->tma_err, 0, 4 * sizeof(int), c->st));
         c->err_zeroed = true;
     }
     PcgArgs a;
@@ -770,9 +851,10 @@ extern "C" int gn_pcg_solve(rg_ctx *c, const float *g, float *p, int32_t iters, 
     return pcg(c, g, p, iters, stats);
 }
 
-static int read_terms(rg_ctx *c, double *terms_dev, double *host5) {
+static int read_terms(rg_ctx *c, double *terms_dev, double *host5, double *dm2 = nullptr) {
     int err = 0;
     CK(cudaMemcpyAsync(host5, terms_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (dm2) CK(cudaMemcpyAsync(dm2, c->dminmax, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(&err, c->tma_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     if (err) return set_err(c, RG_ETIMEOUT, "a kernel gave up waiting for a TMA transfer");
@@ -814,7 +896,7 @@ static int gn_iteration_device(rg_ctx *c, float *u, const rg_schedule *s) {
     int st;
     const long n = 3 * c->M;
     if ((st = evaluate(c, u, c->terms_tmp, c->tg_, true))) return st;
-    LAUNCH(9, launch_gn_begin(c->gn, c->terms_tmp, c->st));
+    LAUNCH(9, launch_gn_begin(c->gn, c->terms_tmp, c->dminmax, c->st));
     if ((st = pcg(c, c->tg_, c->ts, s->pcg_iters, c->terms_tmp + 5))) return st;
     LAUNCH(9, launch_dot(n, c->tg_, c->ts, c->vecpart, c->st));
     LAUNCH(9, launch_gn_slope(c->gn, c->vecpart, vec_blocks(n), c->st));
@@ -824,12 +906,16 @@ static int gn_iteration_device(rg_ctx *c, float *u, const rg_schedule *s) {
         for (int k = 0; k <= s->ls_max; ++k) {
             LAUNCH(9, launch_axpy_copy(n, (float)t, u, c->ts, c->tu, c->st, c->skip));
             if ((st = evaluate(c, c->tu, c->terms_tmp, nullptr, false))) return st;
-            LAUNCH(9, launch_gn_armijo(c->gn, c->terms_tmp, t, s->armijo_c, c->st));
+            LAUNCH(9, launch_gn_armijo(c->gn, c->terms_tmp, c->dminmax, t, s->armijo_c, c->st));
             t *= 0.5;
         }
     }
     LAUNCH(9, launch_gn_accept(c->gn, n, c->tu, u, c->st));
-    LAUNCH(9, launch_gn_report(c->gn, c->terms_tmp + 5, c->gnrep, kGnRows, c->st));
+    if (c->P.gamma == 0.0) {   // the objective left the volume term out: a range pass at the new iterate
+        if ((st = run_range(c, u))) return st;
+        LAUNCH(9, launch_gn_range(c->gn, c->dminmax, c->st));
+    }
+    LAUNCH(9, launch_gn_report(c->gn, c->terms_tmp + 5, c->gnrep, kGnRows, c->P.det_lo, c->P.det_hi, c->st));
     return RG_OK;
 }
 
@@ -838,7 +924,7 @@ static int gn_iteration_device(rg_ctx *c, float *u, const rg_schedule *s) {
 // change between iterations)
 static int gn_run_device(rg_ctx *c, float *u, const rg_schedule *s, bool graph) {
     if (!c->err_zeroed) {
-        CK(cudaMemsetAsync(c->tma_err, 0, 2 * sizeof(int), c->st));
+        CK(cudaMemsetAsync(c->tma_err, 0, 4 * sizeof(int), c->st));
         c->err_zeroed = true;
     }
     CK(cudaMemsetAsync(c->gn, 0, sizeof(GnState), c->st));
@@ -914,7 +1000,7 @@ static int gn_solve_device(rg_ctx *c, float *u, const rg_schedule *s, double *re
     CK(cudaStreamWaitEvent(user, c->gev[1], 0));
     if (st) return st;
     GnState hs;
-    std::vector<double> rows(8 * (size_t)s->gn_iters);
+    std::vector<double> rows(RG_REPORT_COLS * (size_t)s->gn_iters);
     int err = 0;
     CK(cudaMemcpyAsync(&hs, c->gn, sizeof hs, cudaMemcpyDeviceToHost, c->gst));
     CK(cudaMemcpyAsync(rows.data(), c->gnrep, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost, c->gst));
@@ -922,7 +1008,7 @@ static int gn_solve_device(rg_ctx *c, float *u, const rg_schedule *s, double *re
     CK(cudaStreamSynchronize(c->gst));
     if (err) return set_err(c, RG_ETIMEOUT, "a kernel gave up waiting for a TMA transfer");
     const int nrows = hs.halted ? hs.halt_it + 1 : s->gn_iters;
-    if (report) memcpy(report, rows.data(), sizeof(double) * 8 * (size_t)nrows);
+    if (report) memcpy(report, rows.data(), sizeof(double) * RG_REPORT_COLS * (size_t)nrows);
     if (hs.halted)
         return hs.status == RG_EFOLD ? set_err(c, RG_EFOLD, "gn_solve: fold at the current iterate")
                                      : set_err(c, RG_ENONFINITE, "gn_solve: non-finite objective");
@@ -936,11 +1022,13 @@ static int gn_solve_impl(rg_ctx *c, float *u, const rg_schedule *s, double *repo
     if ((s->flags & (RG_SCHED_DEVICE | RG_SCHED_GRAPH)) && s->gn_iters > 0 && s->gn_iters <= kGnRows && !c->prof)
         return gn_solve_device(c, u, s, report, (s->flags & RG_SCHED_GRAPH) != 0);
     const long n = 3 * c->M;
-    double h5[5], slope;
+    double h5[5], slope, dm0[2], dm[2];
     for (int it = 0; it < s->gn_iters; ++it) {
-        double *rep = report ? report + 8 * it : nullptr;
+        double *rep = report ? report + RG_REPORT_COLS * it : nullptr;
+        if (rep)
+            for (int k = 0; k < RG_REPORT_COLS; ++k) rep[k] = 0.0;
         if ((st = evaluate(c, u, c->terms_tmp, c->tg_, true))) return st;
-        if ((st = read_terms(c, c->terms_tmp, h5))) return st;
+        if ((st = read_terms(c, c->terms_tmp, h5, dm0))) return st;
         const double J0 = h5[4];
         if (!isfinite(J0)) {
             if (rep) { rep[0] = it; rep[1] = J0; rep[7] = isinf(J0) ? RG_EFOLD : RG_ENONFINITE; }
@@ -965,18 +1053,27 @@ static int gn_solve_impl(rg_ctx *c, float *u, const rg_schedule *s, double *repo
         for (int k = 0; k <= s->ls_max; ++k) {
             LAUNCH(9, launch_axpy_copy(n, (float)t, u, c->ts, c->tu, c->st));
             if ((st = evaluate(c, c->tu, c->terms_tmp, nullptr, false))) return st;
-            if ((st = read_terms(c, c->terms_tmp, h5))) return st;
+            if ((st = read_terms(c, c->terms_tmp, h5, dm))) return st;
             ++evals;
             if (isfinite(h5[4]) && h5[4] <= std::fma(s->armijo_c * t, slope, J0)) {
                 acc_t = t;
                 Jn = h5[4];
+                dm0[0] = dm[0];
+                dm0[1] = dm[1];
                 break;
             }
             t *= 0.5;
         }
         if (acc_t > 0.0) CK(cudaMemcpyAsync(u, c->tu, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->st));
         if (rep) {
+            if (c->P.gamma == 0.0) {   // the objective left the volume term out: a range pass at the new iterate
+                if ((st = run_range(c, u))) return st;
+                CK(cudaMemcpyAsync(dm0, c->dminmax, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+                CK(cudaStreamSynchronize(c->st));
+            }
             rep[0] = it; rep[1] = J0; rep[2] = slope; rep[3] = acc_t; rep[4] = Jn; rep[5] = evals; rep[7] = 0;
+            rep[8] = dm0[0]; rep[9] = dm0[1];
+            rep[10] = (dm0[0] >= c->P.det_lo && dm0[1] <= c->P.det_hi) ? 1.0 : 0.0;
         }
     }
     CK(cudaStreamSynchronize(c->st));
@@ -1172,7 +1269,7 @@ extern "C" int register_pyramid(const rg_image_geom *img, const void *R, const v
         if (e != RG_OK) return e;
         rg_set_images(cl, Rl[l], Tl[l]);
         if (nk > 0) rg_set_keypoints(cl, nk, kx, ky);
-        status = gn_solve_impl(cl, ul[l], s, report ? report + (long)(Lc - l) * s->gn_iters * 8 : nullptr,
+        status = gn_solve_impl(cl, ul[l], s, report ? report + (long)(Lc - l) * s->gn_iters * RG_REPORT_COLS : nullptr,
                                P.delta_adaptive != 0 && l == Lc);
         P.delta = cl->P.delta;
         rg_ctx_destroy(cl);
@@ -1297,25 +1394,34 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
             g_launches.fetch_add(1, std::memory_order_relaxed);
         }
     }
-    std::vector<double> rows(8 * (size_t)s->gn_iters);
+    // pairs whose schedule halted (fold or non-finite objective) leave the batch
+    std::vector<int> halted(npairs, 0);
+    if (report) memset(report, 0, sizeof(double) * (size_t)npairs * levels * s->gn_iters * RG_REPORT_COLS);
+    std::vector<double> rows(RG_REPORT_COLS * (size_t)s->gn_iters);
     for (int l = Lc; l >= 0 && status == RG_OK; --l) {
         // this level's contexts (delta adapted on the host at the coarsest level)
+        int nact = 0;
         for (int p = 0; p < npairs && status == RG_OK; ++p) {
+            if (halted[p]) continue;
+            ++nact;
             Pair &q = ps[p];
-            size_t w;
-            rg_workspace_size(&q.il[l], &q.gl[l], dtype, 0, s->pcg_iters, &w);
+            size_t w = 0;
+            if (rg_workspace_size(&q.il[l], &q.gl[l], dtype, 0, s->pcg_iters, &w) != RG_OK) {
+                status = RG_EINVAL;
+                break;
+            }
             void *wl = q.take(w);
             status = rg_ctx_create(&q.cl, &q.il[l], &q.gl[l], dtype, &q.P, 0, s->pcg_iters, wl, w, (void *)st);
             if (status) break;
             rg_set_images(q.cl, q.Rl[l], q.Tl[l]);
             if (q.P.delta_adaptive && l == Lc) status = set_delta_adaptive(q.cl, q.ul[l]);
             if (!status) status = ensure_private_stream(q.cl);
-            if (!status && cudaMemsetAsync(q.cl->tma_err, 0, 2 * sizeof(int), st) != cudaSuccess) status = RG_ECUDA;
+            if (!status && cudaMemsetAsync(q.cl->tma_err, 0, 4 * sizeof(int), st) != cudaSuccess) status = RG_ECUDA;
             if (!status && cudaMemsetAsync(q.cl->gn, 0, sizeof(GnState), st) != cudaSuccess) status = RG_ECUDA;
             q.cl->err_zeroed = true;
         }
-        if (status) break;
-        // one graph: every pair's iteration as a branch forked from st
+        if (status || nact == 0) break;
+        // one graph: every active pair's iteration as a branch forked from st
         long long counted = 0;
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
@@ -1324,6 +1430,7 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
         }
         int cst = cudaEventRecord(fork, st) == cudaSuccess ? RG_OK : RG_ECUDA;
         for (int p = 0; p < npairs && cst == RG_OK; ++p) {
+            if (halted[p]) continue;
             rg_ctx *cl = ps[p].cl;
             if (cudaStreamWaitEvent(cl->gst, fork, 0) != cudaSuccess) {
                 cst = RG_ECUDA;
@@ -1366,6 +1473,7 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
         std::vector<double> rep((size_t)npairs * rows.size());
         std::vector<int> err(npairs, 0);
         for (int p = 0; p < npairs && status == RG_OK; ++p) {
+            if (halted[p]) continue;
             rg_ctx *cl = ps[p].cl;
             if (cudaMemcpyAsync(&hs[p], cl->gn, sizeof(GnState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaMemcpyAsync(rep.data() + (size_t)p * rows.size(), cl->gnrep, sizeof(double) * rows.size(),
@@ -1375,29 +1483,42 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
         }
         if (!status && cudaStreamSynchronize(st) != cudaSuccess) status = RG_ECUDA;
         for (int p = 0; p < npairs && status == RG_OK; ++p) {
-            if (err[p]) status = RG_ETIMEOUT;
+            if (halted[p]) continue;
+            if (err[p]) {
+                status = RG_ETIMEOUT;
+                break;
+            }
             const int nrows = hs[p].halted ? hs[p].halt_it + 1 : s->gn_iters;
             if (report)
-                memcpy(report + ((size_t)p * levels + (Lc - l)) * s->gn_iters * 8, rep.data() + (size_t)p * rows.size(),
-                       sizeof(double) * 8 * (size_t)nrows);
-            if (hs[p].halted && !status) status = hs[p].status;
+                memcpy(report + ((size_t)p * levels + (Lc - l)) * s->gn_iters * RG_REPORT_COLS,
+                       rep.data() + (size_t)p * rows.size(), sizeof(double) * RG_REPORT_COLS * (size_t)nrows);
+            if (hs[p].halted) halted[p] = hs[p].status != 0 ? hs[p].status : RG_ENONFINITE;
         }
         for (int p = 0; p < npairs; ++p) {
             Pair &q = ps[p];
+            if (!q.cl) continue;
             q.P.delta = q.cl->P.delta;
             rg_ctx_destroy(q.cl);
             q.cl = nullptr;
-            if (!status && l > 0 && launch_prolong_grid(q.gl[l].m, q.ul[l], q.ul[l - 1], st) != cudaSuccess)
-                status = RG_ECUDA;
-            if (!status && l > 0) g_launches.fetch_add(1, std::memory_order_relaxed);
+            if (!status && !halted[p] && l > 0) {
+                if (launch_prolong_grid(q.gl[l].m, q.ul[l], q.ul[l - 1], st) != cudaSuccess) status = RG_ECUDA;
+                else g_launches.fetch_add(1, std::memory_order_relaxed);
+            }
         }
     }
     for (int p = 0; p < npairs && status == RG_OK; ++p) {
+        if (halted[p]) continue;   // keeps its start value
         const long Mf = (long)fin[p].m[0] * fin[p].m[1] * fin[p].m[2];
         if (cudaMemcpyAsync(u_inout[p], ps[p].ul[0], sizeof(float) * 3 * Mf, cudaMemcpyDeviceToDevice, st) !=
             cudaSuccess)
             status = RG_ECUDA;
     }
+    if (status == RG_OK)
+        for (int p = 0; p < npairs; ++p)
+            if (halted[p]) {
+                status = halted[p];
+                break;
+            }
     if (cudaStreamSynchronize(st) != cudaSuccess && !status) status = RG_ECUDA;
     release();
     return status;
@@ -1414,6 +1535,28 @@ extern "C" int rg_prolong_grid(const int32_t *mc, const float *uc, float *uf, vo
     if (!mc || !uc || !uf) return RG_EINVAL;
     rg_ctx *c = nullptr;
     LAUNCH(10, launch_prolong_grid(mc, uc, uf, (cudaStream_t)stream));
+    return RG_OK;
+}
+
+extern "C" int rg_sync(rg_ctx *c) {
+    if (!c) return RG_EINVAL;
+    CK(cudaStreamSynchronize(c->st));
+    if (!c->err_zeroed) return RG_OK;   // nothing launched yet
+    int f[4] = {0, 0, 0, 0};
+    CK(cudaMemcpy(f, c->tma_err, sizeof f, cudaMemcpyDeviceToHost));
+    if (!f[0] && !f[2]) return RG_OK;
+    CK(cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->st));
+    CK(cudaMemsetAsync(c->tma_err + 2, 0, sizeof(int), c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (f[0]) return set_err(c, RG_ETIMEOUT, "a kernel gave up waiting for a TMA transfer");
+    return set_err(c, RG_ENONFINITE, "an objective evaluated since the last check was not finite (NaN or Inf in the inputs)");
+}
+
+extern "C" int rg_debug_hook(rg_ctx *c, int32_t what, int32_t value) {
+    if (!c) return RG_EINVAL;
+    if (what == RG_HOOK_NO_TMA) c->hook_no_tma = value != 0;
+    else if (what == RG_HOOK_POLL_LIMIT && value > 0) c->hook_poll = value;
+    else return set_err(c, RG_EINVAL, "rg_debug_hook: unknown hook %d or bad value %d", what, value);
     return RG_OK;
 }
 

@@ -84,9 +84,9 @@ struct TileArgs {
     const TImg *T;          // template image
     const float *u;         // node field interpolated per voxel (u, or v for the matvec)
     const float *lin_dT;    // stored dT/dy [3][N] (matvec input)
-    const float *lin_a;     // stored dr/dg [3][N] (matvec input)
+    const float *lin_a;     // stored dr/dg [3][N], component a scaled by 1 / (2 h_a) (matvec input)
     float *st_dT;           // linearisation output dT/dy [3][N]
-    float *st_a;            // linearisation output dr/dg [3][N]
+    float *st_a;            // linearisation output dr/dg [3][N], component a scaled by 1 / (2 h_a)
     float *boxes;           // per-CTA node partials [cta][3][C2+1][C1+1][C0+1]
     double *dpart;          // per-CTA partial sums of (1 - r^2)
     // Stored linearisation streamed by TMA (GN product and diagonal): tensor
@@ -95,10 +95,43 @@ struct TileArgs {
     CUtensorMap map_dT, map_a;
     int *err;               // set to 1 if a bounded wait on a TMA barrier gave up
     const int *skip = nullptr;   // nonzero: the launch does nothing (a line-search try after acceptance)
+    int poll_limit = 1 << 20;    // polls of a TMA barrier before a wait gives up
+    int no_tma = 0;         // test hook: issue no TMA copy (every wait runs out)
 };
 
 constexpr int kTmaBoxX = 36;      // floats per TMA box row: tile columns x0-4 .. x0+31
 constexpr int kTmaStages = 5;     // planes in flight: 3 ahead of the one being used
+
+// Column geometry of the column-marching GN-product kernel (gn_product.cu):
+// a CTA owns TXI x 16 voxel columns in x-y and marches every z plane; lane L
+// holds the x columns x0 - 2 + 2L and x0 - 1 + 2L.
+constexpr int kColBoxX = 68;      // floats per TMA box row: columns x0-4 .. x0+63
+struct ColGeom {
+    int n[3];          // voxels
+    int m[3];          // nodes
+    int rho[3];        // n / (m - 1)
+    int lrho[3];       // log2(rho)
+    float irho[3];     // 1 / rho
+    float inv2h[3];    // 1 / (2 h)
+    int TXI;           // owned voxel columns per tile along x (60 - 60 % rho_x)
+    int nb[2];         // tiles along x, y
+    int C0, C1;        // cells per tile along x, y
+    int nxt, nyt;      // node-plane extent read by a tile's prolongation
+    int box;           // floats per component of a column's node box: (C0 + 1)(C1 + 1) m3
+    int tma;           // 1: tensor maps valid
+};
+
+struct ColArgs {
+    ColGeom g;
+    const float *v;         // node field to prolongate (GN product)
+    float *boxes;           // per-column node boxes [column][3][m3][C1 + 1][C0 + 1]
+    CUtensorMap map_dT, map_a;   // stored dT/dy, a as {x, y, z, component}, box {68, 20, 1, 3}
+    int *err;               // set to 1 if a bounded wait on a TMA barrier gave up
+    const int *skip = nullptr;
+    int chain = 0;          // set by the launcher: CTAs walk several columns
+    int poll_limit = 1 << 20;    // polls of a TMA barrier before a wait gives up
+    int no_tma = 0;         // test hook: issue no TMA copy (every wait runs out)
+};
 
 // Node-box finaliser: out[c][k] = scale * sum over the CTA boxes holding k.
 struct BoxGeom {

@@ -22,6 +22,9 @@ bool ngf_grad_supported(const TileGeom &g);
 cudaError_t launch_ngf_grad(int mode, const TileArgs<float> &a, cudaStream_t st);
 cudaError_t launch_ngf_grad(int mode, const TileArgs<__half> &a, cudaStream_t st);
 cudaError_t launch_gn_matvec(const TileArgs<float> &a, bool diag, cudaStream_t st);
+// Column-marching GN product / diagonal (packed FP32, two x columns per lane).
+bool gn_product_supported(const ColGeom &g);
+cudaError_t launch_gn_product(const ColArgs &a, bool diag, cudaStream_t st);
 
 // Volume change control, Eqs. (7)-(9): per grid cell the 64 bounds d_abc.
 struct VccArgs {
@@ -88,6 +91,7 @@ struct TermsArgs {
     const float *dmin, *dmax; double *dminmax;
     double *terms;         // [5]
     const int *skip = nullptr;   // nonzero: the launch does nothing
+    int *nonfinite = nullptr;    // set to 1 when J is NaN, or +inf without a fold
 };
 cudaError_t launch_terms(const TermsArgs &a, cudaStream_t st);
 
@@ -134,6 +138,7 @@ cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, fl
 // Device side of one Gauss-Newton iteration (line search without host reads).
 struct GnState {
     double J0, Jn, slope, acc_t;
+    double dmin, dmax;   // extremes of the Jacobian bounds d at the iterate after the step
     int done;      // the line search has finished (or the schedule halted): later tries skip
     int evals;     // objective evaluations of the line search
     int halted;    // a non-finite objective stopped the schedule
@@ -142,11 +147,15 @@ struct GnState {
     int it;        // iterations run (report row index)
 };
 constexpr int kGnRows = 256;   // report rows the workspace keeps for device-driven schedules
-cudaError_t launch_gn_begin(GnState *s, const double *terms, cudaStream_t st);
+// dminmax: the {min d, max d} the objective's terms kernel wrote for the same evaluation
+cudaError_t launch_gn_begin(GnState *s, const double *terms, const double *dminmax, cudaStream_t st);
 cudaError_t launch_gn_slope(GnState *s, const double *part, int nparts, cudaStream_t st);
-cudaError_t launch_gn_armijo(GnState *s, const double *terms, double t, double c, cudaStream_t st);
+cudaError_t launch_gn_armijo(GnState *s, const double *terms, const double *dminmax, double t, double c,
+                             cudaStream_t st);
 cudaError_t launch_gn_accept(const GnState *s, long n, const float *tu, float *u, cudaStream_t st);
-cudaError_t launch_gn_report(GnState *s, const double *pcg_stats, double *rep, int rows, cudaStream_t st);
+cudaError_t launch_gn_range(GnState *s, const double *dminmax, cudaStream_t st);   // d range at the new iterate
+cudaError_t launch_gn_report(GnState *s, const double *pcg_stats, double *rep, int rows, double det_lo, double det_hi,
+                             cudaStream_t st);
 
 // Pyramid.
 cudaError_t launch_restrict(const int *n, bool half, const void *in, void *out, cudaStream_t st);

@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(kNT, 1) ngf_grad_kernel(const __grid_constant_
                         if (STORE && own && colin && pC >= 0) {
                             const float inv = interior ? rsqrtf(ff * gg) * rgg : 0.f;
                             const int v = pC * sxy + col;
-                            a.st_a[v] = q0 * inv;
-                            a.st_a[N + v] = q1 * inv;
-                            a.st_a[2 * N + v] = q2 * inv;
+                            a.st_a[v] = q0 * inv * i2h0;   // a = dr/dg, stored with the scale 1 / (2 h)
+                            a.st_a[N + v] = q1 * inv * i2h1;
+                            a.st_a[2 * N + v] = q2 * inv * i2h2;
                         }
                     }
                 }

@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(32 * (TY + 4), TY == 8 ? 2 : 1) ngf_tile_kerne
     auto issue_plane = [&](int j) {
         uint64_t *bar = &bars[j % kTmaStages];
         const int p = z0 - M::HZ + j;
+        if (a.no_tma) return;   // test hook: the waits run out instead
         if (p >= 0 && p < nz) {
             float *st = tma_base + (j % kTmaStages) * S.tma_stage;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(32 * (TY + 4), TY == 8 ? 2 : 1) ngf_tile_kerne
             // reader, stage C of step s - 1, is behind this step's barriers),
             // then wait for plane s
             if (tid == 0 && s + kTmaStages - 2 < nsteps) issue_plane(s + kTmaStages - 2);
-            mbar_wait_bounded(&bars[stage], phase, a.err);
+            mbar_wait_bounded(&bars[stage], phase, a.err, a.poll_limit);
             const float *st = tma_base + stage * S.tma_stage;
             if (colin && zW) {
                 dn[0] = st[o]; dn[1] = st[NW * kTmaBoxX + o]; dn[2] = st[2 * NW * kTmaBoxX + o];
@@ -405,9 +406,8 @@ __global__ void __launch_bounds__(32 * (TY + 4), TY == 8 ? 2 : 1) ngf_tile_kerne
             __syncthreads();
             const float q0l = __shfl_up_sync(FULL, q0_1, 1), q0r = __shfl_down_sync(FULL, q0_1, 1);
             if (pA >= z0 && pA < z0 + TZc && inA && colin) {
-                const float b = (q0l + q0r) * (g.inv2h[0] * g.inv2h[0]) +
-                                (e1[(w - 1) * 32 + L] + e1[(w + 1) * 32 + L]) * (g.inv2h[1] * g.inv2h[1]) +
-                                (q2_2 + qn[2]) * (g.inv2h[2] * g.inv2h[2]);
+                // the stored a carries the central-difference scale 1 / (2 h) per axis
+                const float b = (q0l + q0r) + (e1[(w - 1) * 32 + L] + e1[(w + 1) * 32 + L]) + (q2_2 + qn[2]);
                 zz[0] = b * d_1[0] * d_1[0];
                 zz[1] = b * d_1[1] * d_1[1];
                 zz[2] = b * d_1[2] * d_1[2];
@@ -429,13 +429,14 @@ __global__ void __launch_bounds__(32 * (TY + 4), TY == 8 ? 2 : 1) ngf_tile_kerne
                 const bool interior = intxy && pC >= 1 && pC <= nz - 2;
                 const bool own = inA && pC >= z0 && pC < z0 + TZc;
                 if (interior) {
-                    const float g0 = (tr - tl) * g.inv2h[0];
-                    const float g1 = (e1[(w + 1) * 32 + L] - e1[(w - 1) * 32 + L]) * g.inv2h[1];
-                    const float g2 = (t_p - t_m) * g.inv2h[2];
+                    const float dt0 = tr - tl, dt1 = e1[(w + 1) * 32 + L] - e1[(w - 1) * 32 + L], dt2 = t_p - t_m;
                     if (M::matvec) {
-                        const float dr = 2.f * (acur[0] * g0 + acur[1] * g1 + acur[2] * g2);
+                        // the stored a' = a / (2 h) per axis: a . G t = a' . (plain differences),
+                        // and c' = (2 a . G t) a' carries the adjoint's 1 / (2 h)
+                        const float dr = 2.f * (acur[0] * dt0 + acur[1] * dt1 + acur[2] * dt2);
                         cc[0] = dr * acur[0]; cc[1] = dr * acur[1]; cc[2] = dr * acur[2];
                     } else {
+                        const float g0 = dt0 * g.inv2h[0], g1 = dt1 * g.inv2h[1], g2 = dt2 * g.inv2h[2];
                         const float *e2 = ex2 + (s & 1) * NW * 32;
                         const float f0 = (rr - rl) * g.inv2h[0];
                         const float f1 = (e2[(w + 1) * 32 + L] - e2[(w - 1) * 32 + L]) * g.inv2h[1];
@@ -462,11 +463,12 @@ __global__ void __launch_bounds__(32 * (TY + 4), TY == 8 ? 2 : 1) ngf_tile_kerne
                             cc[0] = sc * q0; cc[1] = sc * q1; cc[2] = sc * q2;
                         }
                         if (M::store && own) {
+                            // a = dr/dg, stored with the central-difference scale 1 / (2 h) per axis
                             const float inv = rsqrtf(ff * gg) * rgg;
                             const long v = (long)pC * sxy + col;
-                            a.st_a[v] = q0 * inv;
-                            a.st_a[N + v] = q1 * inv;
-                            a.st_a[2 * N + v] = q2 * inv;
+                            a.st_a[v] = q0 * inv * g.inv2h[0];
+                            a.st_a[N + v] = q1 * inv * g.inv2h[1];
+                            a.st_a[2 * N + v] = q2 * inv * g.inv2h[2];
                         }
                     }
                 } else if (M::store && own && colin) {
@@ -484,8 +486,11 @@ __global__ void __launch_bounds__(32 * (TY + 4), TY == 8 ? 2 : 1) ngf_tile_kerne
             // ------------------------------------------ stage A: plane pA
             const float cxl_ = __shfl_up_sync(FULL, cx_p, 1), cxr_ = __shfl_down_sync(FULL, cx_p, 1);
             if (pA >= z0 && pA < z0 + TZc && inA && colin) {
-                const float b = (cxl_ - cxr_) * g.inv2h[0] + (e3[(w - 1) * 32 + L] - e3[(w + 1) * 32 + L]) * g.inv2h[1] +
-                                (cz_mm - cc[2]) * g.inv2h[2];
+                // (the GN product's c' already carries 1 / (2 h))
+                const float s0 = M::matvec ? 1.f : g.inv2h[0], s1 = M::matvec ? 1.f : g.inv2h[1];
+                const float s2 = M::matvec ? 1.f : g.inv2h[2];
+                const float b = (cxl_ - cxr_) * s0 + (e3[(w - 1) * 32 + L] - e3[(w + 1) * 32 + L]) * s1 +
+                                (cz_mm - cc[2]) * s2;
                 zz[0] = b * d_2[0];
                 zz[1] = b * d_2[1];
                 zz[2] = b * d_2[2];

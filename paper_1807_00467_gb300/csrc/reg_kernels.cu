@@ -395,6 +395,7 @@ __global__ void terms_kernel(const TermsArgs a) {
     if (threadIdx.x == 0) {
         double J = D + a.alpha * R + a.gamma * V + a.delta * K;
         if (sfold) { J = INFINITY; V = INFINITY; }
+        else if (a.nonfinite && !isfinite(J)) atomicExch(a.nonfinite, 1);
         a.terms[0] = D; a.terms[1] = R; a.terms[2] = V; a.terms[3] = K; a.terms[4] = J;
         if (a.dminmax) { a.dminmax[0] = a.vpart ? smn : 1.0; a.dminmax[1] = a.vpart ? smx : 1.0; }
     }

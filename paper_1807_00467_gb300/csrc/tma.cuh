@@ -32,9 +32,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
 
 // Bounded wait for a TMA plane: gives up after a fixed number of polls and
 // raises the error flag (when given) instead of hanging.
-__device__ __forceinline__ void mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err) {
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err, int limit = 1 << 20) {
     for (int it = 0; !mbar_try_wait(bar, phase); ++it) {
-        if (it > (1 << 20)) {
+        if (it > limit) {
             if (err) atomicExch(err, 1);
             break;
         }

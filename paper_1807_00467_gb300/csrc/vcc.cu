@@ -34,6 +34,11 @@ __device__ __forceinline__ void axpy(float w, const V3 &x, V3 &y) {
 }
 __device__ __forceinline__ void add(const V3 &x, V3 &y) { y.x += x.x; y.y += x.y; y.z += x.z; }
 
+// Packed FP32 (two lanes of f32x2: the bounds of two x-edges a = 2p, 2p + 1)
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
 // corner offset (ox + 2 oy + 4 oz) of edge e = p + 2 q of axis `ax` at end `hi`;
 // p, q are the offsets along the other two axes in increasing axis order
 __host__ __device__ constexpr int corner_of(int ax, int e, int hi) {
@@ -118,40 +123,80 @@ __global__ void __launch_bounds__(NC, VM == 1 ? 4 : 5) vcc_cell_kernel(const Vcc
     int fold = 0;
     float dmn = 3.4e38f, dmx = -3.4e38f;
     Kahan32 en;
+    if constexpr (GN) {
+        // the x-edges in pairs (a = 2p, 2p + 1), one f32x2 lane each
+        float2 e1x[2], e1y[2], e1z[2], d1x[2], d1y[2], d1z[2], g1x[2], g1y[2], g1z[2];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+        for (int p = 0; p < 2; ++p) {
+            e1x[p] = make_float2(E1[2 * p].x, E1[2 * p + 1].x);
+            e1y[p] = make_float2(E1[2 * p].y, E1[2 * p + 1].y);
+            e1z[p] = make_float2(E1[2 * p].z, E1[2 * p + 1].z);
+            d1x[p] = make_float2(D1[2 * p].x, D1[2 * p + 1].x);
+            d1y[p] = make_float2(D1[2 * p].y, D1[2 * p + 1].y);
+            d1z[p] = make_float2(D1[2 * p].z, D1[2 * p + 1].z);
+            g1x[p] = g1y[p] = g1z[p] = make_float2(0.f, 0.f);
+        }
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const V3 X = cross(E2[b], E3[c]);
-            V3 Y{0.f, 0.f, 0.f};
-            if (GN) {
-                Y = cross(D2[b], E3[c]);
+        for (int c = 0; c < 4; ++c) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const V3 X = cross(E2[b], E3[c]);
+                V3 Y = cross(D2[b], E3[c]);
                 add(cross(E2[b], D3[c]), Y);
-            }
-            V3 W{0.f, 0.f, 0.f};
+                const float2 Xx = bc2(X.x), Xy = bc2(X.y), Xz = bc2(X.z);
+                float2 wx = make_float2(0.f, 0.f), wy = wx, wz = wx;   // W = sum_a w e1_a, per lane
 #pragma unroll
-            for (int aa = 0; aa < 4; ++aa) {
-                const float d = dot(E1[aa], X);
-                const bool pos = d > 0.f;
-                float w;
-                if (GN) {
-                    const float rd = __fdividef(1.f, d);
-                    const float dd = dot(D1[aa], X) + dot(E1[aa], Y);
-                    w = pos ? 2.f * rd * rd * rd * dd : 0.f;   // psi''(d) (grad d . v)
-                } else {
+                for (int p = 0; p < 2; ++p) {
+                    const float2 d = fma2(e1z[p], Xz, fma2(e1y[p], Xy, mul2(e1x[p], Xx)));
+                    // grad d . v = d1_a . X + e1_a . Y
+                    const float2 dd = fma2(e1z[p], bc2(Y.z), fma2(e1y[p], bc2(Y.y), fma2(e1x[p], bc2(Y.x),
+                                      fma2(d1z[p], Xz, fma2(d1y[p], Xy, mul2(d1x[p], Xx))))));
+                    const float r0 = __fdividef(1.f, d.x), r1 = __fdividef(1.f, d.y);
+                    const float2 r = make_float2(r0, r1);
+                    float2 w = mul2(mul2(mul2(r, r), mul2(r, bc2(2.f))), dd);   // psi''(d) (grad d . v)
+                    w.x = d.x > 0.f ? w.x : 0.f;
+                    w.y = d.y > 0.f ? w.y : 0.f;
+                    g1x[p] = fma2(w, Xx, g1x[p]);
+                    g1y[p] = fma2(w, Xy, g1y[p]);
+                    g1z[p] = fma2(w, Xz, g1z[p]);
+                    wx = fma2(w, e1x[p], wx);
+                    wy = fma2(w, e1y[p], wy);
+                    wz = fma2(w, e1z[p], wz);
+                }
+                const V3 W{wx.x + wx.y, wy.x + wy.y, wz.x + wz.y};
+                add(cross(E3[c], W), G2[b]);
+                add(cross(W, E2[b]), G3[c]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            G1[2 * p] = V3{g1x[p].x, g1y[p].x, g1z[p].x};
+            G1[2 * p + 1] = V3{g1x[p].y, g1y[p].y, g1z[p].y};
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const V3 X = cross(E2[b], E3[c]);
+                V3 W{0.f, 0.f, 0.f};
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa) {
+                    const float d = dot(E1[aa], X);
+                    const bool pos = d > 0.f;
                     dmn = fminf(dmn, d);
                     dmx = fmaxf(dmx, d);
                     fold += pos ? 0 : 1;
                     const float rd = __frcp_rn(d);
                     const float dm = d - 1.f;
                     en.add(pos ? dm * dm * rd : 0.f);               // psi(d) = (d - 1)^2 / d
-                    w = pos ? dm * (d + 1.f) * rd * rd : 0.f;       // psi'(d) = 1 - 1/d^2
+                    const float w = pos ? dm * (d + 1.f) * rd * rd : 0.f;   // psi'(d) = 1 - 1/d^2
+                    axpy(w, X, G1[aa]);
+                    axpy(w, E1[aa], W);
                 }
-                axpy(w, X, G1[aa]);
-                axpy(w, E1[aa], W);
+                add(cross(E3[c], W), G2[b]);
+                add(cross(W, E2[b]), G3[c]);
             }
-            add(cross(E3[c], W), G2[b]);
-            add(cross(W, E2[b]), G3[c]);
         }
     }
     // edge gradients onto the cell's corners (scaled by 1/g of the edge's axis)

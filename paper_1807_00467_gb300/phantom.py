@@ -340,6 +340,27 @@ def lung_mask(n, h):
     return (_ellipsoid(xc, yc, zc, centres[0], semi) | _ellipsoid(xc, yc, zc, centres[1], semi)).astype(np.uint8)
 
 
+def node_regions(n, h, m):
+    """Boolean [mz][my][mx] masks (body, lungs) of the grid nodes whose support
+    (the box of the node's neighbouring cells, [k - 1, k + 1] x node spacing
+    per axis, clipped to the field of view) lies inside the body ellipsoid,
+    resp. inside one lung ellipsoid of the recipe (both sets are convex, so a
+    box is inside when its eight corners are)."""
+    fov = np.asarray(n, dtype=np.float64) * np.asarray(h, dtype=np.float64)
+    g = fov / (np.asarray(m, dtype=np.float64) - 1.0)
+    lo = [np.clip((np.arange(m[a]) - 1.0) * g[a], 0.0, fov[a]) for a in range(3)]
+    hi = [np.clip((np.arange(m[a]) + 1.0) * g[a], 0.0, fov[a]) for a in range(3)]
+    lung_c, lung_s = _lung_geometry(fov)
+    shapes = [(fov / 2.0, np.array([0.46, 0.40, 0.48]) * fov)] + [(c, lung_s) for c in lung_c]
+    inside = [np.ones((m[2], m[1], m[0]), dtype=bool) for _ in shapes]
+    for cx in (lo[0], hi[0]):
+        for cy in (lo[1], hi[1]):
+            for cz in (lo[2], hi[2]):
+                for k, (c, s) in enumerate(shapes):
+                    inside[k] &= _ellipsoid(cx[None, None, :], cy[None, :, None], cz[:, None, None], c, s)
+    return inside[0], inside[1] | inside[2]
+
+
 def _pair_job(job):
     n, h, seed = job
     ph = make_phantom(n, h, seed, motion="large")

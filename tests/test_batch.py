@@ -71,10 +71,40 @@ def test_batched_graph_equals_per_pair_graph_drive():
         pairs = batch.crop_pairs(R, T, ph.h, [(64, 64, 32), (48, 56, 32), (56, 48, 24), (40, 40, 16)])
         params = api.make_params(eta=10.0, alpha=1.0, gamma=0.001)
         sched = dict(levels=2, gn_iters=3, pcg_iters=10)
-        us, reps, sec = batch.register_batch_graph(pairs, params, **sched)
+        us, reps, sec, code = batch.register_batch_graph(pairs, params, **sched)
+        assert code == 0
         for (Rc, Tc, h, m), ub, rb in zip(pairs, us, reps):
             u = torch.zeros((3,) + m[::-1], device="cuda")
             code, rep = api.register_pyramid(Rc, Tc, h, m, u, params, drive="graph", **sched)
             assert code == 0
             np.testing.assert_array_equal(rb, rep)
             assert torch.equal(ub, u)
+
+
+@pytest.mark.gpu
+def test_batched_graph_a_folded_pair_leaves_the_batch():
+    """A pair whose start folds (y_x = -x) halts at its first iteration with
+    RG_EFOLD: its u keeps the start value and its report stops there; the other
+    pairs run to the end with the bits they get on their own."""
+    import torch
+    from paper_1807_00467_gb300 import _lib, api
+    ph = phantom.make_phantom((64, 64, 32), (1.5, 1.5, 3.0), seed=9, motion="small", n_vessels=12)
+    R, T = torch.from_numpy(ph.R).cuda(), torch.from_numpy(ph.T).cuda()
+    pairs = batch.crop_pairs(R, T, ph.h, [(64, 64, 32), (48, 56, 32), (40, 40, 16)])
+    params = api.make_params(eta=10.0, alpha=1.0, gamma=0.001)
+    sched = dict(levels=2, gn_iters=2, pcg_iters=8)
+    u0 = [torch.zeros((3,) + m[::-1]) for _, _, _, m in pairs]
+    m1, h1 = pairs[1][3], pairs[1][2]
+    g1 = pairs[1][0].shape[2] * h1[0] / (m1[0] - 1)
+    u0[1][0] = -2.0 * torch.arange(m1[0], dtype=torch.float32)[None, None, :] * g1
+    us, reps, sec, code = batch.register_batch_graph(pairs, params, u0=u0, **sched)
+    assert code == _lib.RG_EFOLD
+    assert torch.equal(us[1].cpu(), u0[1])
+    assert reps[1][0, 0, 7] == _lib.RG_EFOLD and np.all(reps[1][0, 1:] == 0) and np.all(reps[1][1] == 0)
+    for p in (0, 2):
+        Rc, Tc, h, m = pairs[p]
+        u = torch.zeros((3,) + m[::-1], device="cuda")
+        c, rep = api.register_pyramid(Rc, Tc, h, m, u, params, drive="graph", **sched)
+        assert c == 0
+        np.testing.assert_array_equal(reps[p], rep)
+        assert torch.equal(us[p], u)

@@ -39,11 +39,20 @@ def _assert_same(out):
 
 @pytest.mark.parametrize("gamma", [0.0, 0.001])
 def test_drives_agree_tiny(gamma):
+    """Also the report's Jacobian bounds (Eqs. (8)-(9)): min d and max d at the
+    final iterate against the oracle's 64 bounds per cell at that iterate, and
+    the [0.25, 4] flag (with gamma = 0 the objective leaves the volume term out
+    and a range pass supplies them)."""
+    from helpers import oracle_problem, rel
     ph = get_phantom("tiny", seed=0)
     out = _solve_all(ph, TINY_M, np.zeros((3,) + TINY_M[::-1]), 4, 20, gamma=gamma)
     _assert_same(out)
-    rep = out["host"][1]
+    rep, u = out["host"][1], out["host"][2]
     assert np.all(rep[:, 3] > 0) and np.all(rep[:, 4] <= rep[:, 1])
+    _, _, st, (dmin, dmax) = oracle_problem(ph, TINY_M, gamma=1.0).vcc(u.astype(np.float64))
+    print(f"gamma {gamma}: final d range [{rep[-1, 8]:.6f}, {rep[-1, 9]:.6f}] (oracle [{dmin:.6f}, {dmax:.6f}])")
+    assert rel(rep[-1, 8], dmin) <= 1e-5 and rel(rep[-1, 9], dmax) <= 1e-5
+    assert rep[-1, 10] == float(dmin >= 0.25 and dmax <= 4.0)
 
 
 def test_drives_agree_with_rejected_steps():
@@ -85,7 +94,7 @@ def test_drives_agree_on_a_fold():
     _assert_same(out)
     code, rep, u = out["graph"]
     assert code == api.RG_EFOLD
-    assert np.isinf(rep[0, 1]) and rep[0, 7] == api.RG_EFOLD and np.all(rep[1:] == 0)
+    assert np.isinf(rep[0, 1]) and rep[0, 7] == api.RG_EFOLD and np.all(rep[1:] == 0) and np.all(rep[0, 8:] == 0)
     np.testing.assert_array_equal(u, u0)
 
 

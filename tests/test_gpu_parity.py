@@ -395,3 +395,55 @@ def test_entry_points_replay_in_a_cuda_graph(tiny):
         torch.cuda.synchronize()
         for a, b in zip((g, terms, hv, p), eager):
             assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("name,nk", [("tiny", 300), ("mid", 3000)])
+def test_adaptive_delta_against_oracle(name, nk):
+    """delta = D(u0) / K(u0), set at the start of the schedule (Sec. II-D2):
+    the value the GPU keeps (rg_get_params) and the first report row's J equal
+    the oracle's at u0 = 0 (the keypoint targets carry the phantom's motion)."""
+    import torch
+
+    from paper_1807_00467_gb300 import api
+    ph = get_phantom(name, seed=3, n_keypoints=nk)
+    m = phantom.CONFIGS[name]["m"]
+    dev = torch.device("cuda:0")
+    ctx = api.Context(torch.from_numpy(ph.R).to(dev), torch.from_numpy(ph.T).to(dev), ph.h, m,
+                      api.make_params(eta=10.0, alpha=1.0, gamma=0.001, delta_adaptive=True), nk_max=nk)
+    ctx.set_keypoints(torch.from_numpy(ph.kp_x).to(dev), torch.from_numpy(ph.kp_y).to(dev))
+    u = torch.zeros(ctx.grid_shape, device=dev)
+    code, rep = ctx.gn_solve(u, gn_iters=1, pcg_iters=5)
+    assert code == 0
+    delta = ctx.get_params().delta
+    P = oracle_problem(ph, m, gamma=0.001, kp=True)
+    u0 = np.zeros(P.grid_shape)
+    D0, K0 = P.ngf_gradient(u0)[0], P.keypoints(u0)[0]
+    P.delta = D0 / K0
+    J0 = P.objective(u0)[0][4]
+    print(f"{name}, {nk} keypoints: delta {delta:.9e} (oracle {D0 / K0:.9e}), J0 {rep[0, 1]:.9e} (oracle {J0:.9e})")
+    assert rel(delta, D0 / K0) <= TOL_OBJ
+    assert rel(rep[0, 1], J0) <= TOL_OBJ
+
+
+def test_fp16_full_size_against_oracle():
+    """FP16-stored images (HU + 1024) at 512x512x128 in the benchmark's launch
+    configuration, against the oracle run on the FP16-rounded images; the
+    quantisation effect itself (oracle on FP32 images vs on FP16-rounded
+    images) is reported separately."""
+    ph = get_phantom("full", seed=0)
+    m = phantom.CONFIGS["full"]["m"]
+    u = _u0(ph, m)
+    ctx = gpu_context(ph, m, gamma=0.001, half=True)
+    terms, grad = ctx.gn_linearize(to_dev(u))
+    v = phantom.random_grid_field(m, 106)
+    Hv = ctx.gn_matvec(to_dev(v)).cpu().numpy()
+    P16 = oracle_problem(ph, m, gamma=0.001, half=True)
+    ot, og, _ = P16.gradient(u)
+    eJ, eg, em = rel(terms[4].item(), ot[4]), rel_l2(grad.cpu().numpy(), og), rel_l2(Hv, P16.linearize(u).matvec(v))
+    P32 = oracle_problem(ph, m, gamma=0.001)
+    qt, qg, _ = P32.gradient(u)
+    print(f"full size FP16: J rel {eJ:.2e}, grad rel-L2 {eg:.2e}, Hv rel-L2 {em:.2e}; quantisation (oracle FP32 vs "
+          f"FP16-rounded images): J rel {rel(ot[4], qt[4]):.2e}, grad rel-L2 {rel_l2(og, qg):.2e}")
+    assert eJ <= TOL_OBJ
+    assert eg <= TOL_GRAD
+    assert em <= TOL_MV

@@ -59,7 +59,8 @@ def test_noalloc_rejects_problems_beyond_the_static_scratch():
     from paper_1807_00467_gb300 import _lib
 
     L = _lib.load()
-    # 64 x 128 x 9 = 73728 tiles > RG_NOALLOC_MAX_CTAS: rejected on the host before any launch
+    # tiles of 28 x 16 voxels in x-y and 32 slices: 74 x 128 x 9 = 85248 > RG_NOALLOC_MAX_CTAS, rejected
+    # on the host before any launch
     ig, gg = _geoms((2048, 2048, 288), (0.5, 0.5, 1.0), (513, 513, 145))
     x = torch.zeros(8, device="cuda")
     D = torch.zeros(1, dtype=torch.float64, device="cuda")
