@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(kNT, 1) gn_product_kernel(const __grid_constan
         y0 = (t / g.nb[0]) * kTY;
     };
     // plane j (voxel plane j - 2) of column (x0, y0) into stage `st`; issued by
-    // lane 0 of warp 0 (callers are warp-uniform)
+    // lane 0 of the last warp (a halo row with the least other work; callers
+    // are warp-uniform)
     auto issue_plane = [&](int x0, int y0, int j, int st) {
         if (a.no_tma || L != 0) return;   // no_tma: test hook, the waits run out instead
         float *dst = tma_base + st * kStageF;
@@ -172,11 +173,11 @@ __global__ void __launch_bounds__(kNT, 1) gn_product_kernel(const __grid_constan
     {
         int x0, y0;
         origin(t, x0, y0);
-        if (tid == 0) {
+        if (tid == kNT - 32) {
             for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
-        if (w == 0)
+        if (w == kNW - 1)
             for (int j = 0; j < kAhead && j < nsteps; ++j) issue_plane(x0, y0, j, j);
     }
 
@@ -192,7 +193,9 @@ __global__ void __launch_bounds__(kNT, 1) gn_product_kernel(const __grid_constan
     constexpr int exh = kEx / 2;                                   // float2 per exchange buffer
     const float2 *ex_t_up = ex_t + up, *ex_t_dn = ex_t + dn, *ex_c_up = ex_c + up, *ex_c_dn = ex_c + dn;
     float2 *park_lane = park + ((w - 2) * 32 + L) * 3;   // this lane's parked parts in a slot (interior warps)
-    const bool node_warp = w * 32 < npad;             // warps that copy the node planes of v
+    // the last warps (halo rows and the interior rows next to them) copy the node planes of v
+    const bool node_warp = (kNW - 1 - w) * 32 < npad;
+    const int ntid = tid - (kNT - npad);              // this thread's node of a plane (when node_warp)
     // work items of the x and y passes go to the threads lane-major, so that
     // every warp takes a share; quotients by the item extents from reciprocals
     // (exact for the item counts and extents here: below 2^11)
@@ -214,15 +217,15 @@ __global__ void __launch_bounds__(kNT, 1) gn_product_kernel(const __grid_constan
         // beyond the plane fill padding), copied asynchronously into the ring
         // (zero outside the grid)
         int ngo = -1;   // offset of the node in a grid plane, -1 outside the grid or the plane
-        if (tid < nplane) {
-            const int ly = tid / nxt, lx = tid - ly * nxt;
+        if (ntid >= 0 && ntid < nplane) {
+            const int ly = ntid / nxt, lx = ntid - ly * nxt;
             const int ux = kx_lo + lx, uy = ky_lo + ly;
             if (ux >= 0 && ux < g.m[0] && uy >= 0 && uy < g.m[1]) ngo = uy * g.m[0] + ux;
         }
         auto node_copy = [&](int kz) {   // node warps only (warp-uniform callers)
             const bool in = ngo >= 0 && kz >= 0 && kz < g.m[2];
             const float *p = in ? a.v + kz * mxy + ngo : a.v;
-            const uint32_t dst = smem_u32(s_nodes + (kz & 3) * npad + tid);
+            const uint32_t dst = smem_u32(s_nodes + (kz & 3) * npad + ntid);
             const uint32_t n = in ? 4u : 0u;   // 0 source bytes: zero fill
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(p), "r"(n) : "memory");
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4), "l"(p + Mn), "r"(n) : "memory");
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(kNT, 1) gn_product_kernel(const __grid_constan
                 float *dst = box + (long)kz * NP;
 #pragma unroll
                 for (int i = 0; i < (NY + kNT - 1) / kNT; ++i) {
-                    const int it = tid + i * kNT;
+                    const int it = (tid + kNT - 64) % kNT + i * kNT;   // from the third warp on
                     if (it < NY) {
                         const int k = it / NP, r = it % NP, jy = r / (C0c + 1), jx = r % (C0c + 1);
                         const float v = y_node<RXY, DG>(src + jx * 3 + k, XRc, jy, C1c);
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(kNT, 1) gn_product_kernel(const __grid_constan
                 if (cell_start && node_warp) asm volatile("cp.async.wait_group 1;" ::: "memory");
                 // the stage of plane s - 1 and the buffers of the last plane were last read before this barrier
                 __syncthreads();
-                if (w == 0) {
+                if (w == kNW - 1) {
                     // 3 planes ahead: of this column, then the first planes of the next one
                     if (CHAIN ? s < nsteps - kAhead : s + kAhead < nsteps)
                         issue_plane(x0, y0, s + kAhead, (j + kAhead) & (kStages - 1));
