@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
@@ -53,7 +54,7 @@ struct rg_ctx {
     BoxGeom bM;
     const BoxGeom *bcur;      // node-box geometry of the last NGF tile launch (read by the node pass)
     int hook_no_tma, hook_poll;   // test hooks (rg_debug_hook)
-    double *rzh, *coef, *pcgpart;
+    double *rzh, *pcgpart, *rzpart, *apart;   // PCG: r_j.z_j, coefficient / r.z / d.q partials
     PcgScalars *sc;
     bool has_lin, minv_valid;
     char err[512];
@@ -272,8 +273,9 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->minv = cv.take<float>(3 * M);
     c->Rh = cv.take<float>(pcg_stride(3 * M) * (size_t)(c->pcg_max + 1));
     c->rzh = cv.take<double>(c->pcg_max + 1);
-    c->coef = cv.take<double>(c->pcg_max + 1);
     c->pcgpart = cv.take<double>((size_t)pcg_blocks(3 * M) * (c->pcg_max + 2));
+    c->rzpart = cv.take<double>(pcg_blocks(3 * M));
+    c->apart = cv.take<double>(std::max(pcg_blocks(3 * M), c->nR));
     c->d = cv.take<float>(3 * M);
     c->q = cv.take<float>(3 * M);
     c->tg_ = cv.take<float>(3 * M);
@@ -598,7 +600,7 @@ static int run_vcc(rg_ctx *c, const float *u, const float *v, int diag = 0) {
 // the partials), then out = sA (NGF boxes) + sB (VCC boxes) + sC L^T w when
 // out is given.
 static int run_nodes(rg_ctx *c, const float *v, bool energy, float *out, double sA, double sB, double sC, bool useA,
-                     bool useB) {
+                     bool useB, double *dpart = nullptr) {
     NodeArgs a;
     for (int i = 0; i < 3; ++i) {
         a.m[i] = c->grid.m[i];
@@ -615,6 +617,8 @@ static int run_nodes(rg_ctx *c, const float *v, bool energy, float *out, double 
     a.sC = (float)sC;
     a.rpart = energy ? c->rpart : nullptr;
     a.out = out;
+    a.dvec = v;
+    a.dpart = v ? dpart : nullptr;
     a.skip = c->skip;
     if (v) LAUNCH(5, launch_curv(a, c->st));
     if (out) LAUNCH(6, launch_nodes(a, c->st));
@@ -709,12 +713,19 @@ extern "C" int gn_linearize(rg_ctx *c, const float *u, double *terms, float *gra
     return evaluate(c, u, terms, grad, true);
 }
 
-static int matvec(rg_ctx *c, const float *v, float *Hv) {
+// H v; with dpart, also the per-block partials of v . H v when the node pass
+// forms H v completely (no keypoint term after it): *ndpart is their count,
+// else 0.
+static int matvec(rg_ctx *c, const float *v, float *Hv, double *dpart = nullptr, int *ndpart = nullptr) {
     int st;
     if ((st = run_tile(c, MODE_MATVEC, v))) return st;
     const bool vcc = c->P.gamma != 0.0;
     if (vcc && (st = run_vcc(c, c->lin_u, v))) return st;
-    if ((st = run_nodes(c, v, false, Hv, c->hbar, c->P.gamma * c->ghat, c->P.alpha * c->ghat, true, vcc))) return st;
+    const bool dq = dpart && c->nk <= 0;
+    if (ndpart) *ndpart = dq ? c->nR : 0;
+    if ((st = run_nodes(c, v, false, Hv, c->hbar, c->P.gamma * c->ghat, c->P.alpha * c->ghat, true, vcc,
+                        dq ? dpart : nullptr)))
+        return st;
     if ((st = run_kp(c, c->lin_u, v, c->P.delta, Hv, false))) return st;
     return RG_OK;
 }
@@ -822,17 +833,19 @@ static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
     a.Rh = c->Rh;
     a.d = c->d;
     a.part = c->pcgpart;
+    a.rzpart = c->rzpart;
+    a.apart = c->apart;
     a.ticket = reinterpret_cast<unsigned *>(c->tma_err + 1);
     a.sc = c->sc;
     a.rzh = c->rzh;
-    a.coef = c->coef;
     LAUNCH(9, launch_pcg_start(a, g, p, c->st));
     for (int k = 0; k < iters; ++k) {
-        if ((st = matvec(c, c->d, c->q))) return st;
-        LAUNCH(9, launch_pcg_alpha(a, c->q, c->st));
-        LAUNCH(9, launch_pcg_step(a, c->q, p, k, c->st));
+        int napart = 0;   // d.q partials: from the node pass, else from the alpha kernel
+        if ((st = matvec(c, c->d, c->q, c->apart, &napart))) return st;
+        if (!napart) LAUNCH(9, launch_pcg_alpha(a, c->q, &napart, c->st));
+        LAUNCH(9, launch_pcg_step(a, c->q, napart, k, c->st));
         LAUNCH(9, launch_pcg_reorth(a, k, c->st));
-        LAUNCH(9, launch_pcg_dir(a, k, c->st));
+        LAUNCH(9, launch_pcg_dir(a, p, k, c->st));
     }
     const int nb = vec_blocks(a.n);
     LAUNCH(9, launch_dot_slot(a.n, c->Rh, a.stride, c->sc, c->vecpart, c->st));

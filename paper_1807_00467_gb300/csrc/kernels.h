@@ -59,6 +59,8 @@ struct NodeArgs {
     float sC;              // scale of L^T w (alpha ghat)
     double *rpart;         // per-block partial sums of |L v|^2, may be NULL
     float *out;            // [3][M] (launch_nodes)
+    const float *dvec = nullptr;   // with dpart: per-block partials of dvec . out (launch_nodes)
+    double *dpart = nullptr;
     const int *skip = nullptr;   // nonzero: the launch does nothing
 };
 int node_blocks(const int *m);
@@ -112,26 +114,30 @@ cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScal
 cudaError_t launch_dot_slot(long n, const float *Rh, long stride, const PcgScalars *sc, double *part,
                             cudaStream_t st);
 
-// Reorthogonalised PCG (float4 streams, FP64 partials reduced by the last
-// block).  Residual history r_0..r_k in slots of `stride` floats.
+// Reorthogonalised PCG (float4 streams; FP64 per-block partials that the
+// blocks of the next kernel reduce in a fixed order).  Residual history
+// r_0..r_k in slots of `stride` floats.
 struct PcgArgs {
     long n, stride;        // vector length, history slot stride (pcg_stride(n))
     const float *minv;     // inverse preconditioner diagonal
     float *Rh;             // residual history
     float *d;              // search direction
-    double *part;          // partials: (RG_PCG_MAX + 2) x pcg_blocks(n)
-    unsigned *ticket;      // last-block ticket (zero between launches)
+    double *part;          // Gram-Schmidt coefficient partials: (pcg_max + 2) x pcg_blocks(n)
+    double *rzpart;        // r.z partials of the reorthogonalised residual: pcg_blocks(n)
+    double *apart;         // d.q partials: max(pcg_blocks(n), node_blocks(m))
+    unsigned *ticket;      // last-block ticket of the start kernel (zero between launches)
     PcgScalars *sc;
     double *rzh;           // r_j . z_j
-    double *coef;          // Gram-Schmidt coefficients
 };
 int pcg_blocks(long n);
 long pcg_stride(long n);
 cudaError_t launch_pcg_start(const PcgArgs &a, const float *g, float *s, cudaStream_t st);
-cudaError_t launch_pcg_alpha(const PcgArgs &a, const float *q, cudaStream_t st);
-cudaError_t launch_pcg_step(const PcgArgs &a, const float *q, float *s, int k, cudaStream_t st);
+// d.q partials into a.apart (their count into *napart)
+cudaError_t launch_pcg_alpha(const PcgArgs &a, const float *q, int *napart, cudaStream_t st);
+// napart: the d.q partials in a.apart (from launch_pcg_alpha or the node pass)
+cudaError_t launch_pcg_step(const PcgArgs &a, const float *q, int napart, int k, cudaStream_t st);
 cudaError_t launch_pcg_reorth(const PcgArgs &a, int k, cudaStream_t st);
-cudaError_t launch_pcg_dir(const PcgArgs &a, int k, cudaStream_t st);
+cudaError_t launch_pcg_dir(const PcgArgs &a, float *s, int k, cudaStream_t st);
 cudaError_t launch_axpy_copy(long n, float t, const float *x, const float *p, float *y, cudaStream_t st,
                              const int *skip = nullptr);
 

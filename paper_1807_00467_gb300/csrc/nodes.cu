@@ -6,7 +6,8 @@
 //
 // node_kernel: per grid node k,
 //   out_k = sA (sum of the NGF node boxes holding k) + sB (sum of the VCC node
-//           boxes holding k) + sC (L^T w)_k.
+//           boxes holding k) + sC (L^T w)_k,
+// optionally with per-block partials of d . out (the PCG step length).
 // The boxes holding a node come from per-axis lookups built once per block
 // (box index, local index, 1 or 2 boxes), so the gather has no per-node
 // integer division.  Blocks are 32 x 4 x 2 node tiles.  No atomics: the result
@@ -89,7 +90,8 @@ __global__ void __launch_bounds__(NT) curv_kernel(const NodeArgs a) {
     }
 }
 
-// out = sA (NGF boxes) + sB (VCC boxes) + sC L^T w
+// out = sA (NGF boxes) + sB (VCC boxes) + sC L^T w (and, with dpart, the
+// per-block partials of dvec . out)
 __global__ void __launch_bounds__(NT, 5) node_kernel(const NodeArgs a) {
     if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     __shared__ int tabA[NX + NY + NZ], tabB[NX + NY + NZ];
@@ -107,34 +109,49 @@ __global__ void __launch_bounds__(NT, 5) node_kernel(const NodeArgs a) {
     __syncthreads();
     const int lx = tid % NX, ly = (tid / NX) % NY, lz = tid / (NX * NY);
     const int kx = x0 + lx, ky = y0 + ly, kz = z0 + lz;
-    if (kx >= mx || ky >= my || kz >= mz) return;
-    float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
-    if (a.boxA) gather_boxes(a.boxA, a.gA, tabA[lx], tabA[NX + ly], tabA[NX + NY + lz], sa[0], sa[1], sa[2]);
-    if (a.boxB) gather_boxes(a.boxB, a.gB, tabB[lx], tabB[NX + ly], tabB[NX + NY + lz], sb[0], sb[1], sb[2]);
-    const unsigned k = ((unsigned)kz * my + ky) * mx + kx, Mu = (unsigned)M, sy = mx, sz = (unsigned)mxy;
-    const bool ix = kx >= 1 && kx <= mx - 2, iy = ky >= 1 && ky <= my - 2, iz = kz >= 1 && kz <= mz - 2;
-    const bool xm = kx - 1 >= 1, xp = kx + 1 <= mx - 2, ym = ky - 1 >= 1, yp = ky + 1 <= my - 2;
-    const bool zm = kz - 1 >= 1, zp = kz + 1 <= mz - 2;
+    float dq = 0.f;   // dvec . out over this thread's node
+    if (kx < mx && ky < my && kz < mz) {
+        float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
+        if (a.boxA) gather_boxes(a.boxA, a.gA, tabA[lx], tabA[NX + ly], tabA[NX + NY + lz], sa[0], sa[1], sa[2]);
+        if (a.boxB) gather_boxes(a.boxB, a.gB, tabB[lx], tabB[NX + ly], tabB[NX + NY + lz], sb[0], sb[1], sb[2]);
+        const unsigned k = ((unsigned)kz * my + ky) * mx + kx, Mu = (unsigned)M, sy = mx, sz = (unsigned)mxy;
+        const bool ix = kx >= 1 && kx <= mx - 2, iy = ky >= 1 && ky <= my - 2, iz = kz >= 1 && kz <= mz - 2;
+        const bool xm = kx - 1 >= 1, xp = kx + 1 <= mx - 2, ym = ky - 1 >= 1, yp = ky + 1 <= my - 2;
+        const bool zm = kz - 1 >= 1, zp = kz + 1 <= mz - 2;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float o = a.sA * sa[c] + a.sB * sb[c];
-        if (a.w) {
-            // L^T w: the rows of L that reference node k along each axis
-            const float *p = a.w + c * Mu + k;
-            const float w0 = __ldg(p);
-            float tx = 0.f, ty = 0.f, tz = 0.f;
-            if (ix) tx -= 2.f * w0;
-            if (xm) tx += __ldg(p - 1);
-            if (xp) tx += __ldg(p + 1);
-            if (iy) ty -= 2.f * w0;
-            if (ym) ty += __ldg(p - sy);
-            if (yp) ty += __ldg(p + sy);
-            if (iz) tz -= 2.f * w0;
-            if (zm) tz += __ldg(p - sz);
-            if (zp) tz += __ldg(p + sz);
-            o = fmaf(a.sC, fmaf(tz, a.ig2[2], fmaf(ty, a.ig2[1], tx * a.ig2[0])), o);
+        for (int c = 0; c < 3; ++c) {
+            float o = a.sA * sa[c] + a.sB * sb[c];
+            if (a.w) {
+                // L^T w: the rows of L that reference node k along each axis
+                const float *p = a.w + c * Mu + k;
+                const float w0 = __ldg(p);
+                float tx = 0.f, ty = 0.f, tz = 0.f;
+                if (ix) tx -= 2.f * w0;
+                if (xm) tx += __ldg(p - 1);
+                if (xp) tx += __ldg(p + 1);
+                if (iy) ty -= 2.f * w0;
+                if (ym) ty += __ldg(p - sy);
+                if (yp) ty += __ldg(p + sy);
+                if (iz) tz -= 2.f * w0;
+                if (zm) tz += __ldg(p - sz);
+                if (zp) tz += __ldg(p + sz);
+                o = fmaf(a.sC, fmaf(tz, a.ig2[2], fmaf(ty, a.ig2[1], tx * a.ig2[0])), o);
+            }
+            a.out[c * Mu + k] = o;
+            if (a.dpart) dq = fmaf(__ldg(a.dvec + c * Mu + k), o, dq);
         }
-        a.out[c * Mu + k] = o;
+    }
+    if (a.dpart) {
+        // FP32 within the warp, FP64 across warps (the PCG's d.q partials)
+        for (int off = 16; off > 0; off >>= 1) dq += __shfl_xor_sync(0xffffffffu, dq, off);
+        __shared__ double red[NT / 32];
+        if ((tid & 31) == 0) red[tid >> 5] = (double)dq;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int i = 0; i < NT / 32; ++i) s += red[i];
+            a.dpart[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+        }
     }
 }
 

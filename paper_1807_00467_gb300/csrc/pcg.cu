@@ -2,12 +2,23 @@
 // system is solved by preconditioned conjugate gradients).
 //
 // Every kernel streams the node vectors as float4 with the same partition:
-// block b owns quads [b Q, (b + 1) Q), Q = 256 qpt, thread t its quads
-// b Q + i 256 + t (i < qpt <= kQmax), so each thread keeps up to kQmax
+// block b owns quads [b Q, (b + 1) Q), Q = kVT qpt, thread t its quads
+// b Q + i kVT + t (i < qpt <= kQmax), so each thread keeps up to kQmax
 // independent 16-byte loads in flight per stream.  Sums are FP32 within a
-// warp and FP64 across warps and blocks; the block that finishes last (atomic ticket, no waiting) reduces them
-// in a fixed order and updates the device scalars, so no separate scalar
-// kernels run and the result does not depend on block scheduling.
+// warp and FP64 across warps and blocks.  A kernel publishes one FP64 partial
+// per block and sum; the blocks of the NEXT kernel each reduce those partials
+// in the same fixed order, so every block derives the same scalar (block 0
+// records it in the device scalars), no block waits for another and no kernel
+// ends in a serial reduction.  One PCG step k, after q = H d:
+//   step:   alpha = r_k . z_k / d . q;  r' = r_k - alpha q;  partials of
+//           (M^-1 r') . r_j, j = 0..k (the classical Gram-Schmidt coefficients)
+//   reorth: c_j = (M^-1 r') . r_j / (r_j . z_j);  r_{k+1} = r' - sum_j c_j r_j,
+//           the history read newest first (the step kernel has just streamed
+//           it oldest first, so its newest slots are still in L2);  partials of
+//           r_{k+1} . z_{k+1}
+//   dir:    beta = r_{k+1} . z_{k+1} / r_k . z_k;  s += alpha d;  d = z_{k+1} + beta d
+// The d . q partials come from the node pass that forms q (no later pass adds
+// to it) or from pcg_alpha_kernel.
 //
 // The preconditioner is diagonal, so z_j = M^-1 r_j is not stored: the
 // Gram-Schmidt coefficients use r . z_j = (M^-1 r) . r_j.
@@ -20,9 +31,9 @@ namespace ngf {
 
 namespace {
 
-constexpr int kVT = 256;            // threads per block
+constexpr int kVT = 512;            // threads per block (two blocks per SM at the full size)
 constexpr int kVW = kVT / 32;
-constexpr int kQmax = 8;            // quads per thread at most
+constexpr int kQmax = 6;            // quads per thread at most
 constexpr int kHist = RG_PCG_MAX + 1;
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
@@ -42,6 +53,21 @@ __device__ __forceinline__ double block_total(float v, double *red) {
     return t;
 }
 
+// Sum of the partials part[0..n) of the previous kernel by the whole block in
+// a fixed order (thread-strided, a fixed shuffle tree, the warps in order):
+// the same value in every block, valid in every thread.
+__device__ __forceinline__ double block_sum_parts(const double *part, int n, double *red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += kVT) s += __ldcg(part + i);
+    s = lb_warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kVW; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
 struct Part {
     long n4;   // whole quads
     int tail;  // trailing floats (n % 4), handled by block 0
@@ -56,7 +82,7 @@ __device__ __forceinline__ void st4(float *p, long q, float4 v) { reinterpret_ca
 
 // ---------------------------------------------------------------------------
 // start: s = 0, r_0 = -g, d = z_0 = M^-1 r_0; scalars reset, |g|, r_0 . z_0
-__global__ void __launch_bounds__(kVT) pcg_start_kernel(Part P, const float *g, const float *minv, float *s, float *r,
+__global__ void __launch_bounds__(kVT, 2) pcg_start_kernel(Part P, const float *g, const float *minv, float *s, float *r,
                                                         float *d, double *part, unsigned *ticket, PcgScalars *sc,
                                                         double *rzh) {
     __shared__ double red[kVW];
@@ -103,10 +129,8 @@ __global__ void __launch_bounds__(kVT) pcg_start_kernel(Part P, const float *g, 
 }
 
 // ---------------------------------------------------------------------------
-// d . q, then alpha = r.z / d.q (stop on a non-positive curvature d.q or a
-// vanishing r.z)
-__global__ void __launch_bounds__(kVT) pcg_alpha_kernel(Part P, const float *d, const float *q, double *part,
-                                                        unsigned *ticket, PcgScalars *sc) {
+// partials of d . q (when a pass after the node pass still adds to q)
+__global__ void __launch_bounds__(kVT, 2) pcg_alpha_kernel(Part P, const float *d, const float *q, double *apart) {
     __shared__ double red[kVW];
     float acc = 0.f;
 #pragma unroll
@@ -119,24 +143,29 @@ __global__ void __launch_bounds__(kVT) pcg_alpha_kernel(Part P, const float *d, 
         acc = fmaf(d[e], q[e], acc);
     }
     const double t = block_total(acc, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
-    if (!lb_last_block(ticket, gridDim.x)) return;
-    if (threadIdx.x < 32) {
-        const double v = lb_sum_parts(part, gridDim.x);
-        if (threadIdx.x == 0) pcg_set_alpha(sc, v);
-    }
+    if (threadIdx.x == 0) apart[blockIdx.x] = t;
 }
 
 // ---------------------------------------------------------------------------
-// s += alpha d;  r_{k+1} = r_k - alpha q;  then the Gram-Schmidt coefficients
-// c_j = (M^-1 r_{k+1}) . r_j / (r_j . z_j), j = 0..k
-__global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars *sc, const float *d, const float *q,
-                                                       const float *minv, float *s, float *Rh, long stride,
-                                                       int k, double *part, unsigned *ticket, const double *rzh,
-                                                       double *coef) {
+// alpha = r.z / d.q (stop on a non-positive curvature d.q or a vanishing r.z);
+// r_{k+1} = r_k - alpha q; then the partials of (M^-1 r_{k+1}) . r_j, j = 0..k
+__global__ void __launch_bounds__(kVT, 2) pcg_step_kernel(Part P, PcgScalars *sc, const double *apart, int napart,
+                                                       const float *q, const float *minv, float *Rh, long stride,
+                                                       int k, double *part) {
     __shared__ double wp[kHist][kVW];
+    __shared__ double red[kVW];
     const int nb = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float al = (float)sc->alpha;
+    // every block forms the same alpha; a block that reads the stop flag block 0
+    // has just set takes the same decision (the flag only ever turns on)
+    const double pq = block_sum_parts(apart, napart, red);
+    const int stop = (sc->stop || !(sc->rz != 0.0) || !(pq > 0.0)) ? 1 : 0;
+    const double al64 = stop ? 0.0 : sc->rz / pq;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->pq = pq;
+        sc->stop = stop;
+        sc->alpha = al64;
+    }
+    const float al = (float)al64;
     const float *r = Rh + (long)k * stride;
     float *rn = Rh + (long)(k + 1) * stride;
     float4 zn[kQmax];
@@ -145,12 +174,9 @@ __global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars 
         const long e = P.quad(i);
         zn[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < P.qpt && e < P.n4) {
-            const float4 dv = ldg4(d, e), qv = ldg4(q, e), rv = ldg4(r, e), m = ldg4(minv, e);
-            float4 sv = ldg4(s, e);
-            sv.x = fmaf(al, dv.x, sv.x); sv.y = fmaf(al, dv.y, sv.y); sv.z = fmaf(al, dv.z, sv.z); sv.w = fmaf(al, dv.w, sv.w);
+            const float4 qv = ldg4(q, e), rv = ldg4(r, e), m = ldg4(minv, e);
             const float4 nv = make_float4(fmaf(-al, qv.x, rv.x), fmaf(-al, qv.y, rv.y), fmaf(-al, qv.z, rv.z),
                                           fmaf(-al, qv.w, rv.w));
-            st4(s, e, sv);
             st4(rn, e, nv);
             zn[i] = make_float4(m.x * nv.x, m.y * nv.y, m.z * nv.z, m.w * nv.w);
         }
@@ -159,12 +185,11 @@ __global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars 
     const bool tail = blockIdx.x == 0 && threadIdx.x < P.tail;
     const long et = 4 * P.n4 + threadIdx.x;
     if (tail) {
-        s[et] = fmaf(al, d[et], s[et]);
         const float nv = fmaf(-al, q[et], r[et]);
         rn[et] = nv;
         zt = minv[et] * nv;
     }
-#pragma unroll 2
+#pragma unroll 1
     for (int j = 0; j <= k; ++j) {
         const float *rj = Rh + (long)j * stride;
         float acc = 0.f;
@@ -183,22 +208,17 @@ __global__ void __launch_bounds__(kVT) pcg_step_kernel(Part P, const PcgScalars 
         for (int w = 0; w < kVW; ++w) t += wp[j][w];
         part[(long)j * nb + blockIdx.x] = t;
     }
-    if (!lb_last_block(ticket, gridDim.x)) return;
-    for (int j = warp; j <= k; j += kVW) {
-        const double v = lb_sum_parts(part + (long)j * nb, nb);
-        if (lane == 0) coef[j] = (sc->stop || rzh[j] == 0.0) ? 0.0 : v / rzh[j];
-    }
 }
 
 // ---------------------------------------------------------------------------
-// r_{k+1} -= sum_j c_j r_j;  then r.z with z = M^-1 r_{k+1} -> beta
-__global__ void __launch_bounds__(kVT, 3) pcg_reorth_kernel(Part P, const float *minv, float *Rh, long stride, int k,
-                                                         const double *coef, double *part, unsigned *ticket,
-                                                         PcgScalars *sc, double *rzh) {
+// c_j = (M^-1 r_{k+1}) . r_j / (r_j . z_j);  r_{k+1} -= sum_j c_j r_j;  then the
+// partials of r.z with z = M^-1 r_{k+1}
+__global__ void __launch_bounds__(kVT, 2) pcg_reorth_kernel(Part P, const PcgScalars *sc, const float *minv, float *Rh,
+                                                         long stride, int k, const double *rzh, const double *cpart,
+                                                         double *rzpart) {
     __shared__ float c[kHist];
     __shared__ double red[kVW];
-    for (int j = threadIdx.x; j <= k; j += kVT) c[j] = (float)coef[j];
-    __syncthreads();
+    const int nb = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *r = Rh + (long)(k + 1) * stride;
     float4 rv[kQmax];
 #pragma unroll
@@ -209,8 +229,15 @@ __global__ void __launch_bounds__(kVT, 3) pcg_reorth_kernel(Part P, const float 
     const bool tail = blockIdx.x == 0 && threadIdx.x < P.tail;
     const long et = 4 * P.n4 + threadIdx.x;
     float rt = tail ? r[et] : 0.f;
+    // the coefficients, every block in the same order (one warp per coefficient)
+    const bool stop = sc->stop != 0;
+    for (int j = warp; j <= k; j += kVW) {
+        const double v = lb_sum_parts(cpart + (long)j * nb, nb);
+        if (lane == 0) c[j] = (stop || rzh[j] == 0.0) ? 0.f : (float)(v / rzh[j]);
+    }
+    __syncthreads();
 #pragma unroll 2
-    for (int j = 0; j <= k; ++j) {
+    for (int j = k; j >= 0; --j) {
         const float *rj = Rh + (long)j * stride;
         const float cj = c[j];
 #pragma unroll
@@ -239,41 +266,45 @@ __global__ void __launch_bounds__(kVT, 3) pcg_reorth_kernel(Part P, const float 
         acc = fmaf(rt, minv[et] * rt, acc);
     }
     const double t = block_total(acc, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
-    if (!lb_last_block(ticket, gridDim.x)) return;
-    if (threadIdx.x < 32) {
-        const double v = lb_sum_parts(part, gridDim.x);
-        if (threadIdx.x == 0) {
-            sc->rz_new = v;
-            if (sc->stop) {
-                sc->beta = 0.0;
-            } else {
-                sc->beta = v / sc->rz;
-                sc->rz = v;
-                sc->steps += 1;
-                rzh[sc->steps] = v;
-            }
-        }
-    }
+    if (threadIdx.x == 0) rzpart[blockIdx.x] = t;
 }
 
 // ---------------------------------------------------------------------------
-// d = M^-1 r_{k+1} + beta d
-__global__ void __launch_bounds__(kVT) pcg_dir_kernel(Part P, const PcgScalars *sc, const float *minv, const float *r,
-                                                      float *d) {
-    const float be = (float)sc->beta;
+// beta = r_{k+1}.z_{k+1} / r_k.z_k;  s += alpha d;  d = M^-1 r_{k+1} + beta d
+__global__ void __launch_bounds__(kVT, 2) pcg_dir_kernel(Part P, PcgScalars *sc, const float *minv, const float *r,
+                                                      float *d, float *s, int k, double *rzh, const double *rzpart) {
+    __shared__ double red[kVW];
+    const double v = block_sum_parts(rzpart, gridDim.x, red);
+    // stop and alpha were set by the step kernel; rzh[k] = r_k . z_k while the
+    // solve runs (block 0 appends rzh[k + 1], which no block reads here)
+    const bool stop = sc->stop != 0;
+    const double beta = stop ? 0.0 : v / rzh[k];
+    const float al = (float)sc->alpha, be = (float)beta;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->rz_new = v;
+        sc->beta = beta;
+        if (!stop) {
+            sc->rz = v;
+            sc->steps += 1;
+            rzh[sc->steps] = v;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < kQmax; ++i) {
         const long e = P.quad(i);
         if (i < P.qpt && e < P.n4) {
-            const float4 m = ldg4(minv, e), rv = ldg4(r, e), dv = ldg4(d, e);
+            const float4 m = ldg4(minv, e), rv = ldg4(r, e), dv = ldg4(d, e), sv = ldg4(s, e);
+            st4(s, e, make_float4(fmaf(al, dv.x, sv.x), fmaf(al, dv.y, sv.y), fmaf(al, dv.z, sv.z),
+                                  fmaf(al, dv.w, sv.w)));
             st4(d, e, make_float4(fmaf(be, dv.x, m.x * rv.x), fmaf(be, dv.y, m.y * rv.y), fmaf(be, dv.z, m.z * rv.z),
                                   fmaf(be, dv.w, m.w * rv.w)));
         }
     }
     if (blockIdx.x == 0 && threadIdx.x < P.tail) {
         const long e = 4 * P.n4 + threadIdx.x;
-        d[e] = fmaf(be, d[e], minv[e] * r[e]);
+        const float dv = d[e];
+        s[e] = fmaf(al, dv, s[e]);
+        d[e] = fmaf(be, dv, minv[e] * r[e]);
     }
 }
 
@@ -281,11 +312,14 @@ Part make_part(long n, int *nb) {
     Part P;
     P.n4 = n / 4;
     P.tail = (int)(n % 4);
-    // blocks: a multiple of the SM count with at most kQmax quads per thread
-    const long per_wave = 152L * kVT * kQmax;
-    const long waves = P.n4 > 0 ? (P.n4 + per_wave - 1) / per_wave : 1;
-    *nb = (int)(152 * waves);
-    P.qpt = (int)((P.n4 + (long)*nb * kVT - 1) / ((long)*nb * kVT));
+    // two blocks per SM while that keeps at most kQmax quads per thread (more
+    // waves beyond); short vectors take fewer blocks of one quad per thread
+    const long fill = 2L * 152 * kVT;
+    long blocks;
+    if (P.n4 <= fill) blocks = P.n4 > 0 ? (P.n4 + kVT - 1) / kVT : 1;
+    else blocks = 2L * 152 * ((P.n4 + fill * kQmax - 1) / (fill * kQmax));
+    *nb = (int)blocks;
+    P.qpt = (int)((P.n4 + blocks * kVT - 1) / (blocks * kVT));
     if (P.qpt < 1) P.qpt = 1;
     return P;
 }
@@ -307,19 +341,19 @@ cudaError_t launch_pcg_start(const PcgArgs &a, const float *g, float *s, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_alpha(const PcgArgs &a, const float *q, cudaStream_t st) {
+cudaError_t launch_pcg_alpha(const PcgArgs &a, const float *q, int *napart, cudaStream_t st) {
     int nb;
     const Part P = make_part(a.n, &nb);
-    pcg_alpha_kernel<<<nb, kVT, 0, st>>>(P, a.d, q, a.part, a.ticket, a.sc);
+    pcg_alpha_kernel<<<nb, kVT, 0, st>>>(P, a.d, q, a.apart);
+    *napart = nb;
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_step(const PcgArgs &a, const float *q, float *s, int k, cudaStream_t st) {
-    if (k < 0 || k + 1 >= kHist) return cudaErrorInvalidValue;
+cudaError_t launch_pcg_step(const PcgArgs &a, const float *q, int napart, int k, cudaStream_t st) {
+    if (k < 0 || k + 1 >= kHist || napart < 1) return cudaErrorInvalidValue;
     int nb;
     const Part P = make_part(a.n, &nb);
-    pcg_step_kernel<<<nb, kVT, 0, st>>>(P, a.sc, a.d, q, a.minv, s, a.Rh, a.stride, k, a.part, a.ticket, a.rzh,
-                                        a.coef);
+    pcg_step_kernel<<<nb, kVT, 0, st>>>(P, a.sc, a.apart, napart, q, a.minv, a.Rh, a.stride, k, a.part);
     return cudaGetLastError();
 }
 
@@ -327,14 +361,15 @@ cudaError_t launch_pcg_reorth(const PcgArgs &a, int k, cudaStream_t st) {
     if (k < 0 || k + 1 >= kHist) return cudaErrorInvalidValue;
     int nb;
     const Part P = make_part(a.n, &nb);
-    pcg_reorth_kernel<<<nb, kVT, 0, st>>>(P, a.minv, a.Rh, a.stride, k, a.coef, a.part, a.ticket, a.sc, a.rzh);
+    pcg_reorth_kernel<<<nb, kVT, 0, st>>>(P, a.sc, a.minv, a.Rh, a.stride, k, a.rzh, a.part, a.rzpart);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_dir(const PcgArgs &a, int k, cudaStream_t st) {
+cudaError_t launch_pcg_dir(const PcgArgs &a, float *s, int k, cudaStream_t st) {
     int nb;
     const Part P = make_part(a.n, &nb);
-    pcg_dir_kernel<<<nb, kVT, 0, st>>>(P, a.sc, a.minv, a.Rh + (long)(k + 1) * a.stride, a.d);
+    pcg_dir_kernel<<<nb, kVT, 0, st>>>(P, a.sc, a.minv, a.Rh + (long)(k + 1) * a.stride, a.d, s, k, a.rzh,
+                                       a.rzpart);
     return cudaGetLastError();
 }
 
