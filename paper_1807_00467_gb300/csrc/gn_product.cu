@@ -300,22 +300,22 @@ __global__ void __launch_bounds__(kNT, 1) gn_product_kernel(const __grid_constan
                         dst[it] = (jx < C0c ? lo : 0.f) + (jx > 0 ? hi : 0.f);
                     }
                 }
-                return;
-            }
-            for (int it = lane_major; it < kTY * XR; it += kNT) {
-                const int row = idiv(it, invXR), r = it - row * XR, jx = (r * 43) >> 7, k = r - jx * 3;
-                const float2 *p = src + (row * 32 + 1 + jx * half) * 3 + k;
-                // the lanes of cell jx (lower parts, none for jx = C0) and of cell
-                // jx - 1 (upper parts, none for jx = 0); a missing cell reads a
-                // neighbouring one inside the row and is discarded
-                const float2 *pl = jx < C0 ? p : p - 3 * half, *ph = jx > 0 ? p : p + 3 * half;
-                float lo, hi;
-                switch (half) {
-                    case 1: lo = pl[0].x; hi = ph[-3].y; break;
-                    case 2: lo = pl[0].x + pl[3].x; hi = ph[-6].y + ph[-3].y; break;
-                    default: lo = (pl[0].x + pl[3].x) + (pl[6].x + pl[9].x); hi = (ph[-12].y + ph[-9].y) + (ph[-6].y + ph[-3].y);
+            } else {
+                for (int it = lane_major; it < kTY * XR; it += kNT) {
+                    const int row = idiv(it, invXR), r = it - row * XR, jx = (r * 43) >> 7, k = r - jx * 3;
+                    const float2 *p = src + (row * 32 + 1 + jx * half) * 3 + k;
+                    // the lanes of cell jx (lower parts, none for jx = C0) and of cell
+                    // jx - 1 (upper parts, none for jx = 0); a missing cell reads a
+                    // neighbouring one inside the row and is discarded
+                    const float2 *pl = jx < C0 ? p : p - 3 * half, *ph = jx > 0 ? p : p + 3 * half;
+                    float lo, hi;
+                    switch (half) {
+                        case 1: lo = pl[0].x; hi = ph[-3].y; break;
+                        case 2: lo = pl[0].x + pl[3].x; hi = ph[-6].y + ph[-3].y; break;
+                        default: lo = (pl[0].x + pl[3].x) + (pl[6].x + pl[9].x); hi = (ph[-12].y + ph[-9].y) + (ph[-6].y + ph[-3].y);
+                    }
+                    dst[it] = (jx < C0 ? lo : 0.f) + (jx > 0 ? hi : 0.f);
                 }
-                dst[it] = (jx < C0 ? lo : 0.f) + (jx > 0 ? hi : 0.f);
             }
         };
         // y reduction of an x-reduced node plane: one thread per node of the box
@@ -334,14 +334,14 @@ __global__ void __launch_bounds__(kNT, 1) gn_product_kernel(const __grid_constan
                         dst[(long)k * g.box + r] = (DG ? 1.f : 2.f) * v;
                     }
                 }
-                return;
-            }
-            const int np = (C1 + 1) * (C0 + 1);
-            for (int it = lane_major; it < 3 * np; it += kNT) {
-                const int k = idiv(it, invNP), r = it - k * np;
-                const int jy = idiv(r, invC0), jx = r - jy * (C0 + 1);
-                const float v = y_node_any<DG>(g.rho[1], xr + (kz & 1) * (kTY * XR) + jx * 3 + k, XR, jy, C1);
-                box[(long)k * g.box + (long)kz * np + r] = (DG ? 1.f : 2.f) * v;
+            } else {
+                const int np = (C1 + 1) * (C0 + 1);
+                for (int it = lane_major; it < 3 * np; it += kNT) {
+                    const int k = idiv(it, invNP), r = it - k * np;
+                    const int jy = idiv(r, invC0), jx = r - jy * (C0 + 1);
+                    const float v = y_node_any<DG>(g.rho[1], xr + (kz & 1) * (kTY * XR) + jx * 3 + k, XR, jy, C1);
+                    box[(long)k * g.box + (long)kz * np + r] = (DG ? 1.f : 2.f) * v;
+                }
             }
         };
 
