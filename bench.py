@@ -87,8 +87,8 @@ def alg_bytes(kernel, N, M):
 
 
 # source file of each timed kernel (the recorded ncu traffic is used only while it is unchanged)
-KSRC = {K_MATVEC: "gn_product.cu", K_GRADLIN: "ngf_grad.cu", K_OBJ: "ngf_grad.cu", K_VCC: "vcc.cu", K_VCC_GN: "vcc.cu",
-        K_CURV: "nodes.cu", K_FIN: "nodes.cu", K_VEC: "pcg.cu"}
+KSRC = {K_MATVEC: "gn_product_body.cuh", K_GRADLIN: "ngf_grad.cu", K_OBJ: "ngf_grad.cu", K_VCC: "vcc_body.cuh",
+        K_VCC_GN: "vcc_body.cuh", K_CURV: "nodes_body.cuh", K_FIN: "nodes_body.cuh", K_VEC: "pcg_body.cuh"}
 
 
 def recorded_traffic(kernel):
@@ -775,6 +775,15 @@ def batch_rates(params, dev, n_pairs=24, runs=(("host", 1), ("host", 4), ("graph
     res["runs"]["batched_graph"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
                                     "gn_matvec_per_s": mv / sec,
                                     "same_bits_as_first": bool(all(torch.equal(a, b) for a, b in zip(first, us)))}
+    # the same graphs with every pair's PCG steps (where the column GN-product
+    # kernel covers its level) in one persistent cooperative kernel per
+    # iteration; same bits
+    batch.register_batch_graph(pairs, params, persistent=True, **sched)
+    us, reps, sec, code = batch.register_batch_graph(pairs, params, persistent=True, **sched)
+    mv = int(sum(r[..., 6].sum() for r in reps))
+    res["runs"]["batched_persistent"] = {"pairs_per_min": 60.0 * n_pairs / sec, "seconds": sec,
+                                         "gn_matvec_per_s": mv / sec,
+                                         "same_bits_as_first": bool(all(torch.equal(a, b) for a, b in zip(first, us)))}
     # tile shapes picked per level geometry by the autotuner (timed on one
     # stream in an untimed pass and cached per process), graph drive, 8 streams
     batch.register_batch(pairs, params, workers=1, drive="graph", autotune=True, **sched)

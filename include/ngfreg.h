@@ -119,6 +119,17 @@ typedef struct {
 /* rg_schedule.flags: run rg_autotune on each level's context (at the start
  * iterate) before its Gauss-Newton steps.  Combines with the flags above. */
 #define RG_SCHED_AUTOTUNE 4
+/* rg_schedule.flags, register_pyramid_batch only: the PCG steps of every pair
+ * whose level the column GN-product kernel covers (volumes at least 68 voxels
+ * wide and 20 high, whole grid cells per axis) run in one persistent
+ * cooperative kernel per level iteration (up to 24 pairs per launch), whose
+ * CTAs take (pair, tile) items from a work counter phase by phase with
+ * bounded grid-barrier waits (RG_ETIMEOUT when one runs out).  Same bits per
+ * pair as without the flag.  RG_SCHED_HOOK_BARRIER is a test hook: the first
+ * grid barrier withholds one arrival and every wait runs out after a short
+ * poll count (no fault, no hang). */
+#define RG_SCHED_PERSISTENT 8
+#define RG_SCHED_HOOK_BARRIER 16
 
 typedef struct rg_ctx rg_ctx;
 
@@ -225,7 +236,8 @@ int register_pyramid(const rg_image_geom *img, const void *R_dev, const void *T_
  * paper has no counterpart).  Per pair p: img[p], R[p], T[p] (dtype shared),
  * fin[p], u_inout[p] and a workspace ws[p] of rg_pyramid_workspace_size(...,
  * nk_max = 0, ...) bytes (ws_bytes[p]); params and sched are shared, no
- * keypoints; 1 <= gn_iters <= 256 and sched->flags is ignored.  At each level
+ * keypoints; 1 <= gn_iters <= 256; of sched->flags only RG_SCHED_PERSISTENT
+ * and RG_SCHED_HOOK_BARRIER apply.  At each level
  * one CUDA graph holds every pair's Gauss-Newton iteration (line search
  * decided on the device) as a parallel branch and is replayed gn_iters times:
  * one graph launch advances all pairs.  Per pair the results have the bits of
@@ -259,9 +271,10 @@ int rg_prolong_grid(const int32_t *mc, const float *uc_dev, float *uf_dev, void 
  * more CTAs return RG_ESCRATCH.  A CTA covers a tile of 28 - 28 % rho_x voxels
  * in x (rho_x = n[0] / (m[0] - 1)), 16 in y and a z chunk of at most 32 slices
  * (fewer, whole grid cells, for large ratios), so the CTA count is
- * ceil(n[0] / tx) x ceil(n[1] / 16) x ceil(n[2] / tz).  Each call overwrites the partials before reading them.  All
- * calls share that array, so calls whose kernels overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
+ * ceil(n[0] / tx) x ceil(n[1] / 16) x ceil(n[2] / tz).  Each call overwrites
+ * the partials before reading them.  All calls share that array, so calls
+ * whose kernels overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.
  * The first call on each device looks the array's device address up with
  * cudaGetSymbolAddress on the current device; make that first call before
  * any stream capture.  Enqueued on cuda_stream; asynchronous. */

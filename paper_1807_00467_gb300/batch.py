@@ -56,15 +56,20 @@ def crop_pairs(R, T, h, shapes, grid_step=4):
     return out
 
 
-def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, stream=None, u0=None):
+def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, armijo_c=1e-4, stream=None, u0=None,
+                         persistent=False, hook_barrier=False):
     """All pairs (R, T, h, m) in lockstep through the multilevel schedule with
     one CUDA graph per level advancing every pair's Gauss-Newton iteration
-    (register_pyramid_batch); no host threads.  Returns (displacements,
-    reports, seconds, code): code is RG_OK, or the halting status (RG_EFOLD,
-    RG_ENONFINITE) of the lowest-numbered pair whose schedule halted; such a
-    pair keeps its start value and its report stops at the halting row, the
-    others are complete.  Other errors raise.  u0: start fields (finest grid)
-    per pair, default zero."""
+    (register_pyramid_batch); no host threads.  persistent: the PCG steps of
+    the pairs whose level the column GN-product kernel covers run in one
+    persistent cooperative kernel per iteration (RG_SCHED_PERSISTENT; same
+    bits); hook_barrier: test hook, that kernel's grid barriers run out
+    (RG_ETIMEOUT).  Returns (displacements, reports, seconds, code): code is
+    RG_OK, or the halting status (RG_EFOLD, RG_ENONFINITE) of the
+    lowest-numbered pair whose schedule halted; such a pair keeps its start
+    value and its report stops at the halting row, the others are complete.
+    Other errors raise.  u0: start fields (finest grid) per pair, default
+    zero."""
     import ctypes as C
 
     from . import _lib
@@ -93,6 +98,7 @@ def register_batch_graph(pairs, params, levels, gn_iters, pcg_iters, ls_max=10, 
         return C.cast(arr, C.c_void_p)
     rep = np.zeros((n, levels, gn_iters, _lib.RG_REPORT_COLS))
     sched = api.make_schedule(levels, gn_iters, pcg_iters, ls_max, armijo_c)
+    sched.flags = (_lib.RG_SCHED_PERSISTENT if persistent else 0) | (_lib.RG_SCHED_HOOK_BARRIER if hook_barrier else 0)
     wsa = (C.c_void_p * n)(*wps)
     wsp = C.cast(wsa, C.c_void_p)
     torch.cuda.synchronize(dev)

@@ -61,6 +61,7 @@ struct rg_ctx {
     GnState *gn;              // device side of a Gauss-Newton iteration
     double *gnrep;            // its report rows [kGnRows][RG_REPORT_COLS]
     double *range_terms;      // terms output of a d-range pass (volume term only)
+    unsigned *bctl;           // control words of a persistent batched PCG launch led by this context
     const int *skip;          // set while a line-search try is launched: the try's kernels skip when *skip
     cudaStream_t gst;         // private stream of device-driven schedules (created on first use)
     cudaEvent_t gev[2];
@@ -286,6 +287,7 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->gn = cv.take<GnState>(1);
     c->gnrep = cv.take<double>(RG_REPORT_COLS * kGnRows);
     c->range_terms = cv.take<double>(8);
+    c->bctl = cv.take<unsigned>(pcg_batch_ctl_words(c->pcg_max));
 }
 
 static void derive(rg_ctx *c) {
@@ -811,21 +813,8 @@ __global__ void pcg_stats_kernel(const PcgScalars *sc, double *stats) {
     stats[2] = sc->rend;
 }
 
-// PCG with full reorthogonalisation (classical Gram-Schmidt of each new
-// residual against all earlier ones in the preconditioner's inner product);
-// same iterates as plain PCG in exact arithmetic, kept so in FP32.  Scalars,
-// dots and coefficients in FP64.
-static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
-    if (iters > c->pcg_max)
-        return set_err(c, RG_EINVAL, "PCG: %d steps requested, the workspace holds %d (pcg_max)", iters, c->pcg_max);
-    if (((uintptr_t)g | (uintptr_t)p) & 15)
-        return set_err(c, RG_EINVAL, "PCG: g and p must be 16-byte aligned");
-    int st;
-    if ((st = ensure_minv(c))) return st;
-    if (!c->err_zeroed) {
-        CK(cudaMemsetAsync(c->tma_err, 0, 4 * sizeof(int), c->st));
-        c->err_zeroed = true;
-    }
+// The PCG's operands and vectors in the context's workspace.
+static PcgArgs pcg_args(rg_ctx *c) {
     PcgArgs a;
     a.n = 3 * c->M;
     a.stride = pcg_stride(a.n);
@@ -838,15 +827,28 @@ static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
     a.ticket = reinterpret_cast<unsigned *>(c->tma_err + 1);
     a.sc = c->sc;
     a.rzh = c->rzh;
-    LAUNCH(9, launch_pcg_start(a, g, p, c->st));
-    for (int k = 0; k < iters; ++k) {
-        int napart = 0;   // d.q partials: from the node pass, else from the alpha kernel
-        if ((st = matvec(c, c->d, c->q, c->apart, &napart))) return st;
-        if (!napart) LAUNCH(9, launch_pcg_alpha(a, c->q, &napart, c->st));
-        LAUNCH(9, launch_pcg_step(a, c->q, napart, k, c->st));
-        LAUNCH(9, launch_pcg_reorth(a, k, c->st));
-        LAUNCH(9, launch_pcg_dir(a, p, k, c->st));
+    return a;
+}
+
+// PCG set-up: the preconditioner (when stale) and the start vectors.
+static int pcg_prepare(rg_ctx *c, const float *g, float *p, int iters) {
+    if (iters > c->pcg_max)
+        return set_err(c, RG_EINVAL, "PCG: %d steps requested, the workspace holds %d (pcg_max)", iters, c->pcg_max);
+    if (((uintptr_t)g | (uintptr_t)p) & 15)
+        return set_err(c, RG_EINVAL, "PCG: g and p must be 16-byte aligned");
+    int st;
+    if ((st = ensure_minv(c))) return st;
+    if (!c->err_zeroed) {
+        CK(cudaMemsetAsync(c->tma_err, 0, 4 * sizeof(int), c->st));
+        c->err_zeroed = true;
     }
+    LAUNCH(9, launch_pcg_start(pcg_args(c), g, p, c->st));
+    return RG_OK;
+}
+
+// PCG wrap-up: the final residual norm and the statistics.
+static int pcg_finish(rg_ctx *c, double *stats) {
+    const PcgArgs a = pcg_args(c);
     const int nb = vec_blocks(a.n);
     LAUNCH(9, launch_dot_slot(a.n, c->Rh, a.stride, c->sc, c->vecpart, c->st));
     LAUNCH(9, launch_pcg_scalar(4, c->vecpart, nb, c->sc, c->st));
@@ -856,6 +858,86 @@ static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
         CK(cudaGetLastError());
     }
     return RG_OK;
+}
+
+// PCG with full reorthogonalisation (classical Gram-Schmidt of each new
+// residual against all earlier ones in the preconditioner's inner product);
+// same iterates as plain PCG in exact arithmetic, kept so in FP32.  Scalars,
+// dots and coefficients in FP64.
+static int pcg(rg_ctx *c, const float *g, float *p, int iters, double *stats) {
+    int st;
+    if ((st = pcg_prepare(c, g, p, iters))) return st;
+    const PcgArgs a = pcg_args(c);
+    for (int k = 0; k < iters; ++k) {
+        int napart = 0;   // d.q partials: from the node pass, else from the alpha kernel
+        if ((st = matvec(c, c->d, c->q, c->apart, &napart))) return st;
+        if (!napart) LAUNCH(9, launch_pcg_alpha(a, c->q, &napart, c->st));
+        LAUNCH(9, launch_pcg_step(a, c->q, napart, k, c->st));
+        LAUNCH(9, launch_pcg_reorth(a, k, c->st));
+        LAUNCH(9, launch_pcg_dir(a, p, k, c->st));
+    }
+    return pcg_finish(c, stats);
+}
+
+// Whether the persistent batched PCG (pcg_batch.cu) can take this context's
+// PCG steps: the column GN-product kernel covers its volume and H has no
+// keypoint term (its node sums use atomics outside the node pass).
+static bool batch_pcg_ok(const rg_ctx *c) { return !c->general_only && c->nk <= 0 && pcg_batch_supported(c->cg); }
+
+// The operands of one PCG step of the context (the GN product H d into q as
+// matvec forms it, the vectors of pcg), with s the PCG iterate.
+static void batch_pair(rg_ctx *c, float *s, BatchPair &b) {
+    ColArgs &a = b.col;
+    a = ColArgs();
+    a.g = c->cg;
+    a.v = c->d;
+    a.boxes = c->boxA;
+    a.map_dT = c->map_col_dT;
+    a.map_a = c->map_col_a;
+    a.err = c->tma_err;
+    a.skip = nullptr;
+    a.poll_limit = c->hook_poll;
+    a.no_tma = c->hook_no_tma;
+    const bool vcc = c->P.gamma != 0.0;
+    VccArgs &v = b.vcc;
+    v = VccArgs();
+    v.diag = 0;
+    for (int i = 0; i < 3; ++i) {
+        v.m[i] = c->grid.m[i];
+        v.ig[i] = (float)(1.0 / c->g[i]);
+        v.nb[i] = c->bB.nb[i];
+    }
+    v.box = c->bB.box;
+    v.u = c->lin_u;
+    v.v = c->d;
+    v.wscale = 1.f;
+    v.boxes = c->boxB;
+    v.epart = c->vpart;
+    v.fold = c->fold;
+    v.dmin = c->dmin;
+    v.dmax = c->dmax;
+    NodeArgs &n = b.nodes;
+    n = NodeArgs();
+    for (int i = 0; i < 3; ++i) {
+        n.m[i] = c->grid.m[i];
+        n.ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
+    }
+    n.boxA = c->boxA;
+    n.gA = c->bM;
+    n.sA = (float)c->hbar;
+    n.boxB = vcc ? c->boxB : nullptr;
+    n.gB = c->bB;
+    n.sB = (float)(c->P.gamma * c->ghat);
+    n.v = c->d;
+    n.w = c->curv_w;
+    n.sC = (float)(c->P.alpha * c->ghat);
+    n.rpart = nullptr;
+    n.out = c->q;
+    n.dvec = c->d;
+    n.dpart = c->apart;
+    b.pcg = pcg_args(c);
+    b.s = s;
+    b.vcc_on = vcc ? 1 : 0;
 }
 
 extern "C" int gn_pcg_solve(rg_ctx *c, const float *g, float *p, int32_t iters, double *stats) {
@@ -905,12 +987,20 @@ struct StreamSwap {   // the context's launches go to another stream for a scope
     ~StreamSwap() { c->st = saved; }
 };
 
-static int gn_iteration_device(rg_ctx *c, float *u, const rg_schedule *s) {
+// part: 0 the whole iteration; 1 up to the PCG start, 2 from the PCG
+// wrap-up on (the PCG steps in between run elsewhere: the persistent batched
+// PCG of register_pyramid_batch)
+static int gn_iteration_device(rg_ctx *c, float *u, const rg_schedule *s, int part = 0) {
     int st;
     const long n = 3 * c->M;
-    if ((st = evaluate(c, u, c->terms_tmp, c->tg_, true))) return st;
-    LAUNCH(9, launch_gn_begin(c->gn, c->terms_tmp, c->dminmax, c->st));
-    if ((st = pcg(c, c->tg_, c->ts, s->pcg_iters, c->terms_tmp + 5))) return st;
+    if (part != 2) {
+        if ((st = evaluate(c, u, c->terms_tmp, c->tg_, true))) return st;
+        LAUNCH(9, launch_gn_begin(c->gn, c->terms_tmp, c->dminmax, c->st));
+        if (part == 1) return pcg_prepare(c, c->tg_, c->ts, s->pcg_iters);
+        if ((st = pcg(c, c->tg_, c->ts, s->pcg_iters, c->terms_tmp + 5))) return st;
+    } else {
+        if ((st = pcg_finish(c, c->terms_tmp + 5))) return st;
+    }
     LAUNCH(9, launch_dot(n, c->tg_, c->ts, c->vecpart, c->st));
     LAUNCH(9, launch_gn_slope(c->gn, c->vecpart, vec_blocks(n), c->st));
     {
@@ -1309,6 +1399,8 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
     if (s->gn_iters < 1 || s->gn_iters > kGnRows || s->levels < 1 || s->levels > 8 || s->ls_max < 0)
         return RG_EINVAL;
     const int levels = s->levels, Lc = levels - 1;
+    const bool persistent = (s->flags & RG_SCHED_PERSISTENT) && s->pcg_iters >= 1;
+    const bool hook_barrier = (s->flags & RG_SCHED_HOOK_BARRIER) != 0;
     rg_ctx *c = nullptr;   // for CK / LAUNCH in this scope
     const size_t es = dtype == RG_F16 ? 2 : 4;
     struct Pair {
@@ -1349,7 +1441,9 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
         cudaStreamDestroy(st);
         return RG_ECUDA;
     }
-    std::vector<cudaEvent_t> join(npairs, nullptr);
+    // join[p]: pair p's first branch; join[npairs + p]: its branch after the
+    // persistent PCG launch; join[2 npairs]: the fork of those branches
+    std::vector<cudaEvent_t> join(2 * npairs + 1, nullptr);
     for (auto &e : join)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
     auto release = [&]() {
@@ -1442,9 +1536,14 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
             break;
         }
         int cst = cudaEventRecord(fork, st) == cudaSuccess ? RG_OK : RG_ECUDA;
+        // pairs whose PCG steps the persistent batched kernel takes (the rest
+        // run their whole iteration in their branch)
+        std::vector<int> pers;
         for (int p = 0; p < npairs && cst == RG_OK; ++p) {
             if (halted[p]) continue;
             rg_ctx *cl = ps[p].cl;
+            const bool inp = persistent && batch_pcg_ok(cl);
+            if (inp) pers.push_back(p);
             if (cudaStreamWaitEvent(cl->gst, fork, 0) != cudaSuccess) {
                 cst = RG_ECUDA;
                 break;
@@ -1452,13 +1551,46 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
             const long long l0 = cl->launches;
             {
                 StreamSwap sw(cl, cl->gst);
-                cst = gn_iteration_device(cl, ps[p].ul[l], s);
+                cst = gn_iteration_device(cl, ps[p].ul[l], s, inp ? 1 : 0);
             }
             counted += cl->launches - l0;
             cl->launches = l0;
             if (!cst && (cudaEventRecord(join[p], cl->gst) != cudaSuccess ||
                          cudaStreamWaitEvent(st, join[p], 0) != cudaSuccess))
                 cst = RG_ECUDA;
+        }
+        if (!cst && !pers.empty()) {
+            // every branch has joined: the cooperative launch has the GPU to itself
+            for (size_t g0 = 0; g0 < pers.size() && !cst; g0 += kBatchMax) {
+                const int ng = (int)std::min(pers.size() - g0, (size_t)kBatchMax);
+                std::vector<BatchPair> bp(ng);
+                for (int i = 0; i < ng; ++i) batch_pair(ps[pers[g0 + i]].cl, ps[pers[g0 + i]].cl->ts, bp[i]);
+                unsigned *ctl = ps[pers[g0]].cl->bctl;
+                if (cudaMemsetAsync(ctl, 0, sizeof(unsigned) * pcg_batch_ctl_words(s->pcg_iters), st) != cudaSuccess ||
+                    launch_pcg_batch(bp.data(), ng, s->pcg_iters, ctl, hook_barrier ? (1 << 12) : (1 << 22),
+                                     hook_barrier ? 1 : 0, st) != cudaSuccess)
+                    cst = RG_ECUDA;
+                counted += 1;
+            }
+            if (!cst && cudaEventRecord(join[2 * npairs], st) != cudaSuccess) cst = RG_ECUDA;
+            for (size_t i = 0; i < pers.size() && !cst; ++i) {
+                const int p = pers[i];
+                rg_ctx *cl = ps[p].cl;
+                if (cudaStreamWaitEvent(cl->gst, join[2 * npairs], 0) != cudaSuccess) {
+                    cst = RG_ECUDA;
+                    break;
+                }
+                const long long l0 = cl->launches;
+                {
+                    StreamSwap sw(cl, cl->gst);
+                    cst = gn_iteration_device(cl, ps[p].ul[l], s, 2);
+                }
+                counted += cl->launches - l0;
+                cl->launches = l0;
+                if (!cst && (cudaEventRecord(join[npairs + p], cl->gst) != cudaSuccess ||
+                             cudaStreamWaitEvent(st, join[npairs + p], 0) != cudaSuccess))
+                    cst = RG_ECUDA;
+            }
         }
         const cudaError_t ce = cudaStreamEndCapture(st, &g);
         g_launches.fetch_sub(counted, std::memory_order_relaxed);   // captured, not run

@@ -163,6 +163,29 @@ cudaError_t launch_gn_range(GnState *s, const double *dminmax, cudaStream_t st);
 cudaError_t launch_gn_report(GnState *s, const double *pcg_stats, double *rep, int rows, double det_lo, double det_hi,
                              cudaStream_t st);
 
+// Persistent batched PCG (pcg_batch.cu): the PCG steps of several volumes'
+// Gauss-Newton systems in one cooperative launch.  Per volume the operands of
+// one reorthogonalised PCG step after launch_pcg_start: the GN product of the
+// NGF term (column kernel, v = the search direction), the VCC product, the
+// curvature and node passes (out = q, d . q partials) and the vector state.
+struct BatchPair {
+    ColArgs col;           // GN product: v = d, boxes; its err flag also reports a barrier that gave up
+    VccArgs vcc;           // VCC product (u = linearisation point, v = d), used when vcc_on
+    NodeArgs nodes;        // curvature (v = d, w) and node pass (out = q, dpart = d . q partials)
+    PcgArgs pcg;           // vectors and device scalars
+    float *s;              // the solution (PCG iterate)
+    int vcc_on;
+};
+constexpr int kBatchMax = 24;   // volumes per launch (the descriptors travel as kernel parameters)
+// control words of one launch, zeroed before it: barrier arrivals, abort flag,
+// then one work counter per phase and PCG step
+inline size_t pcg_batch_ctl_words(int iters) { return 2 + 5 * (size_t)iters; }
+bool pcg_batch_supported(const ColGeom &g);
+// hook_skip: test hook, the first CTA does not arrive at the first grid
+// barrier (every CTA's bounded wait then runs out; RG_ETIMEOUT)
+cudaError_t launch_pcg_batch(const BatchPair *pairs, int npairs, int iters, unsigned *ctl, int poll_limit,
+                             int hook_skip, cudaStream_t st);
+
 // Pyramid.
 cudaError_t launch_restrict(const int *n, bool half, const void *in, void *out, cudaStream_t st);
 cudaError_t launch_prolong_grid(const int *mc, const float *uc, float *uf, cudaStream_t st);

@@ -1,173 +1,45 @@
-// Node passes of the gradient and the GN product.
-//
-// curv_kernel: w = L v per node and per-block partial sums of |L v|^2 (the
-// curvature energy of Eq. (5)); L is the sum over axes of the nodal 3-point
-// second differences at nodes interior to that axis, scaled by 1/g_a^2.
-//
-// node_kernel: per grid node k,
-//   out_k = sA (sum of the NGF node boxes holding k) + sB (sum of the VCC node
-//           boxes holding k) + sC (L^T w)_k,
-// optionally with per-block partials of d . out (the PCG step length).
-// The boxes holding a node come from per-axis lookups built once per block
-// (box index, local index, 1 or 2 boxes), so the gather has no per-node
-// integer division.  Blocks are 32 x 4 x 2 node tiles.  No atomics: the result
-// does not depend on scheduling.
-#include "common.cuh"
-#include "kernels.h"
+// Node passes of the gradient and the GN product: the launches of the bodies
+// in nodes_body.cuh (curvature L v with its energy partials; the node-box
+// gather with the curvature adjoint and the PCG's d . q partials).
+#include "nodes_body.cuh"
 
 namespace ngf {
 
 namespace {
 
-constexpr int NX = 32, NY = 4, NZ = 2, NT = NX * NY * NZ;
+using nodek::NT;
 
-// boxes of geometry b holding node k along axis ax: lo | local index << 16 | count << 24
-__device__ __forceinline__ int box_lookup(const BoxGeom &b, int ax, int k) {
-    const int C = b.C[ax];
-    const int hi = k / C;
-    const int lo = (hi >= 1 && k - hi * C == 0) ? hi - 1 : hi;
-    const int top = min(hi, b.nb[ax] - 1);
-    return lo | ((k - lo * C) << 16) | ((top - lo + 1) << 24);
+__global__ void __launch_bounds__(NT) curv_kernel(const NodeArgs a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
+    __shared__ nodek::NodeSmem sm;
+    nodek::curv_body<true>(a, cuda_block(), sm);
 }
 
-__device__ __forceinline__ void gather_boxes(const float *boxes, const BoxGeom &b, int tx, int ty, int tz, float &s0,
-                                             float &s1, float &s2) {
-    const int ncx = tx >> 24, ncy = ty >> 24, n = ncx * ncy * (tz >> 24);   // 1 or 2 boxes per axis
-    const int BX = b.C[0] + 1, BY = b.C[1] + 1;
-    // first box: its index and the node's offset in it; further boxes step back by one box and C nodes per axis
-    const unsigned cta0 = ((unsigned)(tz & 0xffff) * b.nb[1] + (ty & 0xffff)) * b.nb[0] + (tx & 0xffff);
-    const unsigned off0 = (((tz >> 16) & 0xff) * BY + ((ty >> 16) & 0xff)) * BX + ((tx >> 16) & 0xff);
-    const unsigned sz = 3u * b.box;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {   // at most 2 boxes per axis; all loads issued together
-        if (i >= n) break;
-        const int ix = i & (ncx - 1), iy = (i >> (ncx - 1)) & (ncy - 1), iz = i >> (ncx + ncy - 2);
-        const unsigned cta = cta0 + (iz * b.nb[1] + iy) * b.nb[0] + ix;
-        const unsigned off = off0 - (iz * b.C[2] * BY + iy * b.C[1]) * BX - ix * b.C[0];
-        const float *p = boxes + cta * sz + off;
-        s0 += __ldg(p);
-        s1 += __ldg(p + b.box);
-        s2 += __ldg(p + 2 * b.box);
-    }
+__global__ void __launch_bounds__(NT, 5) node_kernel(const NodeArgs a) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
+    __shared__ nodek::NodeSmem sm;
+    nodek::node_body<true>(a, cuda_block(), sm);
 }
 
 }  // namespace
 
-// w = L v per node (3 components) and per-block partials of |L v|^2.
-__global__ void __launch_bounds__(NT) curv_kernel(const NodeArgs a) {
-    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
-    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
-    const long mxy = (long)mx * my, M = mxy * mz;
-    const int kx = blockIdx.x * NX + (int)threadIdx.x % NX, ky = blockIdx.y * NY + ((int)threadIdx.x / NX) % NY;
-    const int kz = blockIdx.z * NZ + (int)threadIdx.x / (NX * NY);
-    float e = 0.f;
-    if (kx < mx && ky < my && kz < mz) {
-        const long k = (long)kz * mxy + (long)ky * mx + kx;
-        const bool ix = kx >= 1 && kx <= mx - 2, iy = ky >= 1 && ky <= my - 2, iz = kz >= 1 && kz <= mz - 2;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float *v = a.v + c * M + k;
-            const float v0 = __ldg(v);
-            float w = 0.f;
-            if (ix) w = fmaf(__ldg(v + 1) - 2.f * v0 + __ldg(v - 1), a.ig2[0], w);
-            if (iy) w = fmaf(__ldg(v + mx) - 2.f * v0 + __ldg(v - mx), a.ig2[1], w);
-            if (iz) w = fmaf(__ldg(v + mxy) - 2.f * v0 + __ldg(v - mxy), a.ig2[2], w);
-            a.w[c * M + k] = w;
-            e = fmaf(w, w, e);
-        }
-    }
-    if (a.rpart) {
-        // FP32 within the warp (a tree of non-negative terms: relative error <= 5 ulp), FP64 across warps
-        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-        __shared__ double red[NT / 32];
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)e;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < NT / 32; ++i) s += red[i];
-            a.rpart[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
-        }
-    }
-}
-
-// out = sA (NGF boxes) + sB (VCC boxes) + sC L^T w (and, with dpart, the
-// per-block partials of dvec . out)
-__global__ void __launch_bounds__(NT, 5) node_kernel(const NodeArgs a) {
-    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
-    __shared__ int tabA[NX + NY + NZ], tabB[NX + NY + NZ];
-    const int tid = threadIdx.x;
-    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
-    const long mxy = (long)mx * my, M = mxy * mz;
-    const int x0 = blockIdx.x * NX, y0 = blockIdx.y * NY, z0 = blockIdx.z * NZ;
-    if (tid < NX + NY + NZ) {
-        const int ax = tid < NX ? 0 : (tid < NX + NY ? 1 : 2);
-        const int k = ax == 0 ? x0 + tid : (ax == 1 ? y0 + tid - NX : z0 + tid - NX - NY);
-        const int kc = min(k, a.m[ax] - 1);   // nodes beyond the grid are not written
-        if (a.boxA) tabA[tid] = box_lookup(a.gA, ax, kc);
-        if (a.boxB) tabB[tid] = box_lookup(a.gB, ax, kc);
-    }
-    __syncthreads();
-    const int lx = tid % NX, ly = (tid / NX) % NY, lz = tid / (NX * NY);
-    const int kx = x0 + lx, ky = y0 + ly, kz = z0 + lz;
-    float dq = 0.f;   // dvec . out over this thread's node
-    if (kx < mx && ky < my && kz < mz) {
-        float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
-        if (a.boxA) gather_boxes(a.boxA, a.gA, tabA[lx], tabA[NX + ly], tabA[NX + NY + lz], sa[0], sa[1], sa[2]);
-        if (a.boxB) gather_boxes(a.boxB, a.gB, tabB[lx], tabB[NX + ly], tabB[NX + NY + lz], sb[0], sb[1], sb[2]);
-        const unsigned k = ((unsigned)kz * my + ky) * mx + kx, Mu = (unsigned)M, sy = mx, sz = (unsigned)mxy;
-        const bool ix = kx >= 1 && kx <= mx - 2, iy = ky >= 1 && ky <= my - 2, iz = kz >= 1 && kz <= mz - 2;
-        const bool xm = kx - 1 >= 1, xp = kx + 1 <= mx - 2, ym = ky - 1 >= 1, yp = ky + 1 <= my - 2;
-        const bool zm = kz - 1 >= 1, zp = kz + 1 <= mz - 2;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float o = a.sA * sa[c] + a.sB * sb[c];
-            if (a.w) {
-                // L^T w: the rows of L that reference node k along each axis
-                const float *p = a.w + c * Mu + k;
-                const float w0 = __ldg(p);
-                float tx = 0.f, ty = 0.f, tz = 0.f;
-                if (ix) tx -= 2.f * w0;
-                if (xm) tx += __ldg(p - 1);
-                if (xp) tx += __ldg(p + 1);
-                if (iy) ty -= 2.f * w0;
-                if (ym) ty += __ldg(p - sy);
-                if (yp) ty += __ldg(p + sy);
-                if (iz) tz -= 2.f * w0;
-                if (zm) tz += __ldg(p - sz);
-                if (zp) tz += __ldg(p + sz);
-                o = fmaf(a.sC, fmaf(tz, a.ig2[2], fmaf(ty, a.ig2[1], tx * a.ig2[0])), o);
-            }
-            a.out[c * Mu + k] = o;
-            if (a.dpart) dq = fmaf(__ldg(a.dvec + c * Mu + k), o, dq);
-        }
-    }
-    if (a.dpart) {
-        // FP32 within the warp, FP64 across warps (the PCG's d.q partials)
-        for (int off = 16; off > 0; off >>= 1) dq += __shfl_xor_sync(0xffffffffu, dq, off);
-        __shared__ double red[NT / 32];
-        if ((tid & 31) == 0) red[tid >> 5] = (double)dq;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int i = 0; i < NT / 32; ++i) s += red[i];
-            a.dpart[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
-        }
-    }
-}
-
 int node_blocks(const int *m) {
-    return ((m[0] + NX - 1) / NX) * ((m[1] + NY - 1) / NY) * ((m[2] + NZ - 1) / NZ);
+    int gx, gy, gz;
+    nodek::node_grid(m, gx, gy, gz);
+    return gx * gy * gz;
 }
 
 cudaError_t launch_curv(const NodeArgs &a, cudaStream_t st) {
-    const dim3 grid((a.m[0] + NX - 1) / NX, (a.m[1] + NY - 1) / NY, (a.m[2] + NZ - 1) / NZ);
-    curv_kernel<<<grid, NT, 0, st>>>(a);
+    int gx, gy, gz;
+    nodek::node_grid(a.m, gx, gy, gz);
+    curv_kernel<<<dim3(gx, gy, gz), NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_nodes(const NodeArgs &a, cudaStream_t st) {
-    const dim3 grid((a.m[0] + NX - 1) / NX, (a.m[1] + NY - 1) / NY, (a.m[2] + NZ - 1) / NZ);
-    node_kernel<<<grid, NT, 0, st>>>(a);
+    int gx, gy, gz;
+    nodek::node_grid(a.m, gx, gy, gz);
+    node_kernel<<<dim3(gx, gy, gz), NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
