@@ -123,11 +123,11 @@ typedef struct {
  * whose level the column GN-product kernel covers (volumes at least 68 voxels
  * wide and 20 high, whole grid cells per axis) run in one persistent
  * cooperative kernel per level iteration (up to 24 pairs per launch), whose
- * CTAs take (pair, tile) items from a work counter phase by phase with
- * bounded grid-barrier waits (RG_ETIMEOUT when one runs out).  Same bits per
- * pair as without the flag.  RG_SCHED_HOOK_BARRIER is a test hook: the first
- * grid barrier withholds one arrival and every wait runs out after a short
- * poll count (no fault, no hang). */
+ * CTAs take (pair, tile) items from a work counter, each waiting (bounded;
+ * RG_ETIMEOUT when a wait runs out) for the previous phase of its own pair.
+ * Same bits per pair as without the flag.  RG_SCHED_HOOK_BARRIER is a test
+ * hook: the first item's completion is withheld, so the waits on it run out
+ * after a short poll count (no fault, no hang). */
 #define RG_SCHED_PERSISTENT 8
 #define RG_SCHED_HOOK_BARRIER 16
 

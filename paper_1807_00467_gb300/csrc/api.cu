@@ -287,7 +287,7 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->gn = cv.take<GnState>(1);
     c->gnrep = cv.take<double>(RG_REPORT_COLS * kGnRows);
     c->range_terms = cv.take<double>(8);
-    c->bctl = cv.take<unsigned>(pcg_batch_ctl_words(c->pcg_max));
+    c->bctl = cv.take<unsigned>(kBatchCtlWords);
 }
 
 static void derive(rg_ctx *c) {
@@ -1566,7 +1566,7 @@ extern "C" int register_pyramid_batch(int32_t npairs, const rg_image_geom *img, 
                 std::vector<BatchPair> bp(ng);
                 for (int i = 0; i < ng; ++i) batch_pair(ps[pers[g0 + i]].cl, ps[pers[g0 + i]].cl->ts, bp[i]);
                 unsigned *ctl = ps[pers[g0]].cl->bctl;
-                if (cudaMemsetAsync(ctl, 0, sizeof(unsigned) * pcg_batch_ctl_words(s->pcg_iters), st) != cudaSuccess ||
+                if (cudaMemsetAsync(ctl, 0, sizeof(unsigned) * kBatchCtlWords, st) != cudaSuccess ||
                     launch_pcg_batch(bp.data(), ng, s->pcg_iters, ctl, hook_barrier ? (1 << 12) : (1 << 22),
                                      hook_barrier ? 1 : 0, st) != cudaSuccess)
                     cst = RG_ECUDA;

@@ -177,12 +177,13 @@ struct BatchPair {
     int vcc_on;
 };
 constexpr int kBatchMax = 24;   // volumes per launch (the descriptors travel as kernel parameters)
-// control words of one launch, zeroed before it: barrier arrivals, abort flag,
-// then one work counter per phase and PCG step
-inline size_t pcg_batch_ctl_words(int iters) { return 2 + 5 * (size_t)iters; }
+// control words of one launch, zeroed before it: the work counter, the abort
+// flag and per volume one completion counter per phase, each group on a
+// 128-byte line of its own
+constexpr size_t kBatchCtlWords = 64 + 32 * (size_t)kBatchMax;
 bool pcg_batch_supported(const ColGeom &g);
-// hook_skip: test hook, the first CTA does not arrive at the first grid
-// barrier (every CTA's bounded wait then runs out; RG_ETIMEOUT)
+// hook_skip: test hook, the first item's completion is withheld (the waits on
+// it run out; RG_ETIMEOUT)
 cudaError_t launch_pcg_batch(const BatchPair *pairs, int npairs, int iters, unsigned *ctl, int poll_limit,
                              int hook_skip, cudaStream_t st);
 

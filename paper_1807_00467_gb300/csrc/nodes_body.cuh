@@ -78,12 +78,10 @@ struct NodeSmem {
 };
 
 // w = L v per node (3 components) and per-block partials of |L v|^2; block
-// b.bid is the node tile (bx, by, bz) of a gx x gy x gz tiling.
+// (b.x, b.y, b.z) is a node tile of the node_grid tiling, b.bid its index.
 template <bool RO>
 __device__ __forceinline__ void curv_body(const NodeArgs &a, const VBlock &b, NodeSmem &sm) {
-    int gx, gy, gz;
-    node_grid(a.m, gx, gy, gz);
-    const int bx = b.bid % gx, by = (b.bid / gx) % gy, bz = b.bid / (gx * gy);
+    const int bx = b.x, by = b.y, bz = b.z;
     const int mx = a.m[0], my = a.m[1], mz = a.m[2];
     const long mxy = (long)mx * my, M = mxy * mz;
     const int kx = bx * NX + b.tid % NX, ky = by * NY + (b.tid / NX) % NY;
@@ -121,9 +119,7 @@ __device__ __forceinline__ void curv_body(const NodeArgs &a, const VBlock &b, No
 // per-block partials of dvec . out)
 template <bool RO>
 __device__ __forceinline__ void node_body(const NodeArgs &a, const VBlock &b, NodeSmem &sm) {
-    int gx, gy, gz;
-    node_grid(a.m, gx, gy, gz);
-    const int bx = b.bid % gx, by = (b.bid / gx) % gy, bz = b.bid / (gx * gy);
+    const int bx = b.x, by = b.y, bz = b.z;
     const int tid = b.tid;
     const int mx = a.m[0], my = a.m[1], mz = a.m[2];
     const long mxy = (long)mx * my, M = mxy * mz;

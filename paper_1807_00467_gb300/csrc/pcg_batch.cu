@@ -4,7 +4,7 @@
 // objective of Eq. (11)).
 //
 // One CTA per SM (640 threads, the GN-product kernel's shape) runs every PCG
-// step k of every volume as five grid-wide phases:
+// step k of every volume as five phases:
 //   A  H d pieces: the NGF GN product of every column (gn_product_body), the
 //      VCC product of every cell block (vcc_cell_body, five 128-thread blocks
 //      per item) and the curvature L d of every node tile (curv_body, two
@@ -13,18 +13,20 @@
 //   C  step:   alpha, r' = r - alpha q, Gram-Schmidt coefficient partials;
 //   D  reorth: r_{k+1} = r' - sum_j c_j r_j and the partials of r . z;
 //   E  dir:    beta, s += alpha d, d = z + beta d    (pcg_body.cuh).
-// Within a phase the CTAs take (volume, unit) items from an atomic work
-// counter, largest units first; the phases are separated by grid barriers.
+// The CTAs take (volume, unit) items from one atomic work counter in the
+// order (step, phase, volume, unit).  An item waits only for the previous
+// phase of its own volume (per-volume completion counters), whose items all
+// come earlier in that order and are held by running CTAs, so phases of
+// different volumes overlap and nothing waits for a CTA that is not running.
 // Every item runs the same code with the same partition and reduction order
 // as the per-volume kernels, so each volume's iterates equal those of its
 // own launches bit for bit.  Each volume keeps its own FP64 device scalars.
 //
-// Grid barrier: one arrival per CTA (release), then thread 0 polls the count
-// (acquire) with a bounded number of polls; a CTA whose wait runs out raises
+// Waits: thread 0 polls the counter with a growing pause, for a bounded
+// number of polls and at most two seconds; a CTA whose wait runs out raises
 // the launch's abort flag and every volume's error flag (the caller reports
-// RG_ETIMEOUT), and every CTA leaves at its next barrier.  The launch is
-// cooperative, so all CTAs are resident and a barrier only runs out when a
-// test hook withholds an arrival.
+// RG_ETIMEOUT), and the other CTAs leave at their next wait.  The launch is cooperative, so all CTAs are resident and a
+// wait only runs out when a test hook withholds a completion.
 #include "gn_product_body.cuh"
 #include "nodes_body.cuh"
 #include "pcg_body.cuh"
@@ -38,8 +40,11 @@ namespace ngf {
 namespace {
 
 using gnpk::kNT;
-constexpr int kVccPer = kNT / vcck::NC;        // VCC cell blocks per item (5 x 128 threads)
-constexpr int kNodePer = kNT / nodek::NT;      // node tiles per item (2 x 256 threads, 128 idle)
+constexpr int kVccRun = kNT / vcck::NC;        // VCC cell blocks at once (5 x 128 threads)
+constexpr int kNodeRun = kNT / nodek::NT;      // node tiles at once (2 x 256 threads, 128 idle)
+// units per work item: the light phases take several rounds per item, so the
+// per-item cost (work counter, completion record) stays small
+constexpr int kVccPer = 4 * kVccRun, kNodePer = 8 * kNodeRun, kVecPer = 2;
 static_assert(pcgk::kVT <= kNT, "a PCG vector block fits in a CTA");
 
 struct KPair {
@@ -47,6 +52,7 @@ struct KPair {
     pcgk::Part part;       // vector partition (pcg_body.cuh)
     int nvec;              // vector blocks
     int ncols, nvcc, nnode;
+    int nA, nB, nV;        // items of phase A (columns, VCC groups, curvature groups), B and each vector phase
     int rz, rxy;           // GN-product specialisation: rho_z ring phases (0: generic), rho 4 x 4
 };
 
@@ -57,7 +63,7 @@ struct KArgs {
     // curvature groups), phase B and the vector phases; [npairs] = totals
     int colOff[kBatchMax + 1], vccOff[kBatchMax + 1], curvOff[kBatchMax + 1];
     int nodeOff[kBatchMax + 1], vecOff[kBatchMax + 1];
-    unsigned *ctl;
+    unsigned *ctl;         // control words (kCtlAbort, done_ctr)
     int poll_limit;
     int hook_skip;
 };
@@ -69,38 +75,64 @@ __device__ __forceinline__ int find_pair(const int *off, int n, int item) {
     return p;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
+// Control words (kBatchCtlWords): the work counter and the abort flag on
+// lines of their own, then one 128-byte line per volume holding its five
+// completion counters, so that polls of one volume's counters do not contend
+// with the atomics of the others.
+constexpr int kCtlAbort = 32, kCtlDone = 64, kCtlLine = 32;
+__device__ __forceinline__ unsigned *done_ctr(const KArgs &A, int p, int ph) {
+    return A.ctl + kCtlDone + kCtlLine * p + ph;
 }
 
-// Grid barrier number `nbar` (1, 2, ...).  False: the launch was aborted.
-__device__ __forceinline__ bool grid_barrier(const KArgs &A, unsigned nbar, int *s_ok) {
-    __syncthreads();
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until pair p's phase ph has completed `need` items: thread 0 polls
+// with relaxed loads and a growing pause (up to ~4 us) for at most
+// poll_limit polls or two seconds, then one acquire fence; the CTA then
+// proceeds.  False: the launch was aborted (this wait or another CTA's ran out).
+__device__ __forceinline__ bool wait_done(const KArgs &A, int p, int ph, unsigned need, int *s_ok) {
     if (threadIdx.x == 0) {
-        const unsigned target = nbar * gridDim.x;
-        __threadfence();
-        if (!(A.hook_skip && nbar == 1 && blockIdx.x == 0)) atomicAdd(&A.ctl[0], 1u);
+        const volatile unsigned *ctr = done_ctr(A, p, ph);
+        const volatile unsigned *abort_flag = A.ctl + kCtlAbort;
         int ok = 1;
-        for (int it = 0; ld_acquire(&A.ctl[0]) < target; ++it) {
-            if (*(volatile unsigned *)&A.ctl[1]) {
-                ok = 0;
-                break;
+        if (*ctr < need) {
+            const unsigned long long t0 = global_ns();
+            unsigned pause = 32;
+            for (int it = 0; *ctr < need; ++it) {
+                if (*abort_flag) {
+                    ok = 0;
+                    break;
+                }
+                if (it > A.poll_limit || global_ns() - t0 > 2000000000ull) {
+                    atomicExch(A.ctl + kCtlAbort, 1u);
+                    for (int q = 0; q < A.npairs; ++q) atomicExch(A.p[q].b.col.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(pause);
+                if (pause < 4096) pause *= 2;
             }
-            if (it > A.poll_limit) {
-                atomicExch(&A.ctl[1], 1u);
-                for (int q = 0; q < A.npairs; ++q) atomicExch(A.p[q].b.col.err, 1);
-                ok = 0;
-                break;
-            }
-            __nanosleep(64);
         }
         __threadfence();
         *s_ok = ok;
     }
     __syncthreads();
     return *s_ok != 0;
+}
+
+// Record one completed item of pair p's phase ph (after every thread's
+// writes).  Test hook: the launch's first item is never recorded, so the
+// waits of its pair's next phase run out.
+__device__ __forceinline__ void item_done(const KArgs &A, int p, int ph, int it) {
+    __syncthreads();
+    if (threadIdx.x == 0 && !(A.hook_skip && it == 0)) {
+        __threadfence();
+        atomicAdd(done_ctr(A, p, ph), 1u);
+    }
 }
 
 // The next item of a phase's work counter (the same value in every thread).
@@ -110,6 +142,13 @@ __device__ __forceinline__ int next_item(unsigned *ctr, int *s_item) {
     const int it = *s_item;
     __syncthreads();
     return it;
+}
+
+// Node tile bid of a volume as block v (256 threads, named barrier 1 + v) of a CTA.
+__device__ __forceinline__ VBlock node_block(const KPair &P, int tid, int bid, int v) {
+    int gx, gy, gz;
+    nodek::node_grid(P.b.nodes.m, gx, gy, gz);
+    return warp_block(tid % nodek::NT, bid, gx, gy, gz, 1 + v, nodek::NT);
 }
 
 __device__ __forceinline__ void gn_column(const KPair &P, float *smem, uint64_t *bars, int t, uint32_t &pbits) {
@@ -135,72 +174,88 @@ __global__ void __launch_bounds__(kNT, 1) pcg_batch_kernel(const __grid_constant
     }
     __syncthreads();
     uint32_t pbits = 0;
-    unsigned nbar = 0;
     const int np = A.npairs;
     const int nA = A.curvOff[np], nB = A.nodeOff[np], nV = A.vecOff[np];
-    for (int k = 0; k < A.iters; ++k) {
-        unsigned *ctr = A.ctl + 2 + 5 * k;
-        // ---------------------------------------------------------------- A: H d pieces
-        for (int it; (it = next_item(ctr, &s_item)) < nA;) {
-            if (it < A.colOff[np]) {
-                const int p = find_pair(A.colOff, np, it);
-                gn_column(A.p[p], smem, bars, it - A.colOff[p], pbits);
-            } else if (it < A.vccOff[np]) {
-                const int p = find_pair(A.vccOff, np, it);
-                const KPair &P = A.p[p];
-                const int v = tid / vcck::NC, bid = (it - A.vccOff[p]) * kVccPer + v;
-                if (bid < P.nvcc) {
-                    VBlock b{tid % vcck::NC, bid, P.nvcc, 1 + v, vcck::NC};
+    const int per_step = nA + nB + 3 * nV;
+    // items in the order (step, phase, pair, unit); an item waits only for the
+    // previous phase of its own pair, whose items all come earlier in the order
+    for (int it; (it = next_item(A.ctl, &s_item)) < A.iters * per_step;) {
+        const int k = it / per_step;
+        int r = it - k * per_step;
+        if (r < nA) {
+            // ---------------------------------------------------------------- A: H d pieces
+            int p;
+            if (r < A.colOff[np]) p = find_pair(A.colOff, np, r);
+            else if (r < A.vccOff[np]) p = find_pair(A.vccOff, np, r);
+            else p = find_pair(A.curvOff, np, r);
+            const KPair &P = A.p[p];
+            if (k > 0 && !wait_done(A, p, 4, (unsigned)k * P.nV, &s_ok)) return;
+            if (r < A.colOff[np]) {
+                gn_column(P, smem, bars, r - A.colOff[p], pbits);
+            } else if (r < A.vccOff[np]) {
+                const int v = tid / vcck::NC;
+                const int *nb = P.b.vcc.nb;
+                for (int bid = (r - A.vccOff[p]) * kVccPer + v, e = min(bid - v + kVccPer, P.nvcc); bid < e;
+                     bid += kVccRun) {
+                    const VBlock b = warp_block(tid % vcck::NC, bid, nb[0], nb[1], nb[2], 1 + v, vcck::NC);
                     vcck::vcc_cell_body<1>(P.b.vcc, b, reinterpret_cast<vcck::VccSmem *>(smem)[v]);
                 }
             } else {
-                const int p = find_pair(A.curvOff, np, it);
-                const KPair &P = A.p[p];
-                const int v = tid / nodek::NT, bid = (it - A.curvOff[p]) * kNodePer + v;
-                if (v < kNodePer && bid < P.nnode) {
-                    VBlock b{tid % nodek::NT, bid, P.nnode, 1 + v, nodek::NT};
-                    nodek::curv_body<false>(P.b.nodes, b, reinterpret_cast<nodek::NodeSmem *>(smem)[v]);
-                }
+                const int v = tid / nodek::NT;
+                if (v < kNodeRun)
+                    for (int bid = (r - A.curvOff[p]) * kNodePer + v, e = min(bid - v + kNodePer, P.nnode); bid < e;
+                         bid += kNodeRun)
+                        nodek::curv_body<false>(P.b.nodes, node_block(P, tid, bid, v),
+                                                reinterpret_cast<nodek::NodeSmem *>(smem)[v]);
             }
+            item_done(A, p, 0, it);
+            continue;
         }
-        if (!grid_barrier(A, ++nbar, &s_ok)) return;
-        // ---------------------------------------------------------------- B: node pass, d . q partials
-        for (int it; (it = next_item(ctr + 1, &s_item)) < nB;) {
-            const int p = find_pair(A.nodeOff, np, it);
+        r -= nA;
+        if (r < nB) {
+            // ---------------------------------------------------------------- B: node pass, d . q partials
+            const int p = find_pair(A.nodeOff, np, r);
             const KPair &P = A.p[p];
-            const int v = tid / nodek::NT, bid = (it - A.nodeOff[p]) * kNodePer + v;
-            if (v < kNodePer && bid < P.nnode) {
-                VBlock b{tid % nodek::NT, bid, P.nnode, 1 + v, nodek::NT};
-                nodek::node_body<false>(P.b.nodes, b, reinterpret_cast<nodek::NodeSmem *>(smem)[v]);
-            }
+            if (!wait_done(A, p, 0, (unsigned)(k + 1) * P.nA, &s_ok)) return;
+            const int v = tid / nodek::NT;
+            if (v < kNodeRun)
+                for (int bid = (r - A.nodeOff[p]) * kNodePer + v, e = min(bid - v + kNodePer, P.nnode); bid < e;
+                     bid += kNodeRun)
+                    nodek::node_body<false>(P.b.nodes, node_block(P, tid, bid, v),
+                                            reinterpret_cast<nodek::NodeSmem *>(smem)[v]);
+            item_done(A, p, 1, it);
+            continue;
         }
-        if (!grid_barrier(A, ++nbar, &s_ok)) return;
-        // ---------------------------------------------------------------- C, D, E: the vector phases
-        for (int ph = 0; ph < 3; ++ph) {
-            for (int it; (it = next_item(ctr + 2 + ph, &s_item)) < nV;) {
-                const int p = find_pair(A.vecOff, np, it);
-                const KPair &P = A.p[p];
-                if (tid >= pcgk::kVT) continue;
-                const VBlock b{tid, it - A.vecOff[p], P.nvec, 1, pcgk::kVT};
-                const PcgArgs &g = P.b.pcg;
-                pcgk::PcgSmem &sm = *reinterpret_cast<pcgk::PcgSmem *>(smem);
-                if (ph == 0)
-                    pcgk::pcg_step_body(P.part, g.sc, g.apart, P.nnode, P.b.nodes.out, g.minv, g.Rh, g.stride, k,
-                                        g.part, b, sm);
-                else if (ph == 1)
-                    pcgk::pcg_reorth_body(P.part, g.sc, g.minv, g.Rh, g.stride, k, g.rzh, g.part, g.rzpart, b, sm);
-                else
-                    pcgk::pcg_dir_body(P.part, g.sc, g.minv, g.Rh + (long)(k + 1) * g.stride, g.d, P.b.s, k, g.rzh,
-                                       g.rzpart, b, sm);
-            }
-            if ((k + 1 < A.iters || ph < 2) && !grid_barrier(A, ++nbar, &s_ok)) return;
+        // -------------------------------------------------------------------- C, D, E: the vector phases
+        r -= nB;
+        const int ph = r / nV;
+        r -= ph * nV;
+        const int p = find_pair(A.vecOff, np, r);
+        const KPair &P = A.p[p];
+        const unsigned need = (unsigned)(k + 1) * (ph == 0 ? P.nB : P.nV);
+        if (!wait_done(A, p, 1 + ph, need, &s_ok)) return;
+        const int b0 = (r - A.vecOff[p]) * kVecPer;
+        for (int vb = b0; tid < pcgk::kVT && vb < min(b0 + kVecPer, P.nvec); ++vb) {
+            const VBlock b = warp_block(tid, vb, P.nvec, 1, 1, 1, pcgk::kVT);
+            const PcgArgs &g = P.b.pcg;
+            pcgk::PcgSmem &sm = *reinterpret_cast<pcgk::PcgSmem *>(smem);
+            if (vb > b0) b.sync();   // the last block's reads of the shared scratch are done
+            if (ph == 0)
+                pcgk::pcg_step_body(P.part, g.sc, g.apart, P.nnode, P.b.nodes.out, g.minv, g.Rh, g.stride, k, g.part,
+                                    b, sm);
+            else if (ph == 1)
+                pcgk::pcg_reorth_body(P.part, g.sc, g.minv, g.Rh, g.stride, k, g.rzh, g.part, g.rzpart, b, sm);
+            else
+                pcgk::pcg_dir_body(P.part, g.sc, g.minv, g.Rh + (long)(k + 1) * g.stride, g.d, P.b.s, k, g.rzh,
+                                   g.rzpart, b, sm);
         }
+        item_done(A, p, 2 + ph, it);
     }
 }
 
 size_t batch_smem(const KArgs &A) {
     size_t s = std::max(sizeof(pcgk::PcgSmem),
-                        std::max(kVccPer * sizeof(vcck::VccSmem), kNodePer * sizeof(nodek::NodeSmem)));
+                        std::max(kVccRun * sizeof(vcck::VccSmem), kNodeRun * sizeof(nodek::NodeSmem)));
     for (int p = 0; p < A.npairs; ++p) s = std::max(s, sizeof(float) * (size_t)gnpk::pc_smem(A.p[p].b.col.g).total);
     return s;
 }
@@ -237,6 +292,9 @@ cudaError_t launch_pcg_batch(const BatchPair *pairs, int npairs, int iters, unsi
         P.nnode = node_blocks(g.m);
         P.rz = (g.rho[2] == 2 || g.rho[2] == 4) ? g.rho[2] : 0;
         P.rxy = (g.rho[0] == 4 && g.rho[1] == 4) ? 4 : 0;
+        P.nB = (P.nnode + kNodePer - 1) / kNodePer;
+        P.nA = P.ncols + (P.nvcc + kVccPer - 1) / kVccPer + P.nB;
+        P.nV = (P.nvec + kVecPer - 1) / kVecPer;
     }
     // item offsets: phase A holds every column, then every VCC group, then
     // every curvature group
@@ -251,7 +309,7 @@ cudaError_t launch_pcg_batch(const BatchPair *pairs, int npairs, int iters, unsi
     for (int p = 0; p < npairs; ++p) { A.nodeOff[p] = n; n += (A.p[p].nnode + kNodePer - 1) / kNodePer; }
     A.nodeOff[npairs] = n;
     n = 0;
-    for (int p = 0; p < npairs; ++p) { A.vecOff[p] = n; n += A.p[p].nvec; }
+    for (int p = 0; p < npairs; ++p) { A.vecOff[p] = n; n += A.p[p].nV; }
     A.vecOff[npairs] = n;
 
     const size_t smem = batch_smem(A);

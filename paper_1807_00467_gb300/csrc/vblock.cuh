@@ -14,6 +14,7 @@ struct VBlock {
     int nblk;   // blocks in the launch
     int bar;    // 0: the CUDA block (__syncthreads), else a named barrier id
     int nt;     // threads of the block (a multiple of 32)
+    int x, y, z;   // block coordinates of a three-dimensional launch (bid = (z ny + y) nx + x)
     __device__ __forceinline__ void sync() const {
         if (bar == 0) __syncthreads();
         else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
@@ -28,6 +29,24 @@ __device__ __forceinline__ VBlock cuda_block() {
     b.nblk = gridDim.x * gridDim.y * gridDim.z;
     b.bar = 0;
     b.nt = blockDim.x;
+    b.x = blockIdx.x;
+    b.y = blockIdx.y;
+    b.z = blockIdx.z;
+    return b;
+}
+
+// A block of a persistent CTA: warps [w0, w0 + nt / 32), named barrier bar,
+// block bid of a launch of nx x ny x nz blocks.
+__device__ __forceinline__ VBlock warp_block(int tid, int bid, int nx, int ny, int nz, int bar, int nt) {
+    VBlock b;
+    b.tid = tid;
+    b.bid = bid;
+    b.nblk = nx * ny * nz;
+    b.bar = bar;
+    b.nt = nt;
+    b.x = bid % nx;
+    b.y = (bid / nx) % ny;
+    b.z = bid / (nx * ny);
     return b;
 }
 
@@ -39,6 +58,8 @@ __device__ __forceinline__ VBlock cuda_block_1d() {
     b.nblk = gridDim.x;
     b.bar = 0;
     b.nt = blockDim.x;
+    b.x = blockIdx.x;
+    b.y = b.z = 0;
     return b;
 }
 

@@ -80,8 +80,7 @@ __device__ __forceinline__ void vcc_cell_body(const VccArgs &a, const VBlock &vb
     const int tid = vb.tid;
     const int mx = a.m[0], my = a.m[1], mz = a.m[2];
     const long mxy = (long)mx * my, M = mxy * mz;
-    const int bx = vb.bid % a.nb[0], by = (vb.bid / a.nb[0]) % a.nb[1], bz = vb.bid / (a.nb[0] * a.nb[1]);
-    const int cx0 = bx * TX, cy0 = by * TY, cz0 = bz * TZ;
+    const int cx0 = vb.x * TX, cy0 = vb.y * TY, cz0 = vb.z * TZ;
     for (int i = tid; i < NB; i += NC) {
         const int lz = i / (BX * BY), r = i - lz * BX * BY, ly = r / BX, lx = r - ly * BX;
         const int gx = cx0 + lx, gy = cy0 + ly, gz = cz0 + lz;
