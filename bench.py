@@ -87,7 +87,7 @@ def alg_bytes(kernel, N, M):
 
 
 # source file of each timed kernel (the recorded ncu traffic is used only while it is unchanged)
-KSRC = {K_MATVEC: "gn_product_body.cuh", K_GRADLIN: "ngf_grad.cu", K_OBJ: "ngf_grad.cu", K_VCC: "vcc_body.cuh",
+KSRC = {K_MATVEC: "gn_product_body.cuh", K_GRADLIN: "ngf_gcol.cu", K_OBJ: "ngf_gcol.cu", K_VCC: "vcc_body.cuh",
         K_VCC_GN: "vcc_body.cuh", K_CURV: "nodes_body.cuh", K_FIN: "nodes_body.cuh", K_VEC: "pcg_body.cuh"}
 
 

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libngfreg.so")
-SOURCES = ["ngf_tile.cu", "ngf_matvec.cu", "gn_product.cu", "ngf_grad.cu", "reg_kernels.cu", "vcc.cu", "nodes.cu", "pcg.cu", "api.cu", "noalloc.cu", "gn_loop.cu", "pcg_batch.cu", "discrete.cu", "forstner.cu"]
+SOURCES = ["ngf_tile.cu", "ngf_matvec.cu", "gn_product.cu", "ngf_grad.cu", "ngf_gcol.cu", "reg_kernels.cu", "vcc.cu", "nodes.cu", "pcg.cu", "api.cu", "noalloc.cu", "gn_loop.cu", "pcg_batch.cu", "discrete.cu", "forstner.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -37,6 +37,7 @@ struct rg_ctx {
     TileGeom tg;
     BoxGeom bA, bB;
     int nA, nB, nR, nKb, nV;
+    int nD;                   // D partials written by the last objective / gradient pass (tiles or columns)
     long nA_cap, boxA_cap;      // NGF tile scratch sized for every supported tile height
     float *lin_dT, *lin_a, *lin_u;
     float *boxA, *boxB, *curv_w;
@@ -322,6 +323,7 @@ static void derive(rg_ctx *c) {
     c->bM.box = c->cg.box;
     tile_geom(&c->img, &c->grid, c->tg, 16);
     c->nA = c->tg.nb[0] * c->tg.nb[1] * c->tg.nb[2];
+    c->nD = c->nA;
     for (int a = 0; a < 3; ++a) {
         c->bA.m[a] = c->grid.m[a];
         c->bA.nb[a] = c->tg.nb[a];
@@ -474,6 +476,7 @@ extern "C" int rg_set_tile(rg_ctx *c, int32_t tile_y) {
     tile_geom(&c->img, &c->grid, c->tg, tile_y);
     c->tg.eta2 = eta2;
     c->nA = c->tg.nb[0] * c->tg.nb[1] * c->tg.nb[2];
+    c->nD = c->nA;
     for (int a = 0; a < 3; ++a) {
         c->bA.nb[a] = c->tg.nb[a];
         c->bA.C[a] = c->tg.C[a];
@@ -553,6 +556,40 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
         fill(a);
         a.R = a.T = nullptr;
         LAUNCH(pid, launch_gn_matvec(a, mode == MODE_DIAG, c->st));
+        return RG_OK;
+    }
+    c->nD = c->nA;
+    if (mode != MODE_MATVEC && mode != MODE_DIAG && !c->general_only && ngf_gcol_supported(c->cg)) {
+        // objective, gradient and linearisation: the column-marching pass
+        auto gfill = [&](auto &g) {
+            g.g = c->cg;
+            for (int i = 0; i < 3; ++i) {
+                g.invh[i] = c->tg.invh[i];
+                g.invh_rel[i] = c->tg.invh_rel[i];
+            }
+            g.eta2 = c->tg.eta2;
+            g.u = field;
+            g.st_dT = c->lin_dT;
+            g.st_a = c->lin_a;
+            g.boxes = c->boxA;
+            g.dpart = c->dpart;
+            g.skip = c->skip;
+        };
+        if (c->dtype == RG_F32) {
+            GcolArgs<float> g;
+            gfill(g);
+            g.R = (const float *)c->R;
+            g.T = (const float *)c->T;
+            LAUNCH(pid, launch_ngf_gcol(mode, g, c->st));
+        } else {
+            GcolArgs<__half> g;
+            gfill(g);
+            g.R = (const __half *)c->R;
+            g.T = (const __half *)c->T;
+            LAUNCH(pid, launch_ngf_gcol(mode, g, c->st));
+        }
+        c->bcur = &c->bM;
+        c->nD = c->cg.nb[0] * c->cg.nb[1];
         return RG_OK;
     }
     // objective, gradient and linearisation: the persistent pass where the tile shape allows
@@ -650,7 +687,7 @@ static int run_kp(rg_ctx *c, const float *u, const float *v, double scale, float
 static int run_terms(rg_ctx *c, double *terms, bool useD, bool useR, bool useV, bool useK, bool latch = true) {
     TermsArgs t;
     t.dpart = useD ? c->dpart : nullptr;
-    t.nd = c->nA;
+    t.nd = c->nD;
     t.dscale = c->hbar;
     t.rpart = useR ? c->rpart : nullptr;
     t.nr = c->nR;

@@ -26,6 +26,26 @@ cudaError_t launch_gn_matvec(const TileArgs<float> &a, bool diag, cudaStream_t s
 bool gn_product_supported(const ColGeom &g);
 cudaError_t launch_gn_product(const ColArgs &a, bool diag, cudaStream_t st);
 
+// Column-marching objective / gradient / linearisation pass (ngf_gcol.cu):
+// MODE_OBJ, MODE_GRAD, MODE_GRADLIN (MODE_LIN as GRADLIN); node boxes in the
+// GN product's column layout, one D partial per column.
+template <typename TImg>
+struct GcolArgs {
+    ColGeom g;
+    float invh[3];          // float(1 / h), the FP32 cell decision
+    float invh_rel[3];      // 1 - h float(1 / h)
+    float eta2;
+    const TImg *R, *T;
+    const float *u;
+    float *st_dT, *st_a;    // stored linearisation (GRADLIN)
+    float *boxes;           // per-column node boxes [column][3][m3][C1 + 1][C0 + 1]
+    double *dpart;          // per-column partial sums of 1 - r^2
+    const int *skip = nullptr;
+};
+bool ngf_gcol_supported(const ColGeom &g);
+cudaError_t launch_ngf_gcol(int mode, const GcolArgs<float> &a, cudaStream_t st);
+cudaError_t launch_ngf_gcol(int mode, const GcolArgs<__half> &a, cudaStream_t st);
+
 // Volume change control, Eqs. (7)-(9): per grid cell the 64 bounds d_abc.
 struct VccArgs {
     int m[3];
