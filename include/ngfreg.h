@@ -310,9 +310,14 @@ int rg_sync(rg_ctx *ctx);
  * kernels issue no TMA copy, so each of their bounded waits on a TMA barrier
  * runs out (the results are garbage and RG_ETIMEOUT is latched; no copy is
  * ever in flight).  RG_HOOK_POLL_LIMIT (value > 0): polls of a TMA barrier
- * before such a wait gives up (default 2^20). */
+ * before such a wait gives up (default 2^20).  RG_HOOK_PASS (value 0, 1, 2):
+ * the objective / gradient / linearisation pass chosen by the volume's size
+ * (0, the default: the column-marching pass when it has at least one column
+ * of 60 x 16 voxels per SM), always the column-marching pass where it applies
+ * (1), or always the tile pass (2); the results agree within rounding. */
 #define RG_HOOK_NO_TMA 1
 #define RG_HOOK_POLL_LIMIT 2
+#define RG_HOOK_PASS 3
 int rg_debug_hook(rg_ctx *ctx, int32_t what, int32_t value);
 
 /* Latched error text of the last failing call on this context. */

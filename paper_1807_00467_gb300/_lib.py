@@ -17,7 +17,7 @@ RG_NOALLOC_MAX_CTAS = 65536
 RG_CURV, RG_VCC, RG_KP = 1, 2, 4
 RG_PCG_MAX = 63
 RG_F32, RG_F16 = 0, 1
-RG_HOOK_NO_TMA, RG_HOOK_POLL_LIMIT = 1, 2
+RG_HOOK_NO_TMA, RG_HOOK_POLL_LIMIT, RG_HOOK_PASS = 1, 2, 3
 RG_SCHED_PERSISTENT, RG_SCHED_HOOK_BARRIER = 8, 16
 RG_REPORT_COLS = 11     # {it, J, g.p, t, J new, evaluations, pcg steps, status, min d, max d, in bounds}
 

@@ -204,7 +204,7 @@ class Context:
         return _check(_lib.load().rg_sync(self._ctx), self._ctx, "rg_sync")
 
     def debug_hook(self, what, value):
-        """Test hooks of include/ngfreg.h (RG_HOOK_NO_TMA, RG_HOOK_POLL_LIMIT)."""
+        """Test hooks of include/ngfreg.h (RG_HOOK_NO_TMA, RG_HOOK_POLL_LIMIT, RG_HOOK_PASS)."""
         _check(_lib.load().rg_debug_hook(self._ctx, int(what), int(value)), self._ctx, "rg_debug_hook")
 
     def profile(self, enable=True):

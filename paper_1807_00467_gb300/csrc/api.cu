@@ -55,6 +55,7 @@ struct rg_ctx {
     BoxGeom bM;
     const BoxGeom *bcur;      // node-box geometry of the last NGF tile launch (read by the node pass)
     int hook_no_tma, hook_poll;   // test hooks (rg_debug_hook)
+    int hook_pass;                // objective / gradient pass: 0 by size, 1 column-marching, 2 tile (test hook)
     double *rzh, *pcgpart, *rzpart, *apart;   // PCG: r_j.z_j, coefficient / r.z / d.q partials
     PcgScalars *sc;
     bool has_lin, minv_valid;
@@ -559,7 +560,13 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
         return RG_OK;
     }
     c->nD = c->nA;
-    if (mode != MODE_MATVEC && mode != MODE_DIAG && !c->general_only && ngf_gcol_supported(c->cg)) {
+    // the column-marching pass where it covers the volume with at least one
+    // column per SM (narrower volumes keep the z-chunked tile pass, whose
+    // tiles fill the GPU)
+    const bool gcol = mode != MODE_MATVEC && mode != MODE_DIAG && !c->general_only && c->hook_pass != 2 &&
+                      ngf_gcol_supported(c->cg) &&
+                      (c->hook_pass == 1 || c->cg.nb[0] * c->cg.nb[1] >= device_sm_count());
+    if (gcol) {
         // objective, gradient and linearisation: the column-marching pass
         auto gfill = [&](auto &g) {
             g.g = c->cg;
@@ -1738,6 +1745,7 @@ extern "C" int rg_debug_hook(rg_ctx *c, int32_t what, int32_t value) {
     if (!c) return RG_EINVAL;
     if (what == RG_HOOK_NO_TMA) c->hook_no_tma = value != 0;
     else if (what == RG_HOOK_POLL_LIMIT && value > 0) c->hook_poll = value;
+    else if (what == RG_HOOK_PASS && value >= 0 && value <= 2) c->hook_pass = value;
     else return set_err(c, RG_EINVAL, "rg_debug_hook: unknown hook %d or bad value %d", what, value);
     return RG_OK;
 }

@@ -25,8 +25,9 @@
 // Waits: thread 0 polls the counter with a growing pause, for a bounded
 // number of polls and at most two seconds; a CTA whose wait runs out raises
 // the launch's abort flag and every volume's error flag (the caller reports
-// RG_ETIMEOUT), and the other CTAs leave at their next wait.  The launch is cooperative, so all CTAs are resident and a
-// wait only runs out when a test hook withholds a completion.
+// RG_ETIMEOUT), and the other CTAs leave at their next wait.  The launch is
+// cooperative, so all CTAs are resident and a wait only runs out when a test
+// hook withholds a completion.
 #include "gn_product_body.cuh"
 #include "nodes_body.cuh"
 #include "pcg_body.cuh"

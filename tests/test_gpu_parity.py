@@ -51,11 +51,15 @@ def test_objective_and_gradient_tiny(tiny, gamma):
     assert err <= TOL_GRAD
 
 
-def test_identical_images_give_zero_distance(tiny):
+@pytest.mark.parametrize("pass_", [0, 1, 2])
+def test_identical_images_give_zero_distance(tiny, pass_):
+    """Exactly zero in either objective/gradient pass (0: chosen by size, 1:
+    column-marching, 2: tile)."""
     import torch
-    from paper_1807_00467_gb300 import api
+    from paper_1807_00467_gb300 import _lib, api
     R = torch.from_numpy(tiny.R).cuda()
     ctx = api.Context(R, R.clone(), tiny.h, TINY_M, api.make_params(eta=10.0, alpha=1.0, gamma=0.001))
+    ctx.debug_hook(_lib.RG_HOOK_PASS, pass_)
     terms, grad = ctx.ngf_gradient(torch.zeros(ctx.grid_shape, device="cuda"))
     t = terms.cpu().numpy()
     assert t[0] == 0.0 and t[1] == 0.0 and t[2] == 0.0 and t[4] == 0.0
@@ -118,6 +122,36 @@ def test_gradient_pass_matches_general_kernel(n, h, m, half):
     assert rel_l2(out[16][2], out[8][2]) <= 1e-6
     assert rel_l2(out[16][3], out[16][2]) <= 1e-9
     assert rel_l2(out[16][4], out[8][4]) <= 1e-6
+
+
+@pytest.mark.parametrize("n,h,m,half", [((64, 64, 48), (1.0, 1.0, 2.5), (17, 17, 13), False),
+                                        ((96, 48, 36), (0.8, 0.8, 2.5), (25, 13, 19), True),
+                                        ((132, 40, 20), (1.0, 1.1, 2.0), (34, 11, 11), False),   # 3 columns, ragged
+                                        ((64, 48, 64), (1.0, 1.0, 1.5), (9, 7, 9), False)])      # rho 8
+def test_column_pass_matches_tile_pass(n, h, m, half):
+    """The column-marching objective / gradient / linearisation pass (forced by
+    the test hook at these sizes, where the size rule picks the tile pass)
+    against the tile pass: terms, gradient, and the GN product of the stored
+    linearisation."""
+    from paper_1807_00467_gb300 import _lib
+    ph = small_phantom(n, h, seed=8)
+    ctx = gpu_context(ph, m, gamma=0.001, half=half)
+    u = to_dev(_u0(ph, m, 0.6))
+    v = to_dev(phantom.random_grid_field(m, 23))
+    out = {}
+    for p in (1, 2):
+        ctx.debug_hook(_lib.RG_HOOK_PASS, p)
+        to = ctx.ngf_objective(u).cpu().numpy()
+        tg, g = ctx.ngf_gradient(u)
+        tl, gl = ctx.gn_linearize(u)
+        out[p] = (to, tg.cpu().numpy(), g.cpu().numpy(), gl.cpu().numpy(), ctx.gn_matvec(v).cpu().numpy())
+    ctx.debug_hook(_lib.RG_HOOK_PASS, 0)
+    for k in range(5):
+        if out[2][1][k] != 0.0:
+            assert rel(out[1][0][k], out[2][1][k]) <= 1e-6 and rel(out[1][1][k], out[2][1][k]) <= 1e-6, k
+    assert rel_l2(out[1][2], out[2][2]) <= 1e-6
+    assert np.array_equal(out[1][3], out[1][2])     # the linearising pass gives the plain gradient's bits
+    assert rel_l2(out[1][4], out[2][4]) <= 1e-6
 
 
 def test_linearize_gradient_matches_plain_gradient(tiny):
