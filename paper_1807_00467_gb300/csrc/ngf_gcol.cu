@@ -19,8 +19,11 @@
 //                 onto the column's two z-node planes in registers
 // x neighbours by one shuffle per direction (the pair's other column is
 // local), y neighbours through double-buffered exchange rows, z neighbours in
-// registers; one barrier per plane.  The stored linearisation is written once
-// per voxel with 8-byte stores.  P^T: completed node planes are parked per
+// registers; one barrier per plane.  Each thread keeps the dT/dy of its last
+// two planes (read back by stage A) and P u at the two node planes of the
+// current cell in shared-memory slots of its own rather than in registers
+// (no register spills).  The stored linearisation is
+// written once per voxel with 8-byte stores.  P^T: completed node planes are parked per
 // lane (hat-weighted lower and upper parts), reduced along x by all threads
 // in the next plane and along y in the plane after, into the column's node
 // box [3][m3][C1 + 1][C0 + 1] (the GN product's boxes; the node pass sums
@@ -37,7 +40,7 @@ constexpr int kEx = kNW * 64;   // floats per exchange buffer (a float2 per lane
 constexpr unsigned FULL = 0xffffffffu;
 
 struct GcSmem {
-    int ext, exr, exc, nodes, park, xr, total;
+    int ext, exr, exc, nodes, park, xr, dts, us, total;
 };
 
 __host__ __device__ inline GcSmem gc_smem(const ColGeom &g, bool adj) {
@@ -49,6 +52,8 @@ __host__ __device__ inline GcSmem gc_smem(const ColGeom &g, bool adj) {
     s.nodes = off; off += 4 * ((g.nyt * g.nxt + 31) & ~31) * 4;    // node planes of u, [slot][y][x][xyz_]
     s.park = off; off += adj ? 2 * kTY * 32 * 6 : 0;               // parked lane parts of 2 node planes
     s.xr = off; off += adj ? 2 * kTY * (g.C0 + 1) * 3 : 0;         // x-reduced rows of 2 node planes
+    s.dts = off; off += adj ? 2 * 3 * kNT * 2 : 0;                 // per thread: dT/dy of 2 planes
+    s.us = off; off += 2 * 3 * kNT * 2;                             // per thread: P u at 2 node planes
     s.total = off;
     return s;
 }
@@ -285,11 +290,20 @@ __global__ void __launch_bounds__(kNT, 1) ngf_gcol_kernel(const __grid_constant_
         __syncthreads();   // node ring filled, exchange rows cleared; the previous column's passes are done
 
         const float2 z2 = make_float2(0.f, 0.f);
-        float2 U0[3], U1[3];
-        bilinear(cz0, U0);
-        bilinear(cz0 + 1, U1);
+        float2 *usm = reinterpret_cast<float2 *>(smem + S.us) + tid;   // [slot][k], stride kNT
+        int u0s = 0;   // slot of the lower node plane
+        {
+            float2 Ut[3];
+            bilinear(cz0, Ut);
+            for (int k = 0; k < 3; ++k) usm[k * kNT] = Ut[k];
+            bilinear(cz0 + 1, Ut);
+            for (int k = 0; k < 3; ++k) usm[(3 + k) * kNT] = Ut[k];
+        }
         float2 tm = z2, t0 = z2, rm = z2, r0 = z2;        // T(y) and R at planes pC - 1, pC
-        float2 d1[3] = {z2, z2, z2}, d2[3] = {z2, z2, z2};  // dT/dy at planes pW - 1, pW - 2
+        // this thread's dT/dy of planes pW - 2 and pW - 1: [slot = plane parity][component], stride kNT
+        float2 *dts = reinterpret_cast<float2 *>(smem + S.dts) + tid;
+        if (ADJ)
+            for (int i = 0; i < 6; ++i) dts[i * kNT] = z2;
         float2 cxp = z2, czm2 = z2, czm1 = z2;             // c of the adjoint at planes pA, pA - 1
         float2 acc0[3] = {z2, z2, z2}, acc1[3] = {z2, z2, z2};
         float ds_e = 0.f, dc_e = 0.f, ds_o = 0.f, dc_o = 0.f;   // Kahan sums of 1 - r^2
@@ -314,8 +328,10 @@ __global__ void __launch_bounds__(kNT, 1) ngf_gcol_kernel(const __grid_constant_
                 }
                 if (cell_start) {
                     const int kz = pW >> lrz;
-                    U0[0] = U1[0]; U0[1] = U1[1]; U0[2] = U1[2];
-                    bilinear(kz + 1, U1);
+                    float2 Ut[3];
+                    bilinear(kz + 1, Ut);
+                    for (int k = 0; k < 3; ++k) usm[(u0s * 3 + k) * kNT] = Ut[k];   // over the old lower plane
+                    u0s ^= 1;
                     if (node_warp) node_copy(kz + 3);
                 }
 
@@ -323,8 +339,9 @@ __global__ void __launch_bounds__(kNT, 1) ngf_gcol_kernel(const __grid_constant_
                 float2 val, dw[3];
                 {
                     const float2 fz2 = bc2(fz), wz2 = bc2(1.f - fz);
-                    const float2 pu0 = lerp2(U0[0], U1[0], wz2, fz2), pu1 = lerp2(U0[1], U1[1], wz2, fz2);
-                    const float2 pu2 = lerp2(U0[2], U1[2], wz2, fz2);
+                    const float2 *ul = usm + u0s * 3 * kNT, *uh = usm + (u0s ^ 1) * 3 * kNT;
+                    const float2 pu0 = lerp2(ul[0], uh[0], wz2, fz2), pu1 = lerp2(ul[kNT], uh[kNT], wz2, fz2);
+                    const float2 pu2 = lerp2(ul[2 * kNT], uh[2 * kNT], wz2, fz2);
                     const Place xe = place(pu0.x, ih0, a.invh_rel[0], gx, nx), xo = place(pu0.y, ih0, a.invh_rel[0], gx + 1, nx);
                     const Place ye = place(pu1.x, ih1, a.invh_rel[1], gy, ny), yo = place(pu1.y, ih1, a.invh_rel[1], gy, ny);
                     const Place ze = place(pu2.x, ih2, a.invh_rel[2], pW, nz), zo = place(pu2.y, ih2, a.invh_rel[2], pW, nz);
@@ -429,8 +446,9 @@ __global__ void __launch_bounds__(kNT, 1) ngf_gcol_kernel(const __grid_constant_
                     const float2 bsum = add2(add2(bx, sub2(ex_c[bo + up], ex_c[bo + dn])), sub2(czm2, c2));
                     const float2 b1 = mul2(bc2(wz1), bsum), b0 = sub2(bsum, b1);
                     for (int k = 0; k < 3; ++k) {
-                        acc0[k] = fma2(b0, d2[k], acc0[k]);
-                        acc1[k] = fma2(b1, d2[k], acc1[k]);
+                        const float2 d2k = dts[((j & 1) * 3 + k) * kNT];   // dT/dy of plane pA (this slot)
+                        acc0[k] = fma2(b0, d2k, acc0[k]);
+                        acc1[k] = fma2(b1, d2k, acc1[k]);
                     }
                     if (phA == (RZ ? RZ - 1 : rzm) && s >= 4) {
                         const int kz = (s - 4) >> lrz;   // node plane (pA >> lrz) is complete
@@ -444,8 +462,7 @@ __global__ void __launch_bounds__(kNT, 1) ngf_gcol_kernel(const __grid_constant_
                     ex_c[exh - bo] = c1;
                     czm2 = czm1; czm1 = c2;
                     cxp = c0;
-                    for (int k = 0; k < 3; ++k) d2[k] = d1[k];
-                    d1[0] = dw[0]; d1[1] = dw[1]; d1[2] = dw[2];
+                    for (int k = 0; k < 3; ++k) dts[((j & 1) * 3 + k) * kNT] = dw[k];
                 }
                 // ------------------------------------------------ hand over to the next plane
                 ex_t[exh - bo] = val;
