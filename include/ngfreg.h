@@ -157,17 +157,21 @@ int rg_set_stream(rg_ctx *ctx, void *cuda_stream);
 int rg_set_tile(rg_ctx *ctx, int32_t tile_y);
 
 /* Tile autotuner (the paper has no counterpart: it picks launch shapes).
- * Candidates: 16-row tiles on the persistent objective/gradient and GN-product
- * kernels (the default), 16-row tiles on the general column kernel, 8-row
- * tiles on the general column kernel.  Each is timed with CUDA events on the
- * context's stream at u_dev (one linearisation pass and three GN products,
- * after one untimed round; the stream is synchronised) and scored as one
- * Gauss-Newton iteration, gradient pass + 30 products; the fastest is kept in
- * the context (tile_y / general, either may be NULL, report it) and cached
- * per process by image and grid shape, image type and active terms, so later
- * contexts of the same problem skip the timing.  Results of the candidates
- * agree within the stated tolerances, not bit for bit.  The linearisation is
- * discarded: call gn_linearize again before gn_matvec / gn_pcg_solve. */
+ * Candidates (tile_y, general): (16, 2) the specialised kernels with the
+ * column-marching objective/gradient pass (where the volume allows it),
+ * (16, 3) the specialised kernels with the z-chunked tile pass, (16, 1) and
+ * (8, 1) the general column kernel with 16- and 8-row tiles; untuned contexts
+ * use (16, 0), the specialised kernels with the pass chosen by size (the
+ * column pass with at least one 60 x 16 voxel column per SM).  Each is timed
+ * with CUDA events on the context's stream at u_dev (one linearisation pass
+ * and three GN products, after one untimed round; the stream is synchronised)
+ * and scored as one Gauss-Newton iteration, gradient pass + 30 products; the
+ * fastest is kept in the context (tile_y / general, either may be NULL,
+ * report it) and cached per process by image and grid shape, image type and
+ * active terms, so later contexts of the same problem skip the timing.
+ * Results of the candidates agree within the stated tolerances, not bit for
+ * bit. The linearisation is discarded: call gn_linearize again before
+ * gn_matvec / gn_pcg_solve. */
 int rg_autotune(rg_ctx *ctx, const float *u_dev, int32_t *tile_y, int32_t *general);
 
 /* Borrow the reference R (fixed image F) and template T (moving image M),

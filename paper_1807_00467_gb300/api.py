@@ -145,12 +145,14 @@ class Context:
         _check(_lib.load().rg_set_tile(self._ctx, int(tile_y)), self._ctx, "rg_set_tile")
 
     def autotune(self, u):
-        """Times the tile candidates at u and keeps the fastest; returns
-        (tile_y, general_kernel).  Discards the linearisation."""
+        """Times the kernel candidates at u and keeps the fastest; returns
+        (tile_y, general): general 1 for the general kernels, 2 / 3 for the
+        specialised kernels with the column / tile objective-gradient pass
+        (include/ngfreg.h, rg_autotune).  Discards the linearisation."""
         ty, gen = C.c_int32(), C.c_int32()
         _check(_lib.load().rg_autotune(self._ctx, _ptr(self._field(u)), C.byref(ty), C.byref(gen)), self._ctx,
                "rg_autotune")
-        return ty.value, bool(gen.value)
+        return ty.value, gen.value
 
     def set_keypoints(self, kx, ky):
         kx = kx.contiguous().float()

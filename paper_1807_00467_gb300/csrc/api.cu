@@ -55,7 +55,8 @@ struct rg_ctx {
     BoxGeom bM;
     const BoxGeom *bcur;      // node-box geometry of the last NGF tile launch (read by the node pass)
     int hook_no_tma, hook_poll;   // test hooks (rg_debug_hook)
-    int hook_pass;                // objective / gradient pass: 0 by size, 1 column-marching, 2 tile (test hook)
+    int pass_sel;                 // objective / gradient pass: 0 by size, 1 column-marching, 2 tile
+                                  // (autotuner choice, or the RG_HOOK_PASS test hook)
     double *rzh, *pcgpart, *rzpart, *apart;   // PCG: r_j.z_j, coefficient / r.z / d.q partials
     PcgScalars *sc;
     bool has_lin, minv_valid;
@@ -563,9 +564,9 @@ static int run_tile(rg_ctx *c, int mode, const float *field) {
     // the column-marching pass where it covers the volume with at least one
     // column per SM (narrower volumes keep the z-chunked tile pass, whose
     // tiles fill the GPU)
-    const bool gcol = mode != MODE_MATVEC && mode != MODE_DIAG && !c->general_only && c->hook_pass != 2 &&
+    const bool gcol = mode != MODE_MATVEC && mode != MODE_DIAG && !c->general_only && c->pass_sel != 2 &&
                       ngf_gcol_supported(c->cg) &&
-                      (c->hook_pass == 1 || c->cg.nb[0] * c->cg.nb[1] >= device_sm_count());
+                      (c->pass_sel == 1 || c->cg.nb[0] * c->cg.nb[1] >= device_sm_count());
     if (gcol) {
         // objective, gradient and linearisation: the column-marching pass
         auto gfill = [&](auto &g) {
@@ -1251,10 +1252,14 @@ static TuneKey tune_key(const rg_ctx *c) {
                    c->P.gamma != 0.0, c->nk > 0};
 }
 
+// general: 0 the specialised kernels with the objective / gradient pass by
+// size, 1 the general tile kernels, 2 / 3 the specialised kernels with the
+// column-marching / tile pass
 static int apply_tile(rg_ctx *c, int ty, int general) {
     const int st = rg_set_tile(c, ty);
     if (st != RG_OK) return st;
-    c->general_only = general != 0;
+    c->general_only = general == 1;
+    c->pass_sel = general == 2 ? 1 : (general == 3 ? 2 : 0);
     c->has_lin = false;
     c->minv_valid = false;
     return RG_OK;
@@ -1275,7 +1280,12 @@ extern "C" int rg_autotune(rg_ctx *c, const float *u, int32_t *tile_y, int32_t *
         }
     }
     if (!cached) {
-        const std::pair<int, int> cand[3] = {{16, 0}, {16, 1}, {8, 1}};
+        // the column-marching pass where it applies, the tile pass, the general kernels
+        std::vector<std::pair<int, int>> cand;
+        if (ngf_gcol_supported(c->cg)) cand.push_back({16, 2});
+        cand.push_back({16, 3});
+        cand.push_back({16, 1});
+        cand.push_back({8, 1});
         cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
         for (auto &x : e)
             if (cudaEventCreate(&x) != cudaSuccess) {
@@ -1745,7 +1755,7 @@ extern "C" int rg_debug_hook(rg_ctx *c, int32_t what, int32_t value) {
     if (!c) return RG_EINVAL;
     if (what == RG_HOOK_NO_TMA) c->hook_no_tma = value != 0;
     else if (what == RG_HOOK_POLL_LIMIT && value > 0) c->hook_poll = value;
-    else if (what == RG_HOOK_PASS && value >= 0 && value <= 2) c->hook_pass = value;
+    else if (what == RG_HOOK_PASS && value >= 0 && value <= 2) c->pass_sel = value;
     else return set_err(c, RG_EINVAL, "rg_debug_hook: unknown hook %d or bad value %d", what, value);
     return RG_OK;
 }

@@ -11,7 +11,7 @@ from paper_1807_00467_gb300 import phantom
 pytestmark = pytest.mark.gpu
 
 TOL_OBJ, TOL_GRAD, TOL_MV, TOL_U = 1e-6, 1e-5, 1e-5, 0.01
-CANDIDATES = {(16, False), (16, True), (8, True)}
+CANDIDATES = {(16, 2), (16, 3), (16, 1), (8, 1)}   # column pass, tile pass, general kernels
 
 
 @pytest.mark.parametrize("shape,h,m", [((64, 64, 48), (1.0, 1.0, 2.5), (17, 17, 13)),
