@@ -1419,7 +1419,7 @@ extern "C" int register_pyramid(const rg_image_geom *img, const void *R, const v
     int status = RG_OK;
     for (int l = Lc; l >= 0; --l) {
         size_t w;
-        rg_workspace_size(&il[l], &gl[l], dtype, nk, s->pcg_iters, &w);
+        if (rg_workspace_size(&il[l], &gl[l], dtype, nk, s->pcg_iters, &w) != RG_OK) return RG_EINVAL;
         void *wl = take(w);
         rg_ctx *cl = nullptr;
         int e = rg_ctx_create(&cl, &il[l], &gl[l], dtype, &P, nk, s->pcg_iters, wl, w, stream);

@@ -64,7 +64,7 @@ struct VccArgs {
 };
 constexpr int kVccTile[3] = {8, 4, 4};
 cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st);
-cudaError_t launch_vcc_cells(const VccArgs &a, cudaStream_t st);   // gradient / GN product (a.diag == 0)
+cudaError_t launch_vcc_cells(const VccArgs &a, cudaStream_t st);   // gradient / GN product / diagonal
 
 // Node passes: w = L v with the curvature operator L of Eq. (5) and
 // per-block partials of |L v|^2 (launch_curv); out = sA (NGF boxes) +

@@ -35,265 +35,8 @@ struct Kahan {
 };
 
 // ------------------------------------------------------------------ VCC
-// Edge e of the axis-a edges joins corner offsets o0 -> o1; the two other
-// axes carry (e & 1, e >> 1) in increasing axis order.
-__device__ __forceinline__ int edge_corner(int a, int e, int hi) {
-    int o[3];
-    const int p = e & 1, q = e >> 1;
-    if (a == 0) { o[0] = hi; o[1] = p; o[2] = q; }
-    else if (a == 1) { o[0] = p; o[1] = hi; o[2] = q; }
-    else { o[0] = p; o[1] = q; o[2] = hi; }
-    return o[0] + 2 * o[1] + 4 * o[2];
-}
-
-__device__ __forceinline__ void cross3(const float *a, const float *b, float *c) {
-    c[0] = a[1] * b[2] - a[2] * b[1];
-    c[1] = a[2] * b[0] - a[0] * b[2];
-    c[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-// VM = 0: gradient of sum psi(d) (+ energy, folds, min/max d); VM = 1: GN
-// product sum psi''(d) (grad d . v) grad d; VM = 2: diagonal of the GN matrix
-// sum psi''(d) (d d / d u_{k,c})^2.
-//
-// Four threads per grid cell, one per z-edge c of the cell: each evaluates the
-// 16 bounds d_abc of its c (a, b over the x- and y-edges).  Gradients with
-// respect to the x- and y-edges are summed over the four threads with warp
-// shuffles; the first thread of the cell scatters the cell's contributions to
-// its 8 corners in shared memory, and nodes gather them per CTA box.
-template <int VM>
-__global__ void __launch_bounds__(4 * kVccTile[0] * kVccTile[1] * kVccTile[2], 1) vcc_kernel(const VccArgs a) {
-    constexpr bool GN = VM == 1, DG = VM == 2;
-    constexpr int TX = kVccTile[0], TY = kVccTile[1], TZ = kVccTile[2], NC = TX * TY * TZ, NT = 4 * NC;
-    constexpr int BX = TX + 1, BY = TY + 1, BZ = TZ + 1, NB = BX * BY * BZ;
-    constexpr unsigned FULL = 0xffffffffu;
-    __shared__ float su[3][NB];
-    __shared__ float sv[GN ? 3 : 1][GN ? NB : 1];
-    __shared__ float scell[NC][8][3];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int mx = a.m[0], my = a.m[1], mz = a.m[2];
-    const long mxy = (long)mx * my, M = mxy * mz;
-    const int cx0 = blockIdx.x * TX, cy0 = blockIdx.y * TY, cz0 = blockIdx.z * TZ;
-    for (int i = tid; i < NB; i += NT) {
-        const int lz = i / (BX * BY), r = i - lz * BX * BY, ly = r / BX, lx = r - ly * BX;
-        const int gx = cx0 + lx, gy = cy0 + ly, gz = cz0 + lz;
-        const bool ok = gx < mx && gy < my && gz < mz;
-        const long k = (long)gz * mxy + (long)gy * mx + gx;
-        for (int c = 0; c < 3; ++c) {
-            su[c][i] = ok ? a.u[c * M + k] : 0.f;
-            if (GN) sv[c][i] = ok ? a.v[c * M + k] : 0.f;
-        }
-    }
-    __syncthreads();
-    const int cell = tid >> 2, cz_e = tid & 3;   // z-edge index of this thread
-    const int lx = cell % TX, ly = (cell / TX) % TY, lz = cell / (TX * TY);
-    const bool valid = cx0 + lx < mx - 1 && cy0 + ly < my - 1 && cz0 + lz < mz - 1;
-    const int base = (lz * BY + ly) * BX + lx;
-    auto corner = [&](int o) { return base + (o & 1) + ((o >> 1) & 1) * BX + (o >> 2) * BX * BY; };
-    // edge vectors: x-edges (4), y-edges (4), this thread's z-edge
-    float E1[4][3], E2[4][3], E3[3], D1[GN ? 4 : 1][3], D2[GN ? 4 : 1][3], D3[3];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int x0c = corner(edge_corner(0, e, 0)), x1c = corner(edge_corner(0, e, 1));
-        const int y0c = corner(edge_corner(1, e, 0)), y1c = corner(edge_corner(1, e, 1));
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            E1[e][k] = (k == 0 ? 1.f : 0.f) + (su[k][x1c] - su[k][x0c]) * a.ig[0];
-            E2[e][k] = (k == 1 ? 1.f : 0.f) + (su[k][y1c] - su[k][y0c]) * a.ig[1];
-            if (GN) {
-                D1[e][k] = (sv[k][x1c] - sv[k][x0c]) * a.ig[0];
-                D2[e][k] = (sv[k][y1c] - sv[k][y0c]) * a.ig[1];
-            }
-        }
-    }
-    {
-        const int z0c = corner(edge_corner(2, cz_e, 0)), z1c = corner(edge_corner(2, cz_e, 1));
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            E3[k] = (k == 2 ? 1.f : 0.f) + (su[k][z1c] - su[k][z0c]) * a.ig[2];
-            D3[k] = GN ? (sv[k][z1c] - sv[k][z0c]) * a.ig[2] : 0.f;
-        }
-    }
-    float G1[4][3] = {}, G2[4][3] = {}, G3[3] = {0.f, 0.f, 0.f};
-    float acc[DG ? 8 : 1][3] = {};
-    int fold = 0;
-    float dmn = 3.4e38f, dmx = -3.4e38f;
-    Kahan en;
-    if (valid) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            float x23[3], y23[3], W1[3] = {0.f, 0.f, 0.f};
-            cross3(E2[b], E3, x23);
-            if (GN) {
-                float p[3], q[3];
-                cross3(D2[b], E3, p);
-                cross3(E2[b], D3, q);
-                y23[0] = p[0] + q[0]; y23[1] = p[1] + q[1]; y23[2] = p[2] + q[2];
-            }
-#pragma unroll
-            for (int aa = 0; aa < 4; ++aa) {
-                const float *e1 = E1[aa];
-                const float d = e1[0] * x23[0] + e1[1] * x23[1] + e1[2] * x23[2];
-                if (VM == 0) {
-                    dmn = fminf(dmn, d);
-                    dmx = fmaxf(dmx, d);
-                }
-                if (!(d > 0.f)) {
-                    ++fold;
-                    continue;
-                }
-                if (DG) {
-                    const float rd = __fdividef(1.f, d);
-                    const float w = 2.f * rd * rd * rd;     // psi''(d)
-                    float x31[3], x12[3];
-                    cross3(E3, e1, x31);
-                    cross3(e1, E2[b], x12);
-                    const int xo0 = edge_corner(0, aa, 0), xo1 = edge_corner(0, aa, 1);
-                    const int yo0 = edge_corner(1, b, 0), yo1 = edge_corner(1, b, 1);
-                    const int zo0 = edge_corner(2, cz_e, 0), zo1 = edge_corner(2, cz_e, 1);
-#pragma unroll
-                    for (int o = 0; o < 8; ++o) {
-                        const float sx = (o == xo1 ? 1.f : 0.f) - (o == xo0 ? 1.f : 0.f);
-                        const float sy = (o == yo1 ? 1.f : 0.f) - (o == yo0 ? 1.f : 0.f);
-                        const float sz = (o == zo1 ? 1.f : 0.f) - (o == zo0 ? 1.f : 0.f);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float gd = sx * a.ig[0] * x23[k] + sy * a.ig[1] * x31[k] + sz * a.ig[2] * x12[k];
-                            acc[o][k] = fmaf(w * gd, gd, acc[o][k]);
-                        }
-                    }
-                    continue;
-                }
-                float w;
-                if (GN) {
-                    const float rd = __fdividef(1.f, d);
-                    const float *de1 = D1[aa];
-                    const float dd = de1[0] * x23[0] + de1[1] * x23[1] + de1[2] * x23[2] + e1[0] * y23[0] +
-                                     e1[1] * y23[1] + e1[2] * y23[2];
-                    w = 2.f * rd * rd * rd * dd;            // psi''(d) (grad d . v)
-                } else {
-                    const float rd = __frcp_rn(d);
-                    const float dm = d - 1.f;
-                    en.add(dm * dm * rd);                   // psi(d) = (d - 1)^2 / d
-                    w = dm * (d + 1.f) * rd * rd;           // psi'(d) = 1 - 1/d^2
-                }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    G1[aa][k] = fmaf(w, x23[k], G1[aa][k]);
-                    W1[k] = fmaf(w, e1[k], W1[k]);
-                }
-            }
-            if (!DG) {
-                float t2[3], t3[3];
-                cross3(E3, W1, t2);       // sum_a w (e3_c x e1_a)
-                cross3(W1, E2[b], t3);    // sum_a w (e1_a x e2_b)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    G2[b][k] += t2[k];
-                    G3[k] += t3[k];
-                }
-            }
-        }
-    }
-    // sum over the four z-edge threads of the cell (aligned lane groups of 4)
-    float out[8][3];
-    if (DG) {
-#pragma unroll
-        for (int o = 0; o < 8; ++o)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float v = acc[o][k];
-                v += __shfl_xor_sync(FULL, v, 1);
-                v += __shfl_xor_sync(FULL, v, 2);
-                out[o][k] = v;
-            }
-    } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                G1[e][k] += __shfl_xor_sync(FULL, G1[e][k], 1);
-                G1[e][k] += __shfl_xor_sync(FULL, G1[e][k], 2);
-                G2[e][k] += __shfl_xor_sync(FULL, G2[e][k], 1);
-                G2[e][k] += __shfl_xor_sync(FULL, G2[e][k], 2);
-            }
-        float G3a[4][3];
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) G3a[e][k] = __shfl_sync(FULL, G3[k], (lane & ~3) | e);
-#pragma unroll
-        for (int o = 0; o < 8; ++o) out[o][0] = out[o][1] = out[o][2] = 0.f;
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float g1 = G1[e][k] * a.ig[0], g2 = G2[e][k] * a.ig[1], g3 = G3a[e][k] * a.ig[2];
-                out[edge_corner(0, e, 1)][k] += g1;
-                out[edge_corner(0, e, 0)][k] -= g1;
-                out[edge_corner(1, e, 1)][k] += g2;
-                out[edge_corner(1, e, 0)][k] -= g2;
-                out[edge_corner(2, e, 1)][k] += g3;
-                out[edge_corner(2, e, 0)][k] -= g3;
-            }
-    }
-    if (cz_e == 0)
-#pragma unroll
-        for (int o = 0; o < 8; ++o)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) scell[cell][o][k] = valid ? out[o][k] : 0.f;
-    __syncthreads();
-    // gather per node of the box from the (up to) 8 cells of this tile
-    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    float *dst = a.boxes + (long)cta * 3 * a.box;
-    for (int i = tid; i < NB; i += NT) {
-        const int bz = i / (BX * BY), r = i - bz * BX * BY, by = r / BX, bx = r - by * BX;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-            const int qx = bx - ox, qy = by - oy, qz = bz - oz;
-            if (qx < 0 || qy < 0 || qz < 0 || qx >= TX || qy >= TY || qz >= TZ) continue;
-            const int c = (qz * TY + qy) * TX + qx;
-            s0 += scell[c][o][0];
-            s1 += scell[c][o][1];
-            s2 += scell[c][o][2];
-        }
-        dst[i] = s0 * a.wscale;
-        dst[a.box + i] = s1 * a.wscale;
-        dst[2 * a.box + i] = s2 * a.wscale;
-    }
-    if (VM == 0) {
-        double t = block_sum(en.value());
-        __shared__ int sfold;
-        if (tid == 0) sfold = 0;
-        __syncthreads();
-        if (fold) atomicAdd(&sfold, fold);
-        for (int off = 16; off > 0; off >>= 1) {
-            dmn = fminf(dmn, __shfl_xor_sync(FULL, dmn, off));
-            dmx = fmaxf(dmx, __shfl_xor_sync(FULL, dmx, off));
-        }
-        __shared__ float wmn[NT / 32], wmx[NT / 32];
-        if ((tid & 31) == 0) { wmn[tid >> 5] = dmn; wmx[tid >> 5] = dmx; }
-        __syncthreads();
-        if (tid == 0) {
-            float mn = wmn[0], mxv = wmx[0];
-            for (int i = 1; i < NT / 32; ++i) { mn = fminf(mn, wmn[i]); mxv = fmaxf(mxv, wmx[i]); }
-            a.epart[cta] = t;
-            a.fold[cta] = sfold;
-            a.dmin[cta] = mn;
-            a.dmax[cta] = mxv;
-        }
-    }
-}
-
-cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st) {
-    dim3 grid(a.nb[0], a.nb[1], a.nb[2]);
-    constexpr int NT = 4 * kVccTile[0] * kVccTile[1] * kVccTile[2];
-    if (!a.diag) return launch_vcc_cells(a, st);   // gradient and GN product: one thread per cell
-    vcc_kernel<2><<<grid, NT, 0, st>>>(a);
-    return cudaGetLastError();
-}
+// gradient, GN product and GN diagonal: one thread per cell (vcc.cu)
+cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st) { return launch_vcc_cells(a, st); }
 
 // ------------------------------------------------------------------ keypoints
 int kp_blocks(int nk) { return nk <= 0 ? 1 : (nk + 255) / 256; }

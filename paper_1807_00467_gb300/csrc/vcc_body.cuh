@@ -1,6 +1,7 @@
 // Volume change control, Eqs. (7)-(9): gradient (and energy) of
-// sum_cells sum_{a,b,c} psi(d_abc) and its Gauss-Newton product
-// sum psi''(d) (grad d . v) grad d, one thread per grid cell: the body of the
+// sum_cells sum_{a,b,c} psi(d_abc), its Gauss-Newton product
+// sum psi''(d) (grad d . v) grad d and the diagonal of that product,
+// sum psi''(d) (d d / d u_{k,c})^2, one thread per grid cell: the body of the
 // kernels of vcc.cu, shared with the persistent batched PCG kernel
 // (pcg_batch.cu).
 //
@@ -11,8 +12,11 @@
 //   G1_a = sum_bc w X_bc,
 //   G2_b = sum_c e3_c x W_bc,   G3_c = sum_b W_bc x e2_b,   W_bc = sum_a w e1_a,
 // so each (b, c) pair costs one cross product (two for the directional
-// derivative) plus four dot products.  Bounds with d <= 0 are folds: weight 0
-// here, counted for the energy pass (the objective is then +inf).
+// derivative) plus four dot products.  For the diagonal, d d_abc / d u is
+// +-X_bc / g_x at the ends of e1_a, +-(e3_c x e1_a) / g_y at the ends of e2_b
+// and +-(e1_a x e2_b) / g_z at the ends of e3_c (summed where two of these
+// edges share a corner).  Bounds with d <= 0 are folds: weight 0 here,
+// counted for the energy pass (the objective is then +inf).
 #pragma once
 
 #include "common.cuh"
@@ -70,10 +74,10 @@ struct VccSmem {
 };
 
 // VM = 0: gradient of sum psi(d) (+ energy, folds, min / max d);
-// VM = 1: GN product along v.
+// VM = 1: GN product along v; VM = 2: diagonal of the GN matrix.
 template <int VM>
 __device__ __forceinline__ void vcc_cell_body(const VccArgs &a, const VBlock &vb, VccSmem &sm) {
-    constexpr bool GN = VM == 1;
+    constexpr bool GN = VM == 1, DG = VM == 2;
     float (&su)[3][NB] = sm.su;
     float (&sv)[3][NB] = sm.sv;
     float (&scell)[8 * 3][NC] = sm.scell;
@@ -134,7 +138,50 @@ __device__ __forceinline__ void vcc_cell_body(const VccArgs &a, const VBlock &vb
     int fold = 0;
     float dmn = 3.4e38f, dmx = -3.4e38f;
     Kahan32 en;
-    if constexpr (GN) {
+    float out[8][3];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) out[o][0] = out[o][1] = out[o][2] = 0.f;
+    if constexpr (DG) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const V3 X = cross(E2[b], E3[c]);
+                const V3 gx{X.x * ig0, X.y * ig0, X.z * ig0};
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa) {
+                    const float d = dot(E1[aa], X);
+                    const float rd = __fdividef(1.f, d);
+                    const float w = d > 0.f ? 2.f * rd * rd * rd : 0.f;   // psi''(d)
+                    const V3 Y = cross(E3[c], E1[aa]), Z = cross(E1[aa], E2[b]);
+                    const V3 gy{Y.x * ig1, Y.y * ig1, Y.z * ig1}, gz{Z.x * ig2, Z.y * ig2, Z.z * ig2};
+                    // corners and signs are compile-time once the loops are unrolled
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) {
+                        const int sx = (o == corner_of(0, aa, 1)) - (o == corner_of(0, aa, 0));
+                        const int sy = (o == corner_of(1, b, 1)) - (o == corner_of(1, b, 0));
+                        const int sz = (o == corner_of(2, c, 1)) - (o == corner_of(2, c, 0));
+                        if (sx == 0 && sy == 0 && sz == 0) continue;
+                        V3 g{0.f, 0.f, 0.f};
+                        bool first = true;
+                        auto term = [&](int sg, const V3 &t) {
+                            if (sg == 0) return;
+                            const V3 st = sg > 0 ? t : V3{-t.x, -t.y, -t.z};
+                            if (first) g = st;
+                            else add(st, g);
+                            first = false;
+                        };
+                        term(sx, gx);
+                        term(sy, gy);
+                        term(sz, gz);
+                        out[o][0] = fmaf(w * g.x, g.x, out[o][0]);
+                        out[o][1] = fmaf(w * g.y, g.y, out[o][1]);
+                        out[o][2] = fmaf(w * g.z, g.z, out[o][2]);
+                    }
+                }
+            }
+        }
+    } else if constexpr (GN) {
         // the x-edges in pairs (a = 2p, 2p + 1), one f32x2 lane each
         float2 e1x[2], e1y[2], e1z[2], d1x[2], d1y[2], d1z[2], g1x[2], g1y[2], g1z[2];
 #pragma unroll
@@ -211,11 +258,8 @@ __device__ __forceinline__ void vcc_cell_body(const VccArgs &a, const VBlock &vb
         }
     }
     // edge gradients onto the cell's corners (scaled by 1/g of the edge's axis)
-    float out[8][3];
 #pragma unroll
-    for (int o = 0; o < 8; ++o) out[o][0] = out[o][1] = out[o][2] = 0.f;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 4 && !DG; ++e) {
         const V3 g1{G1[e].x * ig0, G1[e].y * ig0, G1[e].z * ig0};
         const V3 g2{G2[e].x * ig1, G2[e].y * ig1, G2[e].z * ig1};
         const V3 g3{G3[e].x * ig2, G3[e].y * ig2, G3[e].z * ig2};

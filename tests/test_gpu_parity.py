@@ -266,6 +266,24 @@ def test_pcg_tiny(tiny):
     assert rel_l2(p.cpu().numpy(), po) <= 1e-4
 
 
+@pytest.mark.parametrize("m,gamma", [(TINY_M, 1.0), ((9, 9, 7), 1.0), (TINY_M, 0.001)])
+def test_pcg_first_step_is_the_jacobi_direction(tiny, m, gamma):
+    """From p0 = 0 one PCG step is alpha M^-1 g: on the same right-hand side it
+    checks the Jacobi diagonal M (NGF, curvature and volume-change parts; the
+    volume-change part dominant at gamma = 1, a ragged cell grid in the second
+    case) against the oracle's."""
+    u = _u0(tiny, m) + phantom.random_grid_field(m, 7, scale=0.2)
+    ctx = gpu_context(tiny, m, gamma=gamma)
+    _, g = ctx.gn_linearize(to_dev(u))
+    p, stats = ctx.gn_pcg_solve(g, 1)
+    gh = g.cpu().numpy().astype(np.float64)
+    po, so = oracle_problem(tiny, m, gamma=gamma).linearize(u).pcg(gh, 1)
+    assert stats.cpu().numpy()[0] == so[0] == 1
+    err = rel_l2(p.cpu().numpy(), po)
+    print(f"m={m} gamma={gamma}: first PCG step rel-L2 {err:.2e}")
+    assert err <= TOL_GRAD
+
+
 def _replay(ph, m, ctx, u, gn_iters, pcg_iters, steps_checked=None, gamma=0.001):
     """Run the GPU schedule one Gauss-Newton step at a time; the oracle repeats
     chosen steps from the GPU's iterate (per-step parity, 0.01 mm)."""
