@@ -134,8 +134,9 @@ typedef struct {
 typedef struct rg_ctx rg_ctx;
 
 /* Workspace bytes a context for this problem needs (nk_max: the largest
- * keypoint count rg_set_keypoints will be given; pcg_max: the longest PCG
- * solve, 0..RG_PCG_MAX, whose residual history the workspace keeps).
+ * keypoint count rg_set_keypoints will be given, at most 2^27, with a grid of
+ * fewer than 2^31 nodes when nonzero; pcg_max: the longest PCG solve,
+ * 0..RG_PCG_MAX, whose residual history the workspace keeps).
  * Returns RG_EINVAL on bad geometry or sizes. */
 int rg_workspace_size(const rg_image_geom *img, const rg_grid_geom *grid, rg_dtype dtype,
                       int32_t nk_max, int32_t pcg_max, size_t *bytes);
@@ -179,7 +180,11 @@ int rg_autotune(rg_ctx *ctx, const float *u_dev, int32_t *tile_y, int32_t *gener
  * The pointers must stay valid while the context uses them. */
 int rg_set_images(rg_ctx *ctx, const void *R_dev, const void *T_dev);
 
-/* Borrow keypoints: x_dev, ykp_dev are float32 [nk][3] (mm), Eq. (10). */
+/* Borrow keypoints: x_dev, ykp_dev are float32 [nk][3] (mm), Eq. (10).
+ * Also indexes the keypoints' cells on the context stream (the trilinear
+ * weights of x_i are fixed), so the penalty's node sums are gathered in a
+ * fixed order, without atomics: the same bits on every call.  x_dev's
+ * contents must not change while set; call again after changing them. */
 int rg_set_keypoints(rg_ctx *ctx, int32_t nk, const float *x_dev, const float *ykp_dev);
 
 /* terms_dev: double[5] = {D, R, V, K, J}, Eq. (11).  J = +inf on a fold. */

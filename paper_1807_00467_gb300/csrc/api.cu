@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <map>
@@ -58,6 +59,7 @@ struct rg_ctx {
     int pass_sel;                 // objective / gradient pass: 0 by size, 1 column-marching, 2 tile
                                   // (autotuner choice, or the RG_HOOK_PASS test hook)
     double *rzh, *pcgpart, *rzpart, *apart;   // PCG: r_j.z_j, coefficient / r.z / d.q partials
+    KpIndex kpix;             // keypoint index (rebuilt by rg_set_keypoints)
     PcgScalars *sc;
     bool has_lin, minv_valid;
     char err[512];
@@ -291,6 +293,13 @@ static void layout(rg_ctx *c, Carver &cv) {
     c->gnrep = cv.take<double>(RG_REPORT_COLS * kGnRows);
     c->range_terms = cv.take<double>(8);
     c->bctl = cv.take<unsigned>(kBatchCtlWords);
+    const long nkx = c->nk_max > 0 ? c->nk_max : 0;
+    c->kpix.cell = cv.take<int>(nkx);
+    c->kpix.frac = cv.take<float>(3 * nkx);
+    c->kpix.sb = cv.take<int>(nkx);
+    c->kpix.perm = cv.take<int>(nkx);
+    c->kpix.src = cv.take<float>(3 * nkx);
+    c->kpix.soc = cv.take<int>(nkx > 0 ? M : 0);
 }
 
 static void derive(rg_ctx *c) {
@@ -347,6 +356,8 @@ extern "C" int rg_workspace_size(const rg_image_geom *img, const rg_grid_geom *g
     if (check_geom(img, grid) != RG_OK || !bytes || (dtype != RG_F32 && dtype != RG_F16) || nk_max < 0 ||
         pcg_max < 0 || pcg_max > RG_PCG_MAX)
         return RG_EINVAL;
+    // the keypoint index holds cell indices and 8 nk gather threads in int
+    if (nk_max > (1 << 27) || (nk_max > 0 && (long)grid->m[0] * grid->m[1] * grid->m[2] > INT_MAX)) return RG_EINVAL;
     rg_ctx tmp;
     memset(&tmp, 0, sizeof tmp);
     tmp.img = *img;
@@ -500,6 +511,24 @@ extern "C" int rg_set_images(rg_ctx *c, const void *R, const void *T) {
     return RG_OK;
 }
 
+// keypoint launch arguments of the context (geometry, keypoints, index)
+static KpArgs kp_args(const rg_ctx *c) {
+    KpArgs k;
+    for (int i = 0; i < 3; ++i) {
+        k.m[i] = c->grid.m[i];
+        k.ig[i] = (float)(1.0 / c->g[i]);
+    }
+    k.nk = c->nk;
+    k.kx = c->kx;
+    k.ky = c->ky;
+    k.u = k.v = nullptr;
+    k.scale = 1.f;
+    k.out = nullptr;
+    k.part = nullptr;
+    k.ix = c->kpix;
+    return k;
+}
+
 extern "C" int rg_set_keypoints(rg_ctx *c, int32_t nk, const float *x, const float *y) {
     if (!c) return RG_EINVAL;
     if (nk < 0 || nk > c->nk_max || (nk > 0 && (!x || !y)))
@@ -508,6 +537,7 @@ extern "C" int rg_set_keypoints(rg_ctx *c, int32_t nk, const float *x, const flo
     c->kx = x;
     c->ky = y;
     c->minv_valid = false;
+    if (nk > 0) LAUNCH(7, launch_kp_index(kp_args(c), c->st));
     return RG_OK;
 }
 
@@ -674,14 +704,7 @@ static int run_nodes(rg_ctx *c, const float *v, bool energy, float *out, double 
 
 static int run_kp(rg_ctx *c, const float *u, const float *v, double scale, float *out, bool energy) {
     if (c->nk <= 0) return RG_OK;
-    KpArgs k;
-    for (int i = 0; i < 3; ++i) {
-        k.m[i] = c->grid.m[i];
-        k.ig[i] = (float)(1.0 / c->g[i]);
-    }
-    k.nk = c->nk;
-    k.kx = c->kx;
-    k.ky = c->ky;
+    KpArgs k = kp_args(c);
     k.u = u;
     k.v = v;
     k.scale = (float)scale;
@@ -811,12 +834,8 @@ extern "C" int regularizer_apply(rg_ctx *c, int32_t which, const float *u, const
     } else if (which == RG_KP) {
         CK(cudaMemsetAsync(out, 0, sizeof(float) * 3 * c->M, c->st));
         if (c->nk > 0) {
-            KpArgs k;
-            for (int i = 0; i < 3; ++i) {
-                k.m[i] = c->grid.m[i];
-                k.ig[i] = (float)(1.0 / c->g[i]);
-            }
-            k.nk = c->nk; k.kx = c->kx; k.ky = c->ky; k.u = u; k.v = v; k.scale = 1.f; k.out = out; k.part = c->kpart;
+            KpArgs k = kp_args(c);
+            k.u = u; k.v = v; k.scale = 1.f; k.out = out; k.part = c->kpart;
             LAUNCH(7, launch_kp(k, c->st));
         }
         if (energy) {
@@ -839,14 +858,10 @@ static int ensure_minv(rg_ctx *c) {
     const bool vcc = c->P.gamma != 0.0;
     if (vcc && (st = run_vcc(c, c->lin_u, nullptr, 1))) return st;
     if ((st = run_nodes(c, nullptr, false, c->minv, 2.0 * c->hbar, c->P.gamma * c->ghat, 0.0, true, vcc))) return st;
-    float ig2[3], ig[3];
-    for (int i = 0; i < 3; ++i) {
-        ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
-        ig[i] = (float)(1.0 / c->g[i]);
-    }
+    float ig2[3];
+    for (int i = 0; i < 3; ++i) ig2[i] = (float)(1.0 / (c->g[i] * c->g[i]));
     LAUNCH(10, launch_jacobi_diag(1, c->grid.m, ig2, c->P.alpha * c->ghat, c->P.tau, c->minv, c->st));
-    if (c->nk > 0 && c->P.delta != 0.0)
-        LAUNCH(10, launch_kp_diag(c->grid.m, ig, c->nk, c->kx, 2.0 * c->P.delta, c->minv, c->st));
+    if (c->nk > 0 && c->P.delta != 0.0) LAUNCH(10, launch_kp_diag(kp_args(c), 2.0 * c->P.delta, c->minv, c->st));
     LAUNCH(10, launch_invert(3 * c->M, c->minv, c->st));
     c->minv_valid = true;
     return RG_OK;

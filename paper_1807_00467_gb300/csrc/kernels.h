@@ -88,6 +88,18 @@ cudaError_t launch_curv(const NodeArgs &a, cudaStream_t st);
 cudaError_t launch_nodes(const NodeArgs &a, cudaStream_t st);
 
 // Keypoint penalty, Eq. (10).
+// The keypoint index (launch_kp_index, once per set of keypoints): every
+// keypoint's cell (linear index of its lowest node) and fractions, the
+// keypoints sorted by (cell, keypoint index), and for every cell the sorted
+// position of its first keypoint (-1: none).  The node sums gather through it
+// without atomics.
+struct KpIndex {
+    int *cell;             // [nk]
+    float *frac;           // [nk][3]
+    int *sb, *perm;        // [nk]: sorted cells, keypoint at each sorted position
+    int *soc;              // [M]: first sorted position of each cell, -1 if none
+    float *src;            // [nk][3]: per-call scratch (res_i, or (P v)(x_i))
+};
 struct KpArgs {
     int m[3];
     float ig[3];           // 1 / g_a
@@ -96,11 +108,13 @@ struct KpArgs {
     const float *u;        // [3][M]
     const float *v;        // NULL: gradient 2 P^T res; else 2 P^T P v
     float scale;           // multiplies the node contributions (delta)
-    float *out;            // accumulated with atomics
+    float *out;            // the node contributions are added to it (NULL: energy only)
     double *part;          // per-CTA partial sums of |res|^2
+    KpIndex ix;
     const int *skip = nullptr;   // nonzero: the launch does nothing
 };
 int kp_blocks(int nk);
+cudaError_t launch_kp_index(const KpArgs &a, cudaStream_t st);
 cudaError_t launch_kp(const KpArgs &a, cudaStream_t st);
 
 // Objective terms {D, R, V, K, J} from the partial sums.
@@ -125,8 +139,7 @@ struct PcgScalars {
 int vec_blocks(long n);
 cudaError_t launch_jacobi_diag(int alpha_on, const int *m, const float *ig2, double alpha_ghat, double tau,
                                float *minv, cudaStream_t st);
-cudaError_t launch_kp_diag(const int *m, const float *ig, int nk, const float *kx, double two_delta, float *diag,
-                           cudaStream_t st);
+cudaError_t launch_kp_diag(const KpArgs &a, double two_delta, float *diag, cudaStream_t st);
 cudaError_t launch_invert(long n, float *d, cudaStream_t st);
 cudaError_t launch_dot(long n, const float *x, const float *y, double *part, cudaStream_t st);
 cudaError_t launch_pcg_scalar(int which, const double *part, int nparts, PcgScalars *sc, cudaStream_t st,

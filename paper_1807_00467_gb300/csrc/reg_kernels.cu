@@ -39,8 +39,80 @@ struct Kahan {
 cudaError_t launch_vcc(const VccArgs &a, cudaStream_t st) { return launch_vcc_cells(a, st); }
 
 // ------------------------------------------------------------------ keypoints
+// A keypoint's trilinear weights are fixed by its position x_i: cell c_i =
+// floor(x_i / g) clamped to the grid, fractions f_i = x_i / g - c_i.  The
+// index built once per set of keypoints sorts them by (cell, i); the node
+// sums 2 P^T src (gradient: src_i = x_i + (P u)(x_i) - y_i; GN product: src_i =
+// (P v)(x_i); diagonal: 2 delta w^2) are then gathered without atomics: node
+// n receives from the cells n - o of its corner offsets o = 0..7 in the order
+// (o, i), summed by one thread (the one of the smallest o whose cell holds
+// keypoints), so repeated calls give the same bits.
 int kp_blocks(int nk) { return nk <= 0 ? 1 : (nk + 255) / 256; }
 
+// corner o = ox + 2 oy + 4 oz of a cell: trilinear weight from the fractions
+__device__ __forceinline__ float kp_weight(int o, const float *f) {
+    return ((o & 1) ? f[0] : 1.f - f[0]) * ((o & 2) ? f[1] : 1.f - f[1]) * ((o & 4) ? f[2] : 1.f - f[2]);
+}
+
+// index, step 1: cell and fractions of every keypoint
+__global__ void kp_cells_kernel(const KpArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nk) return;
+    const int mm[3] = {a.m[0], a.m[1], a.m[2]};
+    int c[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        const float t = a.kx[3 * i + ax] * a.ig[ax];
+        const int ci = max(0, min((int)floorf(t), mm[ax] - 2));
+        c[ax] = ci;
+        a.ix.frac[3 * i + ax] = t - ci;
+    }
+    a.ix.cell[i] = (c[2] * mm[1] + c[1]) * mm[0] + c[0];
+}
+
+// index, step 2: the rank of (cell_i, i) among all keypoints (a permutation:
+// the pairs are distinct), keypoints in 256-wide shared-memory tiles
+__global__ void __launch_bounds__(256) kp_rank_kernel(const KpArgs a) {
+    __shared__ int tile[256];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ci = i < a.nk ? a.ix.cell[i] : 0;
+    int rank = 0;
+    for (int j0 = 0; j0 < a.nk; j0 += 256) {
+        __syncthreads();
+        if (j0 + (int)threadIdx.x < a.nk) tile[threadIdx.x] = a.ix.cell[j0 + threadIdx.x];
+        __syncthreads();
+        const int nj = min(256, a.nk - j0);
+        for (int t = 0; t < nj; ++t) {
+            const int cj = tile[t];
+            rank += (cj < ci || (cj == ci && j0 + t < i)) ? 1 : 0;
+        }
+    }
+    if (i < a.nk) {
+        a.ix.perm[rank] = i;
+        a.ix.sb[rank] = ci;
+    }
+}
+
+// index, step 3: the first sorted position of every cell that holds keypoints
+// (soc is -1 everywhere before)
+__global__ void kp_heads_kernel(const KpArgs a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.nk) return;
+    if (r == 0 || a.ix.sb[r] != a.ix.sb[r - 1]) a.ix.soc[a.ix.sb[r]] = r;
+}
+
+cudaError_t launch_kp_index(const KpArgs &a, cudaStream_t st) {
+    if (a.nk <= 0) return cudaSuccess;
+    const long M = (long)a.m[0] * a.m[1] * a.m[2];
+    cudaError_t e = cudaMemsetAsync(a.ix.soc, 0xff, sizeof(int) * M, st);
+    if (e != cudaSuccess) return e;
+    const int nb = kp_blocks(a.nk);
+    kp_cells_kernel<<<nb, 256, 0, st>>>(a);
+    kp_rank_kernel<<<nb, 256, 0, st>>>(a);
+    kp_heads_kernel<<<nb, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// per keypoint: residual (energy) and the source of its node contributions
 __global__ void kp_kernel(const KpArgs a) {
     if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,25 +120,14 @@ __global__ void kp_kernel(const KpArgs a) {
     const long mxy = (long)mx * my, M = mxy * mz;
     float e = 0.f;
     if (i < a.nk) {
-        int c[3];
-        float f[3];
-        const int mm[3] = {mx, my, mz};
-        for (int ax = 0; ax < 3; ++ax) {
-            const float t = a.kx[3 * i + ax] * a.ig[ax];
-            int ci = (int)floorf(t);
-            ci = max(0, min(ci, mm[ax] - 2));
-            c[ax] = ci;
-            f[ax] = t - ci;
-        }
-        const long base = (long)c[2] * mxy + (long)c[1] * mx + c[0];
+        const float f[3] = {a.ix.frac[3 * i], a.ix.frac[3 * i + 1], a.ix.frac[3 * i + 2]};
+        const long base = a.ix.cell[i];
         float w[8];
         long nd[8];
         for (int o = 0; o < 8; ++o) {
-            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-            w[o] = (ox ? f[0] : 1.f - f[0]) * (oy ? f[1] : 1.f - f[1]) * (oz ? f[2] : 1.f - f[2]);
-            nd[o] = base + ox + oy * mx + oz * mxy;
+            w[o] = kp_weight(o, f);
+            nd[o] = base + (o & 1) + ((o >> 1) & 1) * mx + (o >> 2) * mxy;
         }
-        float src[3];
         for (int k = 0; k < 3; ++k) {
             float pu = 0.f, pv = 0.f;
             for (int o = 0; o < 8; ++o) {
@@ -75,11 +136,8 @@ __global__ void kp_kernel(const KpArgs a) {
             }
             const float res = a.kx[3 * i + k] + pu - a.ky[3 * i + k];
             e = fmaf(res, res, e);
-            src[k] = a.v ? pv : res;
+            if (a.out) a.ix.src[3 * i + k] = a.v ? pv : res;
         }
-        if (a.out)
-            for (int o = 0; o < 8; ++o)
-                for (int k = 0; k < 3; ++k) atomicAdd(a.out + k * M + nd[o], 2.f * a.scale * w[o] * src[k]);
     }
     if (a.part) {
         double t = block_sum((double)e);
@@ -87,8 +145,58 @@ __global__ void kp_kernel(const KpArgs a) {
     }
 }
 
+// node sums: thread (r, o) for the first sorted keypoint r of a cell and a
+// corner o of that cell owns node n = cell + o unless a cell n - o' with o' < o
+// holds keypoints; the owner adds, in the order (o'', i), the contributions
+// of every keypoint in the cells n - o'' to out[n] (diag: 2 delta w^2 to all
+// three components; else 2 scale w src_i)
+template <bool DIAG>
+__global__ void kp_gather_kernel(const KpArgs a, double two_delta, float *out) {
+    if (a.skip && *a.skip) return;   // uniform: every block reads the same flag
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = t >> 3, o = t & 7;
+    if (r >= a.nk) return;
+    const int *sb = a.ix.sb;
+    if (r > 0 && sb[r] == sb[r - 1]) return;
+    const int mx = a.m[0], my = a.m[1];
+    const long mxy = (long)mx * my, M = mxy * a.m[2];
+    const int b = sb[r];
+    const int cz = b / (int)mxy, cy = (b - cz * (int)mxy) / mx, cx = b - cz * (int)mxy - cy * mx;
+    const int nx = cx + (o & 1), ny = cy + ((o >> 1) & 1), nz = cz + (o >> 2);
+    // the cell n - o' of corner offset o', or -1 outside the cell grid
+    auto cell_at = [&](int op) {
+        const int x = nx - (op & 1), y = ny - ((op >> 1) & 1), z = nz - (op >> 2);
+        if (x < 0 || y < 0 || z < 0 || x > mx - 2 || y > my - 2 || z > a.m[2] - 2) return -1;
+        return (z * my + y) * mx + x;
+    };
+    for (int op = 0; op < o; ++op) {
+        const int c = cell_at(op);
+        if (c >= 0 && a.ix.soc[c] >= 0) return;
+    }
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int op = 0; op < 8; ++op) {
+        const int c = cell_at(op);
+        const int s = c >= 0 ? a.ix.soc[c] : -1;
+        if (s < 0) continue;
+        for (int q = s; q < a.nk && sb[q] == c; ++q) {
+            const int i = a.ix.perm[q];
+            const float f[3] = {a.ix.frac[3 * i], a.ix.frac[3 * i + 1], a.ix.frac[3 * i + 2]};
+            const float w = kp_weight(op, f);
+            if (DIAG) {
+                const float add = (float)(two_delta * w * w);
+                acc[0] += add; acc[1] += add; acc[2] += add;
+            } else {
+                for (int k = 0; k < 3; ++k) acc[k] += 2.f * a.scale * w * a.ix.src[3 * i + k];
+            }
+        }
+    }
+    const long n = (long)nz * mxy + (long)ny * mx + nx;
+    for (int k = 0; k < 3; ++k) out[k * M + n] += acc[k];
+}
+
 cudaError_t launch_kp(const KpArgs &a, cudaStream_t st) {
     kp_kernel<<<kp_blocks(a.nk), 256, 0, st>>>(a);
+    if (a.out && a.nk > 0) kp_gather_kernel<false><<<(8 * a.nk + 255) / 256, 256, 0, st>>>(a, 0.0, a.out);
     return cudaGetLastError();
 }
 
@@ -186,35 +294,9 @@ cudaError_t launch_jacobi_diag(int alpha_on, const int *m, const float *ig2, dou
     return cudaGetLastError();
 }
 
-__global__ void kp_diag_kernel(int mx, int my, int mz, float igx, float igy, float igz, int nk, const float *kx,
-                               double two_delta, float *diag) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nk) return;
-    const long mxy = (long)mx * my, M = mxy * mz;
-    const int mm[3] = {mx, my, mz};
-    const float ig[3] = {igx, igy, igz};
-    int c[3];
-    float f[3];
-    for (int ax = 0; ax < 3; ++ax) {
-        const float t = kx[3 * i + ax] * ig[ax];
-        int ci = (int)floorf(t);
-        ci = max(0, min(ci, mm[ax] - 2));
-        c[ax] = ci;
-        f[ax] = t - ci;
-    }
-    for (int o = 0; o < 8; ++o) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-        const float w = (ox ? f[0] : 1.f - f[0]) * (oy ? f[1] : 1.f - f[1]) * (oz ? f[2] : 1.f - f[2]);
-        const long nd = (long)(c[2] + oz) * mxy + (long)(c[1] + oy) * mx + c[0] + ox;
-        const float add = (float)(two_delta * w * w);
-        for (int k = 0; k < 3; ++k) atomicAdd(diag + k * M + nd, add);
-    }
-}
-
-cudaError_t launch_kp_diag(const int *m, const float *ig, int nk, const float *kx, double two_delta, float *diag,
-                           cudaStream_t st) {
-    if (nk <= 0) return cudaSuccess;
-    kp_diag_kernel<<<(nk + 255) / 256, 256, 0, st>>>(m[0], m[1], m[2], ig[0], ig[1], ig[2], nk, kx, two_delta, diag);
+cudaError_t launch_kp_diag(const KpArgs &a, double two_delta, float *diag, cudaStream_t st) {
+    if (a.nk <= 0) return cudaSuccess;
+    kp_gather_kernel<true><<<(8 * a.nk + 255) / 256, 256, 0, st>>>(a, two_delta, diag);
     return cudaGetLastError();
 }
 

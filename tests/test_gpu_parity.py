@@ -197,6 +197,60 @@ def test_keypoint_objective_gradient_matvec():
     assert rel_l2(ctx.gn_matvec(to_dev(v)).cpu().numpy(), P.linearize(u).matvec(v)) <= TOL_MV
 
 
+def _crowded_keypoints(ph, m, nk, seed):
+    """Keypoints crowded into the 8 cells around one node (many per cell, so
+    every node there gathers from several cells), some on nodes, some spread
+    over the grid including its faces, two on the far corner (clamped cell,
+    fraction 1); targets y = x + N(0, 2 mm)."""
+    g = np.array([ph.n[a] * ph.h[a] / (m[a] - 1) for a in range(3)])
+    rng = np.random.default_rng(seed)
+    node = np.array([m[0] // 2, m[1] // 2, m[2] // 2])
+    kx = (node + rng.uniform(-1.0, 1.0, size=(nk, 3))) * g
+    kx[: nk // 8] = (node + rng.integers(-1, 2, size=(nk // 8, 3))) * g
+    kx[nk // 8: nk // 4] = rng.uniform(0.0, 1.0, size=(nk // 4 - nk // 8, 3)) * g * (np.array(m) - 1)
+    kx[-2:] = (np.array(m) - 1) * g
+    ky = kx + rng.normal(0.0, 2.0, size=(nk, 3))
+    return kx.astype(np.float32), ky.astype(np.float32)
+
+
+def test_keypoint_node_sums_crowded_cells_are_exact_and_repeatable(tiny):
+    """The keypoint penalty (Eq. 10) with many keypoints per cell: energy,
+    gradient 2 P^T res and GN product 2 P^T P v against the oracle, the same
+    bits on repeated calls (the node sums are gathered in a fixed order), and
+    its Jacobi diagonal 2 delta sum w^2 through the first PCG step."""
+    import torch
+
+    import oracle
+    from paper_1807_00467_gb300 import api
+    m = TINY_M
+    nk = 400
+    kx, ky = _crowded_keypoints(tiny, m, nk, 11)
+    u = _u0(tiny, m)
+    v = phantom.random_grid_field(m, 12)
+    ctx = api.Context(torch.from_numpy(tiny.R).cuda(), torch.from_numpy(tiny.T).cuda(), tiny.h, m,
+                      api.make_params(eta=10.0, alpha=1.0, gamma=0.0, delta=5.0), nk_max=nk)
+    ctx.set_keypoints(to_dev(kx), to_dev(ky))
+    P = oracle.Problem(tiny.R, tiny.T, tiny.h, m, eta=10.0, alpha=1.0, gamma=0.0, delta=5.0,
+                       kx=kx.astype(np.float64), ky=ky.astype(np.float64))
+    e, gk = ctx.regularizer_apply(api.RG_KP, to_dev(u))
+    _, hv = ctx.regularizer_apply(api.RG_KP, to_dev(u), to_dev(v))
+    eo, go = P.keypoints(u)
+    _, hvo = P.keypoints(u, v)
+    assert rel(e.item(), eo) <= TOL_OBJ
+    assert rel_l2(gk.cpu().numpy(), go) <= TOL_GRAD
+    assert rel_l2(hv.cpu().numpy(), hvo) <= TOL_MV
+    for _ in range(3):
+        e2, g2 = ctx.regularizer_apply(api.RG_KP, to_dev(u))
+        _, h2 = ctx.regularizer_apply(api.RG_KP, to_dev(u), to_dev(v))
+        assert e2.item() == e.item() and torch.equal(g2, gk) and torch.equal(h2, hv)
+    # the preconditioner: keypoint diagonal dominant at delta = 5
+    _, g = ctx.gn_linearize(to_dev(u))
+    p, stats = ctx.gn_pcg_solve(g, 1)
+    po, so = P.linearize(u).pcg(g.cpu().numpy().astype(np.float64), 1)
+    assert stats.cpu().numpy()[0] == so[0] == 1
+    assert rel_l2(p.cpu().numpy(), po) <= TOL_GRAD
+
+
 @pytest.mark.parametrize("n,h,m", [
     ((40, 24, 20), (1.1, 0.9, 2.0), (21, 7, 11)),     # rho (2, 4, 2), ragged tiles in x, y, z
     ((64, 32, 16), (1.0, 1.3, 2.5), (9, 5, 3)),       # rho 8
