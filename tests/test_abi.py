@@ -65,6 +65,16 @@ def test_workspace_size_and_geometry_validation(lib):
         assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, 30, C.byref(sz)) == -1
     ig, gg = _geom((64, 64, 48), (1.0, -1.0, 1.0), (17, 17, 13))
     assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, 30, C.byref(sz)) == -1
+    # the keypoint index: per keypoint its cell, fractions, sorted cell, rank
+    # owner and source (36 B), per node the first sorted keypoint of its cell
+    # (4 B); at most 2^27 keypoints
+    ig, gg = _geom((64, 64, 48), (1.0, 1.0, 1.0), (17, 17, 13))
+    s0, s1 = C.c_size_t(), C.c_size_t()
+    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 0, 30, C.byref(s0)) == 0
+    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 1000, 30, C.byref(s1)) == 0
+    assert s1.value - s0.value >= 36 * 1000 + 4 * 17 * 17 * 13
+    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, 1 << 27, 30, C.byref(sz)) == 0
+    assert lib.rg_workspace_size(C.byref(ig), C.byref(gg), 0, (1 << 27) + 1, 30, C.byref(sz)) == -1
 
 
 def test_context_host_validation(lib):
