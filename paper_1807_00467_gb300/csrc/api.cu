@@ -537,7 +537,10 @@ extern "C" int rg_set_keypoints(rg_ctx *c, int32_t nk, const float *x, const flo
     c->kx = x;
     c->ky = y;
     c->minv_valid = false;
-    if (nk > 0) LAUNCH(7, launch_kp_index(kp_args(c), c->st));
+    if (nk > 0) {
+        const KpArgs k = kp_args(c);
+        for (int step = 0; step < 3; ++step) LAUNCH(7, launch_kp_index(k, step, c->st));
+    }
     return RG_OK;
 }
 
@@ -712,6 +715,7 @@ static int run_kp(rg_ctx *c, const float *u, const float *v, double scale, float
     k.part = energy ? c->kpart : nullptr;
     k.skip = c->skip;
     LAUNCH(7, launch_kp(k, c->st));
+    if (out) LAUNCH(7, launch_kp_gather(k, c->st));
     return RG_OK;
 }
 
@@ -837,6 +841,7 @@ extern "C" int regularizer_apply(rg_ctx *c, int32_t which, const float *u, const
             KpArgs k = kp_args(c);
             k.u = u; k.v = v; k.scale = 1.f; k.out = out; k.part = c->kpart;
             LAUNCH(7, launch_kp(k, c->st));
+            LAUNCH(7, launch_kp_gather(k, c->st));
         }
         if (energy) {
             if ((st = run_terms(c, c->terms_tmp, false, false, false, true))) return st;

@@ -114,8 +114,10 @@ struct KpArgs {
     const int *skip = nullptr;   // nonzero: the launch does nothing
 };
 int kp_blocks(int nk);
-cudaError_t launch_kp_index(const KpArgs &a, cudaStream_t st);
-cudaError_t launch_kp(const KpArgs &a, cudaStream_t st);
+// index steps 0 (cells and fractions), 1 (ranks), 2 (first rank per cell)
+cudaError_t launch_kp_index(const KpArgs &a, int step, cudaStream_t st);
+cudaError_t launch_kp(const KpArgs &a, cudaStream_t st);          // residuals, energy, sources
+cudaError_t launch_kp_gather(const KpArgs &a, cudaStream_t st);   // node sums into a.out
 
 // Objective terms {D, R, V, K, J} from the partial sums.
 struct TermsArgs {

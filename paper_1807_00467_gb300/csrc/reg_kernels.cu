@@ -100,15 +100,19 @@ __global__ void kp_heads_kernel(const KpArgs a) {
     if (r == 0 || a.ix.sb[r] != a.ix.sb[r - 1]) a.ix.soc[a.ix.sb[r]] = r;
 }
 
-cudaError_t launch_kp_index(const KpArgs &a, cudaStream_t st) {
+cudaError_t launch_kp_index(const KpArgs &a, int step, cudaStream_t st) {
     if (a.nk <= 0) return cudaSuccess;
-    const long M = (long)a.m[0] * a.m[1] * a.m[2];
-    cudaError_t e = cudaMemsetAsync(a.ix.soc, 0xff, sizeof(int) * M, st);
-    if (e != cudaSuccess) return e;
     const int nb = kp_blocks(a.nk);
-    kp_cells_kernel<<<nb, 256, 0, st>>>(a);
-    kp_rank_kernel<<<nb, 256, 0, st>>>(a);
-    kp_heads_kernel<<<nb, 256, 0, st>>>(a);
+    if (step == 0) {
+        const long M = (long)a.m[0] * a.m[1] * a.m[2];
+        const cudaError_t e = cudaMemsetAsync(a.ix.soc, 0xff, sizeof(int) * M, st);
+        if (e != cudaSuccess) return e;
+        kp_cells_kernel<<<nb, 256, 0, st>>>(a);
+    } else if (step == 1) {
+        kp_rank_kernel<<<nb, 256, 0, st>>>(a);
+    } else {
+        kp_heads_kernel<<<nb, 256, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -196,7 +200,12 @@ __global__ void kp_gather_kernel(const KpArgs a, double two_delta, float *out) {
 
 cudaError_t launch_kp(const KpArgs &a, cudaStream_t st) {
     kp_kernel<<<kp_blocks(a.nk), 256, 0, st>>>(a);
-    if (a.out && a.nk > 0) kp_gather_kernel<false><<<(8 * a.nk + 255) / 256, 256, 0, st>>>(a, 0.0, a.out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kp_gather(const KpArgs &a, cudaStream_t st) {
+    if (!a.out || a.nk <= 0) return cudaSuccess;
+    kp_gather_kernel<false><<<(8 * a.nk + 255) / 256, 256, 0, st>>>(a, 0.0, a.out);
     return cudaGetLastError();
 }
 
