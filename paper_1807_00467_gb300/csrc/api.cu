@@ -1444,8 +1444,12 @@ extern "C" int register_pyramid(const rg_image_geom *img, const void *R, const v
         rg_ctx *cl = nullptr;
         int e = rg_ctx_create(&cl, &il[l], &gl[l], dtype, &P, nk, s->pcg_iters, wl, w, stream);
         if (e != RG_OK) return e;
-        rg_set_images(cl, Rl[l], Tl[l]);
-        if (nk > 0) rg_set_keypoints(cl, nk, kx, ky);
+        e = rg_set_images(cl, Rl[l], Tl[l]);
+        if (e == RG_OK && nk > 0) e = rg_set_keypoints(cl, nk, kx, ky);
+        if (e != RG_OK) {
+            rg_ctx_destroy(cl);
+            return e;
+        }
         status = gn_solve_impl(cl, ul[l], s, report ? report + (long)(Lc - l) * s->gn_iters * RG_REPORT_COLS : nullptr,
                                P.delta_adaptive != 0 && l == Lc);
         P.delta = cl->P.delta;
